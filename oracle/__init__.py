@@ -1,0 +1,199 @@
+"""FP64 CPU oracle for the differentiable ambiguity function (test infrastructure).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline / reference
+legs of ``bench.py`` may import this package.  It loads ``graf_oracle.c``
+(plain C, direct double sums, no FFT) through ctypes, compiling it with gcc on
+first use, and shares no code with the CUDA library.
+
+Conventions (paper Sec. 4.1, Eqs. 8, 11, 12, 17-19, 22):
+  * ``s`` is complex128 of length N; ``phi`` float64 phases, s = exp(j phi).
+  * windows are ``(k_lo, k_hi, m_lo, m_hi, k_ml, m_ml)``: delay and Doppler
+    ranges (inclusive, Doppler in fftshift order [-M/2, M/2-1]) and the
+    mainlobe box |k|<=k_ml and |m|<=m_ml that the losses exclude.
+  * loss scalars ``out8`` = (L, PSL_soft, ISL, PSL_hard, E, |Omega|,
+    sum_Omega p*Ahat^2, 0).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "graf_oracle.c")
+_LIB_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_LIB_DIR, "liborc.so")
+_lock = threading.Lock()
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int64)
+_i64 = ctypes.c_int64
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/liborc.so`` (gcc, -O2)."""
+    os.makedirs(_LIB_DIR, exist_ok=True)
+    stale = (not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC)
+    if force or stale:
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", _SRC, "-o", tmp,
+                               "-lm", "-lpthread"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.orc_signal_from_phase.argtypes = [_dp, _i64, _dp]
+            lib.orc_energy.argtypes = [_dp, _i64]
+            lib.orc_energy.restype = ctypes.c_double
+            lib.orc_af_complex.argtypes = [_dp, _i64, _i64, _i64, _i64, _i64, _i64, _dp, ctypes.c_int]
+            lib.orc_af_ahat.argtypes = [_dp, _i64, _i64, _i64, _i64, _i64, _i64, ctypes.c_double,
+                                        _dp, ctypes.c_int]
+            lib.orc_af_cells.argtypes = [_dp, _i64, _i64, _i64, _ip, _ip, ctypes.c_double, _dp]
+            lib.orc_loss.argtypes = [_dp, _i64, _i64, _ip, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_double, _dp, ctypes.c_int]
+            lib.orc_grad.argtypes = [_dp, _i64, _i64, _ip, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_double, _dp, _dp, _dp, ctypes.c_int]
+            lib.orc_fd_grad_phi.argtypes = [_dp, _i64, _i64, _ip, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp,
+                                            ctypes.c_int]
+            lib.orc_fd_grad_s.argtypes = [_dp, _i64, _i64, _ip, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp,
+                                          ctypes.c_int]
+            for f in ("orc_af_complex", "orc_af_ahat", "orc_af_cells", "orc_loss", "orc_grad",
+                      "orc_fd_grad_phi", "orc_fd_grad_s"):
+                getattr(lib, f).restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _threads(nthreads):
+    return int(nthreads) if nthreads else (os.cpu_count() or 1)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _s_buf(s):
+    s = np.ascontiguousarray(np.asarray(s, dtype=np.complex128))
+    return s, s.view(np.float64)
+
+
+def _check(st, what):
+    if st != 0:
+        raise ValueError(f"oracle {what} failed with status {st}")
+
+
+def full_window(N: int, M: int, k_ml: int = 0, m_ml=None):
+    """All 2N-1 delays and all M Doppler bins.  ``m_ml=None`` gives the default
+    mainlobe box of the full-AF workloads: k=0, |m| < M/N (first null of the
+    zero-delay row of a unit-modulus code).  A box size of -1 excludes nothing."""
+    if m_ml is None:
+        m_ml = max(M // N - 1, 0)
+    return (-(N - 1), N - 1, -(M // 2), M - 1 - M // 2, k_ml, m_ml)
+
+
+def signal_from_phase(phi) -> np.ndarray:
+    phi = np.ascontiguousarray(np.asarray(phi, dtype=np.float64))
+    out = np.empty(phi.shape[0], dtype=np.complex128)
+    _load().orc_signal_from_phase(_ptr(phi), phi.shape[0], _ptr(out.view(np.float64)))
+    return out
+
+
+def energy(s) -> float:
+    s, sv = _s_buf(s)
+    return float(_load().orc_energy(_ptr(sv), s.shape[0]))
+
+
+def af_complex(s, M, k_lo, k_hi, m_lo, m_hi, nthreads=None) -> np.ndarray:
+    """X[k,m] over the window, shape (k_hi-k_lo+1, m_hi-m_lo+1), complex128."""
+    s, sv = _s_buf(s)
+    X = np.empty((k_hi - k_lo + 1, m_hi - m_lo + 1), dtype=np.complex128)
+    st = _load().orc_af_complex(_ptr(sv), s.shape[0], M, k_lo, k_hi, m_lo, m_hi,
+                                _ptr(X.view(np.float64)), _threads(nthreads))
+    _check(st, "af_complex")
+    return X
+
+
+def af_ahat(s, M, k_lo, k_hi, m_lo, m_hi, eps, nthreads=None) -> np.ndarray:
+    """Energy-normalised, eps-stabilised |X| over the window (float64)."""
+    s, sv = _s_buf(s)
+    A = np.empty((k_hi - k_lo + 1, m_hi - m_lo + 1), dtype=np.float64)
+    st = _load().orc_af_ahat(_ptr(sv), s.shape[0], M, k_lo, k_hi, m_lo, m_hi, float(eps),
+                             _ptr(A), _threads(nthreads))
+    _check(st, "af_ahat")
+    return A
+
+
+def af_cells(s, M, ks, ms, eps) -> np.ndarray:
+    """Ahat at the listed (k, m) cells, each computed by its own direct sum."""
+    s, sv = _s_buf(s)
+    ks = np.ascontiguousarray(np.asarray(ks, dtype=np.int64))
+    ms = np.ascontiguousarray(np.asarray(ms, dtype=np.int64))
+    out = np.empty(ks.shape[0], dtype=np.float64)
+    st = _load().orc_af_cells(_ptr(sv), s.shape[0], M, ks.shape[0], ks.ctypes.data_as(_ip),
+                              ms.ctypes.data_as(_ip), float(eps), _ptr(out))
+    _check(st, "af_cells")
+    return out
+
+
+def _win(window):
+    w = np.ascontiguousarray(np.asarray(window, dtype=np.int64))
+    assert w.shape == (6,)
+    return w
+
+
+def loss(s, M, window, w_psl=1.0, w_isl=1.0, beta=50.0, eps=1e-12, nthreads=None) -> np.ndarray:
+    s, sv = _s_buf(s)
+    w = _win(window)
+    out = np.zeros(8, dtype=np.float64)
+    st = _load().orc_loss(_ptr(sv), s.shape[0], M, w.ctypes.data_as(_ip), w_psl, w_isl, beta, eps,
+                          _ptr(out), _threads(nthreads))
+    _check(st, "loss")
+    return out
+
+
+def grad(s, M, window, w_psl=1.0, w_isl=1.0, beta=50.0, eps=1e-12, nthreads=None):
+    """Returns (grad_s complex128 = dL/dRe s + j dL/dIm s,
+    grad_phi float64 = dL/dphi for s = exp(j phi), out8)."""
+    s, sv = _s_buf(s)
+    w = _win(window)
+    N = s.shape[0]
+    gs = np.zeros(N, dtype=np.complex128)
+    gp = np.zeros(N, dtype=np.float64)
+    out = np.zeros(8, dtype=np.float64)
+    st = _load().orc_grad(_ptr(sv), N, M, w.ctypes.data_as(_ip), w_psl, w_isl, beta, eps,
+                          _ptr(gs.view(np.float64)), _ptr(gp), _ptr(out), _threads(nthreads))
+    _check(st, "grad")
+    return gs, gp, out
+
+
+def fd_grad_phi(phi, M, window, w_psl=1.0, w_isl=1.0, beta=50.0, eps=1e-12, h=1e-6,
+                nthreads=None) -> np.ndarray:
+    phi = np.ascontiguousarray(np.asarray(phi, dtype=np.float64))
+    w = _win(window)
+    out = np.zeros(phi.shape[0], dtype=np.float64)
+    st = _load().orc_fd_grad_phi(_ptr(phi), phi.shape[0], M, w.ctypes.data_as(_ip), w_psl, w_isl,
+                                 beta, eps, h, _ptr(out), _threads(nthreads))
+    _check(st, "fd_grad_phi")
+    return out
+
+
+def fd_grad_s(s, M, window, w_psl=1.0, w_isl=1.0, beta=50.0, eps=1e-12, h=1e-6,
+              nthreads=None) -> np.ndarray:
+    s, sv = _s_buf(s)
+    w = _win(window)
+    out = np.zeros(s.shape[0], dtype=np.complex128)
+    st = _load().orc_fd_grad_s(_ptr(sv), s.shape[0], M, w.ctypes.data_as(_ip), w_psl, w_isl, beta,
+                               eps, h, _ptr(out.view(np.float64)), _threads(nthreads))
+    _check(st, "fd_grad_s")
+    return out
