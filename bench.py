@@ -1,0 +1,347 @@
+"""Benchmark: batched ambiguity-function forward + backward on GB300.
+
+Workload: 256 random polyphase codes (phases i.i.d. uniform on [0, 2 pi),
+seeded), N = 1024, M = 2048, all 2047 delays and 2048 Doppler bins, loss
+PSL_soft (log-sum-exp, beta = 50) + ISL over the AF minus the zero-delay
+mainlobe, forward and Wirtinger backward with respect to the phases, FP32.
+One step = graf_af_loss + graf_af_backward over the batch; metric = AF cells
+per second, cells = B (2N-1) M per step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs under torchrun, one rank per GPU, each on its own batch (weak
+scaling, no data-path collective).  Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+B, N, M = 256, 1024, 2048
+BETA, EPS = 50.0, 1e-12
+SEED = 2506229350 + 2
+METRIC = "AF fwd+bwd Gcells/s at N=1024 M=2048"
+UNIT = "Gcells/s"
+WORKLOAD = ("256 random polyphase codes, N=1024, M=2048, all 2047 delays x 2048 Doppler bins, "
+            "PSL(log-sum-exp beta=50)+ISL, forward + Wirtinger backward w.r.t. phases")
+CELLS = B * (2 * N - 1) * M
+FLOP_PER_ROW = 5.0 * M * math.log2(M)          # nominal radix-2 count of one M-point FFT
+ALG_FLOP_BWD = B * (2 * N - 1) * FLOP_PER_ROW  # adjoint DFT of every delay row
+SMS, FP32_LANES = 152, 128
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def _measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2506_22935_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".py")):
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_record():
+    """DRAM bytes per launch of the backward kernel from the committed ncu
+    summary, valid only if the kernel sources are unchanged since."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        rec = json.load(f)
+    if rec.get("source_hash") != _kernel_hash():
+        return None
+    return rec.get("af_backward_bytes_per_launch_full_batch")
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling while the GPU is under load."""
+    FIELDS = ("clocks.sm,clocks.max.sm,utilization.gpu,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.index)], stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [c.strip() for c in r]
+            if len(r) < 9:
+                continue
+            try:
+                clk, cmax, util = float(r[0]), float(r[1]), float(r[2])
+            except ValueError:
+                continue
+            mx = cmax
+            if util < 50:
+                continue
+            sm.append(clk)
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples_under_load": len(sm)}
+
+
+def _oracle_cols(cols, nthreads=None):
+    """FP64 oracle loss + gradient (forward + backward) of ONE waveform of the
+    workload over all 2047 delays and `cols` Doppler bins centred on m = 0
+    (cols = M is the whole AF).  Every cell costs the same O(N - |k|) in the
+    forward and O(1) per (k, n) in the adjoint, so a Doppler slice is a
+    representative sample.  Returns (cells, seconds, cores)."""
+    import numpy as np
+
+    import oracle
+    from paper_2506_22935_gb300 import inputs
+    phi = inputs.random_phases(SEED, 1, N)[0].astype(np.float64)
+    s = oracle.signal_from_phase(phi)
+    m_lo = -(cols // 2)
+    win = (-(N - 1), N - 1, m_lo, m_lo + cols - 1, 0, max(M // N - 1, 0))
+    cores = nthreads or os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.grad(s, M, win, 1.0, 1.0, BETA, EPS, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return (2 * N - 1) * cols, dt, cores
+
+
+def _oracle_budget_cols(seconds):
+    """Doppler bins of one waveform the oracle processes in about `seconds`."""
+    _, dt, _ = _oracle_cols(8)
+    cols = int(8 * seconds / max(dt, 1e-6))
+    return max(1, min(M, cols))
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return
+    budget = min(30.0, 150.0 / (args.steps + args.warmup))
+    cols = _oracle_budget_cols(budget)
+    for _ in range(args.warmup):
+        _oracle_cols(cols)
+    times, cells, cores = [], 0, 1
+    for _ in range(args.steps):
+        c, dt, cores = _oracle_cols(cols)
+        times.append(dt)
+        cells = c
+    v = cells / statistics.mean(times) / 1e9
+    sample = (f"per step: all 2047 delays x {cols} of {M} Doppler bins of 1 of {B} waveforms "
+              f"(N={N}), FP64 loss + gradient")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD + " (FP64 oracle, bounded sample per step)",
+                                            "B": B, "N": N, "M": M},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_graf(args):
+    import torch
+
+    from paper_2506_22935_gb300 import graf as g
+    from paper_2506_22935_gb300 import inputs
+
+    rank, world, local = _env_rank()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    g.load()
+
+    phi_h = inputs.random_phases(SEED + 1000 * rank, B, N)
+    x = torch.from_numpy(phi_h).to(dev)
+    w, loss = g.Window.full(N, M), g.Loss(1.0, 1.0, BETA, EPS)
+    wc, lc = w.c(), loss.c()
+    nb = g.graf_af_backward_workspace_bytes(B, N, M, wc)
+    ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+    out8 = torch.empty((B, 8), dtype=torch.float32, device=dev)
+    grad = torch.empty((B, N), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 126 MB L2
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+
+    def loss_call(xp, o8p):
+        st = g.graf_af_loss(xp, g.GRAF_IN_PHASE, B, N, M, wc, lc, o8p, ws.data_ptr(), nb, sp)
+        assert st == 0, g.graf_status_string(st)
+
+    def bwd_call(xp, o8p, gp):
+        st = g.graf_af_backward(xp, g.GRAF_IN_PHASE, B, N, M, wc, lc, o8p, None, None, gp, ws.data_ptr(),
+                                nb, sp)
+        assert st == 0, g.graf_status_string(st)
+
+    launches_per_step = 4  # loss rows, loss finalize, backward rows, gradient reduce
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    with ClockSampler(dev.index) as clk:
+        for _ in range(args.warmup):
+            loss_call(x.data_ptr(), out8.data_ptr())
+            bwd_call(x.data_ptr(), out8.data_ptr(), grad.data_ptr())
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        for i in range(args.steps):
+            flush.zero_()
+            e0, e1, e2 = ev[i]
+            e0.record(stream)
+            loss_call(x.data_ptr(), out8.data_ptr())
+            e1.record(stream)
+            bwd_call(x.data_ptr(), out8.data_ptr(), grad.data_ptr())
+            e2.record(stream)
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+    step_ms = sum(e0.elapsed_time(e2) for e0, _, e2 in ev)
+    bwd_ms = sum(e1.elapsed_time(e2) for _, e1, e2 in ev) / args.steps
+    loss_ms = sum(e0.elapsed_time(e1) for e0, e1, _ in ev) / args.steps
+    t = torch.tensor([step_ms], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    step_ms = t.item()
+    ms_per_step = step_ms / args.steps
+    value = world * CELLS * args.steps / (step_ms / 1e3) / 1e9
+    assert torch.isfinite(out8).all() and torch.isfinite(grad).all()
+
+    # end to end: pinned host phases in, loss scalars and gradient out, per step
+    xh = torch.from_numpy(phi_h).pin_memory()
+    o8h = torch.empty((B, 8), dtype=torch.float32).pin_memory()
+    gh = torch.empty((B, N), dtype=torch.float32).pin_memory()
+    xd = torch.empty_like(x)
+    for _ in range(2):
+        xd.copy_(xh, non_blocking=True)
+        loss_call(xd.data_ptr(), out8.data_ptr())
+        bwd_call(xd.data_ptr(), out8.data_ptr(), grad.data_ptr())
+        o8h.copy_(out8, non_blocking=True)
+        gh.copy_(grad, non_blocking=True)
+    torch.cuda.synchronize(dev)
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        xd.copy_(xh, non_blocking=True)
+        loss_call(xd.data_ptr(), out8.data_ptr())
+        bwd_call(xd.data_ptr(), out8.data_ptr(), grad.data_ptr())
+        o8h.copy_(out8, non_blocking=True)
+        gh.copy_(grad, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e2e_ms += a.elapsed_time(b)
+    t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = world * CELLS * args.steps / (t.item() / 1e3) / 1e9
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    peaks, src = _measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    achieved = ALG_FLOP_BWD / (bwd_ms / 1e3) / 1e12
+    executed_bwd = B * N * 2 * FLOP_PER_ROW
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": _traffic_record(),
+                "kernel": "af_backward_kernel<2048> (+ gradient reduce)",
+                "peak_source": f"FP32 FMA peak = {SMS} SMs x {FP32_LANES} lanes x 2 x {sm_max:.0f} MHz "
+                               f"(sm_max_mhz from MEASURED_PEAKS.json, {src})",
+                "algorithmic_flop_per_launch": ALG_FLOP_BWD,
+                "executed_flop_per_launch": executed_bwd,
+                "executed_frac": executed_bwd / (bwd_ms / 1e3) / 1e12 / peak_tflops,
+                "loss_kernel_ms": loss_ms, "backward_kernel_ms": bwd_ms}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cols = _oracle_budget_cols(15.0)
+        cells, dt, cores = _oracle_cols(cols)
+        cpu = {"value": cells / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"all 2047 delays x {cols} of {M} Doppler bins of 1 of {B} waveforms (N={N}), "
+                         f"FP64 loss + gradient, {dt:.1f} s on {cores} threads"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "B_per_gpu": B, "N": N, "M": M, "beta": BETA, "eps": EPS,
+                       "seed": SEED, "l2": "flushed between steps (256 MB write, outside the timed events)"},
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B * N * 4,
+                    "d2h_bytes_per_step": B * 8 * 4 + B * N * 4},
+            "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="graf", choices=["graf", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_graf(args)
+
+
+if __name__ == "__main__":
+    main()

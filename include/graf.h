@@ -1,0 +1,170 @@
+/*
+ * graf.h - C ABI of the GB300 (sm_103a) differentiable ambiguity-function
+ * library: the discrete ambiguity function (AF) of a complex waveform, its
+ * fused sidelobe losses and their Wirtinger-calculus gradient.
+ *
+ * Method (Bara et al., "GRAF: differentiable radar ambiguity functions"):
+ *   lag product   R[k,n] = s[n] conj(s[n-k])                        Sec. 4.1, Eq. 8
+ *                 aperiodic: s[n] = 0 outside [0,N), k = -(N-1)..N-1 (the
+ *                 non-periodic extension listed in Sec. 8.5)
+ *   row DFT       X[k,m] = sum_n R[k,n] exp(-2 pi j m n / M)          Sec. 4.1, Eq. 11
+ *                 M-point (zero padded), m in [-M/2, M/2-1]         Algorithm 1 step 5
+ *   magnitude     Ahat[k,m] = sqrt(|X[k,m]|^2 + eps) / E,           Eq. 12, Eq. 17
+ *                 E = sum_n |s[n]|^2 (= max |X| = |X[0,0]|)
+ *   losses on the sidelobe region Omega (Eqs. 18, 19, 22):
+ *                 ISL = sum_Omega Ahat^2,  PSL_hard = max_Omega Ahat^2,
+ *                 PSL_soft = (1/beta) log sum_Omega exp(beta Ahat^2),
+ *                 L = w_psl PSL_soft + w_isl ISL
+ *   gradient      Wirtinger calculus, Sec. 3.3 Eq. 6 and Sec. 4.2 Eqs. 13-15:
+ *                 grad_s = 2 dL/ds* = dL/dRe(s) + j dL/dIm(s) (PyTorch's
+ *                 convention) and, for s = exp(j phi), grad_phi = dL/dphi.
+ *
+ * Conventions for every entry point:
+ *   - All array arguments are DEVICE pointers (cudaMalloc'd or torch CUDA
+ *     memory) owned by the caller, unless a comment says "host".  Nothing is
+ *     allocated, freed or synchronised inside the compute calls: they only
+ *     enqueue kernels on `stream` (a cudaStream_t passed as void*; NULL is the
+ *     legacy default stream) and return.
+ *   - Batches are B waveforms of equal length N stored contiguously:
+ *     GRAF_IN_COMPLEX: graf_c32 x[B][N] (interleaved re, im; complex64);
+ *     GRAF_IN_PHASE:   float   x[B][N] phases phi, s[n] = exp(j phi[n]).
+ *   - Constraints: 1 <= B <= 2^20, 1 <= N <= M, M a power of two in
+ *     [GRAF_M_MIN, GRAF_M_MAX], window inside k in [-(N-1), N-1] and
+ *     m in [-M/2, M/2-1] with lo <= hi, mainlobe box sizes >= -1, eps >= 0,
+ *     beta > 0.  A violated constraint returns GRAF_ERR_INVALID_ARG before
+ *     anything is enqueued.  A kernel launch error returns GRAF_ERR_CUDA.
+ *   - Results are deterministic: every reduction runs in a fixed order.
+ */
+#ifndef GRAF_H
+#define GRAF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define GRAF_API __attribute__((visibility("default")))
+#else
+#define GRAF_API
+#endif
+
+#define GRAF_VERSION 1
+#define GRAF_M_MIN 8
+#define GRAF_M_MAX 16384
+#define GRAF_LOSS_OUT 8 /* floats per waveform in out8 / saved8 */
+
+typedef enum {
+    GRAF_OK = 0,
+    GRAF_ERR_INVALID_ARG = 1,
+    GRAF_ERR_UNSUPPORTED = 2,
+    GRAF_ERR_NOMEM = 3,
+    GRAF_ERR_CUDA = 4,
+    GRAF_ERR_TIMEOUT = 5,
+    GRAF_ERR_DEVICE_FLAG = 6,
+    GRAF_ERR_WORKSPACE = 7
+} graf_status_t;
+
+/* complex64, interleaved; layout-compatible with float2 and torch.complex64 */
+typedef struct {
+    float re, im;
+} graf_c32;
+
+/* Delay/Doppler window (inclusive bounds, Doppler in fftshift order) and the
+ * mainlobe box |k| <= k_ml && |m| <= m_ml that the losses exclude; the
+ * sidelobe region is Omega = window minus box (Eq. 18: "the sidelobe region
+ * excluding the mainlobe").  A box size of -1 excludes nothing. */
+typedef struct {
+    int32_t k_lo, k_hi;
+    int32_t m_lo, m_hi;
+    int32_t k_ml, m_ml;
+} graf_window_t;
+
+/* Composite loss weights (Eq. 22, lambda_2 = w_psl, lambda_3 = w_isl), the
+ * soft-max temperature beta of PSL_soft and the magnitude stabiliser eps. */
+typedef struct {
+    float w_psl, w_isl, beta, eps;
+} graf_loss_t;
+
+typedef enum { GRAF_IN_COMPLEX = 0, GRAF_IN_PHASE = 1 } graf_input_t;
+
+/* Human-readable name of a status code (static string, never NULL). */
+GRAF_API const char* graf_status_string(graf_status_t status);
+
+/* GRAF_VERSION of the loaded library. */
+GRAF_API int32_t graf_version(void);
+
+/*
+ * graf_af_forward - the energy-normalised AF over a window (Algorithm 1 with
+ * the aperiodic lag, Eqs. 8, 11, 12, 17).
+ *   x       [B][N] signal (see graf_input_t)
+ *   w       window; k_ml / m_ml are ignored here
+ *   eps     magnitude stabiliser (>= 0)
+ *   af_out  float [B][k_hi-k_lo+1][m_hi-m_lo+1], row = delay k ascending,
+ *           column = Doppler m ascending (fftshift order): Ahat[k,m].
+ * Every cell of the window is written.
+ */
+GRAF_API graf_status_t graf_af_forward(const void* x, graf_input_t kind, int32_t B, int32_t N,
+                              int32_t M, graf_window_t w, float eps, float* af_out,
+                              void* stream);
+
+/*
+ * Workspace (device bytes, 256-byte aligned) that graf_af_loss needs for the
+ * given shape; 0 only if the arguments are invalid.
+ */
+GRAF_API size_t graf_af_loss_workspace_bytes(int32_t B, int32_t N, int32_t M, graf_window_t w);
+
+/*
+ * graf_af_loss - fused sidelobe losses (Eqs. 18, 19, 22) without writing the
+ * AF to memory.
+ *   out8  float [B][GRAF_LOSS_OUT]: per waveform
+ *         {L, PSL_soft, ISL, PSL_hard, E, |Omega|, S_p, 0}
+ *         where S_p = sum_Omega p Ahat^2, p = exp(beta (Ahat^2 - PSL_soft)),
+ *         the softmax-weighted term the energy gradient needs.  If Omega is
+ *         empty, L = PSL_soft = ISL = PSL_hard = S_p = 0.
+ *   workspace  caller-owned scratch of graf_af_loss_workspace_bytes();
+ *         too small -> GRAF_ERR_WORKSPACE.  Its contents are overwritten.
+ */
+GRAF_API graf_status_t graf_af_loss(const void* x, graf_input_t kind, int32_t B, int32_t N, int32_t M,
+                           graf_window_t w, graf_loss_t l, float* out8, void* workspace,
+                           size_t workspace_bytes, void* stream);
+
+/* Workspace bytes for graf_af_backward (and for graf_af_loss_backward). */
+GRAF_API size_t graf_af_backward_workspace_bytes(int32_t B, int32_t N, int32_t M, graf_window_t w);
+
+/*
+ * graf_af_backward - gradient of L (as defined for graf_af_loss) with respect
+ * to the input, by the Wirtinger chain rule of Sec. 4.2 (Eqs. 13-15): cell
+ * adjoint dL/dX* = (dL/dAhat^2) X / E^2, the row adjoint of the DFT (an
+ * unnormalised inverse DFT), the product rule on R[k,n] = s[n] conj(s[n-k])
+ * for both factors, and the energy term dL/dE * s.  The AF rows are
+ * recomputed, never stored.
+ *   saved8   [B][GRAF_LOSS_OUT] from graf_af_loss on the SAME x, window and
+ *            loss (PSL_soft, ISL and S_p are used)
+ *   dL       float [B] upstream gradient dOut/dL per waveform, or NULL for 1
+ *   grad_s   graf_c32 [B][N] = dL * (dL/dRe s + j dL/dIm s), or NULL
+ *   grad_phi float [B][N] = dL * dL/dphi, or NULL; requires GRAF_IN_PHASE
+ * At least one of grad_s / grad_phi must be non-NULL.
+ */
+GRAF_API graf_status_t graf_af_backward(const void* x, graf_input_t kind, int32_t B, int32_t N,
+                               int32_t M, graf_window_t w, graf_loss_t l, const float* saved8,
+                               const float* dL, graf_c32* grad_s, float* grad_phi,
+                               void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * graf_af_loss_backward - one forward+backward step: graf_af_loss into out8,
+ * then graf_af_backward with saved8 = out8, in stream order.  Same arguments
+ * and workspace as graf_af_backward.
+ */
+GRAF_API graf_status_t graf_af_loss_backward(const void* x, graf_input_t kind, int32_t B, int32_t N,
+                                    int32_t M, graf_window_t w, graf_loss_t l, float* out8,
+                                    const float* dL, graf_c32* grad_s, float* grad_phi,
+                                    void* workspace, size_t workspace_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRAF_H */

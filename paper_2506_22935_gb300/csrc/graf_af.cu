@@ -1,0 +1,293 @@
+// graf_af.cu - reductions that follow the row kernels (loss finalisation,
+// gradient reduction) and the dispatch over the row length M.
+#include <math_constants.h>
+
+#include "graf_kernels.cuh"
+
+namespace graf {
+
+// |Omega| = |window| - |window intersect mainlobe box|, exact in int64.
+__device__ __forceinline__ long long omega_count(const AfParams& p) {
+    const long long nk = p.k_hi - p.k_lo + 1, nm = p.m_hi - p.m_lo + 1;
+    long long bk = 0, bm = 0;
+    if (p.k_ml >= 0 && p.m_ml >= 0) {
+        const int kl = max(p.k_lo, -p.k_ml), kh = min(p.k_hi, p.k_ml);
+        const int ml = max(p.m_lo, -p.m_ml), mh = min(p.m_hi, p.m_ml);
+        bk = kh >= kl ? kh - kl + 1 : 0;
+        bm = mh >= ml ? mh - ml + 1 : 0;
+    }
+    return nk * nm - bk * bm;
+}
+
+// One warp per waveform: merge the tile records in a fixed order (double).
+__global__ void loss_finalize_kernel(AfParams p, float* out8) {
+    const int b = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (b >= p.B) return;
+    const double beta = p.beta;
+    double isl = 0.0, mx = -CUDART_INF, z = 0.0, T = 0.0;
+    for (int i = lane; i < p.tiles; i += 32) {
+        const float4 r = p.rec[(size_t)b * p.tiles + i];
+        isl += r.x;
+        if (r.y > -CUDART_INF_F) {
+            const double m2 = r.y;
+            if (m2 > mx) {
+                const double f = exp(beta * (mx - m2));
+                z = z * f + r.z;
+                T = T * f + r.w;
+                mx = m2;
+            } else {
+                const double f = exp(beta * (m2 - mx));
+                z += r.z * f;
+                T += r.w * f;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double i2 = __shfl_xor_sync(0xffffffffu, isl, o);
+        const double m2 = __shfl_xor_sync(0xffffffffu, mx, o);
+        const double z2 = __shfl_xor_sync(0xffffffffu, z, o);
+        const double t2 = __shfl_xor_sync(0xffffffffu, T, o);
+        isl += i2;
+        if (m2 > mx) {
+            const double f = exp(beta * (mx - m2));
+            z = z * f + z2;
+            T = T * f + t2;
+            mx = m2;
+        } else if (m2 > -CUDART_INF) {
+            const double f = exp(beta * (m2 - mx));
+            z += z2 * f;
+            T += t2 * f;
+        }
+    }
+    if (lane == 0) {
+        float* o = out8 + (size_t)b * 8;
+        const double cnt = (double)omega_count(p);
+        if (mx == -CUDART_INF || z <= 0.0) {
+            o[0] = 0.0f; o[1] = 0.0f; o[2] = 0.0f; o[3] = 0.0f; o[6] = 0.0f;
+        } else {
+            const double psl_soft = mx + log(z) / beta;
+            o[0] = (float)(p.w_psl * psl_soft + p.w_isl * isl);
+            o[1] = (float)psl_soft;
+            o[2] = (float)isl;
+            o[3] = (float)mx;
+            o[6] = (float)(T / z);
+        }
+        o[5] = (float)cnt;
+        o[7] = 0.0f;
+    }
+}
+
+__device__ __forceinline__ float2 signal_at(const AfParams& p, int b, int n) {
+    if (p.kind == 1) {
+        float sn, cs;
+        sincosf(static_cast<const float*>(p.x)[(size_t)b * p.N + n], &sn, &cs);
+        return make_float2(cs, sn);
+    }
+    return static_cast<const float2*>(p.x)[(size_t)b * p.N + n];
+}
+
+// Base weight of transformed row k (see the backward kernel): every Doppler
+// bin of rows k and -k that lies in the window, when the window spans all bins.
+__device__ __forceinline__ int base_weight(const AfParams& p, int k) {
+    if (!p.full_m) return 0;
+    return ((k >= p.k_lo && k <= p.k_hi) ? 1 : 0) + ((k > 0 && -k >= p.k_lo && -k <= p.k_hi) ? 1 : 0);
+}
+
+// dL/ds* of the FFT part = sum over tiles (fixed order).  grad_phi =
+// 2 Im(dL/ds* conj(s)): the row-uniform part and the energy terms are s[n]
+// times real numbers and contribute nothing to it.
+__global__ void grad_phi_kernel(AfParams p, const float* dL, float* grad_phi) {
+    const int nblk = (p.N + blockDim.x - 1) / blockDim.x;
+    const int b = blockIdx.x / nblk;
+    const int n = (blockIdx.x % nblk) * blockDim.x + threadIdx.x;
+    if (n >= p.N) return;
+    const float2* gp = p.gpart + (size_t)b * p.tiles * p.N + n;
+    float2 g = gp[0];
+    for (int i = 1; i < p.tiles; ++i) g = cadd(g, gp[(size_t)i * p.N]);
+    const float2 s = signal_at(p, b, n);
+    const float scale = 2.0f * (dL ? dL[b] : 1.0f);
+    grad_phi[(size_t)b * p.N + n] = scale * (g.y * s.x - g.x * s.y);
+}
+
+// Per waveform, in FP64: U = sum_k w_b(k) (C[k] + eps) over the transformed
+// rows, C[k] = sum_n |s[n]|^2 |s[n-k]|^2 (Parseval: sum_m |X[k,m]|^2 = M C[k]).
+__global__ void uniform_sum_kernel(AfParams p) {
+    extern __shared__ double a_sm[];
+    __shared__ double red[32];
+    const int b = blockIdx.x;
+    for (int n = threadIdx.x; n < p.N; n += blockDim.x) {
+        const float2 s = signal_at(p, b, n);
+        a_sm[n] = (double)s.x * s.x + (double)s.y * s.y;
+    }
+    __syncthreads();
+    double acc = 0.0;
+    for (int k = p.r_lo + threadIdx.x; k <= p.r_hi; k += blockDim.x) {
+        const int wb = base_weight(p, k);
+        if (wb == 0) continue;
+        double c = 0.0;
+        for (int n = k; n < p.N; ++n) c += a_sm[n] * a_sm[n - k];
+        acc += wb * (c + (double)p.eps);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) s += red[w];
+        p.usum[b] = s;
+    }
+}
+
+// grad_s = 2 dL [g_fft + dLdE_fft s + g_u], with (all FP64 after the sums)
+//   dLdE_fft = -2 E sum_tiles csum           (energy term of the FFT part)
+//   g_u[n]   = A' M s[n] ( sum_k w_b(k)(|s[n-k]|^2 [n>=k] + |s[n+k]|^2 [n+k<N]) / E^2
+//                          - 2 U / E^3 )    (row-uniform part in closed form)
+// with A' = w_isl + w_psl p0, p0 = exp(-beta PSL_soft) evaluated exactly as in
+// the backward kernel.  grad_phi, if requested, uses g_fft alone.
+__global__ void grad_s_kernel(AfParams p, const float* dL, float2* grad_s, float* grad_phi) {
+    extern __shared__ double a_sm[];
+    const int nblk = (p.N + blockDim.x - 1) / blockDim.x;
+    const int b = blockIdx.x / nblk;
+    const int n0 = (blockIdx.x % nblk) * blockDim.x;
+    for (int n = threadIdx.x; n < p.N; n += blockDim.x) {
+        const float2 s = signal_at(p, b, n);
+        a_sm[n] = (double)s.x * s.x + (double)s.y * s.y;
+    }
+    __syncthreads();
+    const int n = n0 + threadIdx.x;
+    if (n >= p.N) return;
+    const float2* gp = p.gpart + (size_t)b * p.tiles * p.N + n;
+    float2 g = gp[0];
+    for (int i = 1; i < p.tiles; ++i) g = cadd(g, gp[(size_t)i * p.N]);
+    double cs = 0.0;
+    for (int i = 0; i < p.tiles; ++i) cs += p.csum[(size_t)b * p.tiles + i];
+    const float2 s = signal_at(p, b, n);
+    const float* sv = p.saved8 + (size_t)b * 8;
+    const double E = sv[4];
+    const float bl2 = p.beta * 1.4426950408889634f;
+    const float p0 = exp2f(-(sv[1] * bl2));
+    const double Ap = (double)fmaf(p.w_psl, p0, p.w_isl);
+    double corr = 0.0;
+    for (int k = p.r_lo; k <= p.r_hi; ++k) {
+        const int wb = base_weight(p, k);
+        if (wb == 0) continue;
+        double t = 0.0;
+        if (n >= k) t += a_sm[n - k];
+        if (n + k < p.N) t += a_sm[n + k];
+        corr += wb * t;
+    }
+    const double gu = Ap * (double)p.M * (corr / (E * E) - 2.0 * p.usum[b] / (E * E * E));
+    const double coef = -2.0 * E * cs + gu;  // real multiplier of s[n]
+    const double scale = 2.0 * (dL ? (double)dL[b] : 1.0);
+    grad_s[(size_t)b * p.N + n] = make_float2((float)(scale * (g.x + coef * s.x)),
+                                              (float)(scale * (g.y + coef * s.y)));
+    if (grad_phi) grad_phi[(size_t)b * p.N + n] = (float)(scale * ((double)g.y * s.x - (double)g.x * s.y));
+}
+
+#define GRAF_DISPATCH_M(FN, M, ...)                      \
+    switch (M) {                                         \
+        case 8: return FN<8>(__VA_ARGS__);               \
+        case 16: return FN<16>(__VA_ARGS__);             \
+        case 32: return FN<32>(__VA_ARGS__);             \
+        case 64: return FN<64>(__VA_ARGS__);             \
+        case 128: return FN<128>(__VA_ARGS__);           \
+        case 256: return FN<256>(__VA_ARGS__);           \
+        case 512: return FN<512>(__VA_ARGS__);           \
+        case 1024: return FN<1024>(__VA_ARGS__);         \
+        case 2048: return FN<2048>(__VA_ARGS__);         \
+        case 4096: return FN<4096>(__VA_ARGS__);         \
+        case 8192: return FN<8192>(__VA_ARGS__);         \
+        case 16384: return FN<16384>(__VA_ARGS__);       \
+        default: return cudaErrorInvalidValue;           \
+    }
+
+template <int M>
+static size_t smem_need_m(int N, int which) {
+    return which == 2 ? backward_smem<M>(N) : forward_smem<M>(N);
+}
+static size_t smem_need(int M, int N, int which) {
+    switch (M) {
+        case 8: return smem_need_m<8>(N, which);
+        case 16: return smem_need_m<16>(N, which);
+        case 32: return smem_need_m<32>(N, which);
+        case 64: return smem_need_m<64>(N, which);
+        case 128: return smem_need_m<128>(N, which);
+        case 256: return smem_need_m<256>(N, which);
+        case 512: return smem_need_m<512>(N, which);
+        case 1024: return smem_need_m<1024>(N, which);
+        case 2048: return smem_need_m<2048>(N, which);
+        case 4096: return smem_need_m<4096>(N, which);
+        case 8192: return smem_need_m<8192>(N, which);
+        case 16384: return smem_need_m<16384>(N, which);
+        default: return (size_t)-1;
+    }
+}
+
+size_t row_kernel_smem(int M, int N, int which) { return smem_need(M, N, which); }
+
+cudaError_t run_forward(const AfParams& p, cudaStream_t st) { GRAF_DISPATCH_M(run_forward_m, p.M, p, st) }
+cudaError_t run_loss(const AfParams& p, cudaStream_t st) {
+    cudaError_t e;
+    switch (p.M) {
+        case 8: e = run_loss_m<8>(p, st); break;
+        case 16: e = run_loss_m<16>(p, st); break;
+        case 32: e = run_loss_m<32>(p, st); break;
+        case 64: e = run_loss_m<64>(p, st); break;
+        case 128: e = run_loss_m<128>(p, st); break;
+        case 256: e = run_loss_m<256>(p, st); break;
+        case 512: e = run_loss_m<512>(p, st); break;
+        case 1024: e = run_loss_m<1024>(p, st); break;
+        case 2048: e = run_loss_m<2048>(p, st); break;
+        case 4096: e = run_loss_m<4096>(p, st); break;
+        case 8192: e = run_loss_m<8192>(p, st); break;
+        case 16384: e = run_loss_m<16384>(p, st); break;
+        default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    const int wpb = 4;
+    loss_finalize_kernel<<<(p.B + wpb - 1) / wpb, 32 * wpb, 0, st>>>(p, p.out8);
+    return cudaGetLastError();
+}
+cudaError_t run_backward(const AfParams& p, const float* dL, float2* grad_s, float* grad_phi,
+                         cudaStream_t st) {
+    cudaError_t e;
+    switch (p.M) {
+        case 8: e = run_backward_m<8>(p, st); break;
+        case 16: e = run_backward_m<16>(p, st); break;
+        case 32: e = run_backward_m<32>(p, st); break;
+        case 64: e = run_backward_m<64>(p, st); break;
+        case 128: e = run_backward_m<128>(p, st); break;
+        case 256: e = run_backward_m<256>(p, st); break;
+        case 512: e = run_backward_m<512>(p, st); break;
+        case 1024: e = run_backward_m<1024>(p, st); break;
+        case 2048: e = run_backward_m<2048>(p, st); break;
+        case 4096: e = run_backward_m<4096>(p, st); break;
+        case 8192: e = run_backward_m<8192>(p, st); break;
+        case 16384: e = run_backward_m<16384>(p, st); break;
+        default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    const long long grid = (long long)((p.N + 255) / 256) * p.B;
+    if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    if (!grad_s) {
+        grad_phi_kernel<<<(unsigned)grid, 256, 0, st>>>(p, dL, grad_phi);
+        return cudaGetLastError();
+    }
+    const size_t sm = (size_t)p.N * sizeof(double);
+    if (sm > 48 * 1024) {
+        e = cudaFuncSetAttribute(uniform_sum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(grad_s_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    uniform_sum_kernel<<<p.B, 256, sm, st>>>(p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    grad_s_kernel<<<(unsigned)grid, 256, sm, st>>>(p, dL, grad_s, grad_phi);
+    return cudaGetLastError();
+}
+
+}  // namespace graf

@@ -1,0 +1,370 @@
+// graf_af_impl.cuh - the ambiguity-function row kernels (forward store, fused
+// losses, backward with recomputation) as templates over the row length M;
+// graf_af_m*.cu instantiate them, a few M per translation unit.
+//
+// One CTA = 256 threads = 256/TPR row slots; a CTA owns one waveform b and a
+// tile of consecutive delay rows k >= 0.  Per row a slot builds the aperiodic
+// lag product (Eq. 8) from the waveform in shared memory, transforms it
+// (Eq. 11) with row_fft, and consumes the result in registers.  Rows k < 0
+// are never transformed: |X[-k, m]| = |X[k, -m]|, so row k also serves delay
+// -k with the Doppler axis mirrored (the loss weight of a transformed cell
+// counts both cells, and its adjoint adds both).
+#pragma once
+#include <math_constants.h>
+
+#include "graf_kernels.cuh"
+
+namespace graf {
+
+
+// --------------------------------------------------------------- lag product
+// v[w] = R[k, n] = s[n] conj(s[n - k]) for n = t + TPR w, support k <= n < N
+// (k >= 0), zero elsewhere (Eq. 8, aperiodic).  HALF: N <= M/2, so registers
+// w >= VALS/2 are zero and never touched.
+template <int M, bool HALF>
+__device__ __forceinline__ void build_lag_row(float2* v, const float2* s_sm, int N, int k, int t,
+                                              bool valid) {
+    using P = RowPlan<M>;
+    constexpr int WN = HALF ? P::VALS / 2 : P::VALS;
+    sfor<0, WN>([&](auto w) {
+        const int n = t + P::TPR * decltype(w)::value;
+        float2 r = make_float2(0.0f, 0.0f);
+        // k <= n < N as one unsigned compare that depends on k (not hoistable)
+        if (valid && (unsigned)(n - k) < (unsigned)(N - k)) r = cmulc(s_sm[n], s_sm[n - k]);
+        v[w] = r;
+    });
+    if constexpr (HALF) {
+        sfor<WN, P::VALS>([&](auto w) { v[w] = make_float2(0.0f, 0.0f); });
+    }
+}
+
+// ---------------------------------------------------------- forward (store)
+// Ahat = sqrt(|X|^2 + eps) / E (Eq. 12, Eq. 17) for every window cell of
+// rows k and -k.  Stores are coalesced along m (consecutive threads hold
+// consecutive Doppler bins) and streaming (written once, never re-read here).
+template <int M, bool HALF>
+__global__ void __launch_bounds__(kThreads, 1) af_forward_kernel(AfParams p) {
+    using P = RowPlan<M>;
+    extern __shared__ __align__(256) unsigned char smem[];
+    float2* s_sm = reinterpret_cast<float2*>(smem);
+    float2* bufs = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(p.N));
+    float* red = reinterpret_cast<float*>(smem + smem_signal_bytes<M>(p.N) + row_buffer_bytes<M>());
+
+    const int tid = threadIdx.x, slot = tid / P::TPR, t = tid % P::TPR;
+    const int b = blockIdx.x / p.tiles, tile = blockIdx.x % p.tiles;
+    const float E = load_signal(p, b, s_sm, red);
+    const float invE = 1.0f / E;
+    float2* buf = bufs + (size_t)slot * (P::SPLIT ? P::SMEM_ROW / 2 : P::SMEM_ROW);
+    const ColMasks cm = col_masks<M>(p, t);
+
+    const int ncols = p.m_hi - p.m_lo + 1;
+    const size_t rows_out = (size_t)(p.k_hi - p.k_lo + 1);
+    float* out_b = p.af_out + (size_t)b * rows_out * ncols;
+    const int row0 = p.r_lo + tile * p.rows_per_tile;
+    const int row_end = min(row0 + p.rows_per_tile, p.r_hi + 1);
+    const int iters = (p.rows_per_tile + (kThreads / P::TPR) - 1) / (kThreads / P::TPR);
+
+    float2 v[P::VALS];
+    for (int it = 0; it < iters; ++it) {
+        const int k = row0 + slot + it * (kThreads / P::TPR);
+        const bool valid = k < row_end;
+        build_lag_row<M, HALF>(v, s_sm, p.N, k, t, valid);
+        row_sync<P::TPR>(slot);
+        row_fft<M, false, HALF, false>(v, buf, t, slot);
+        if (valid) {
+            const RowMasks rmk = row_masks(p, cm, k);
+            const bool in_pos = rmk.pos != 0ull, in_neg = rmk.neg != 0ull;
+            // row k at rp[m], row -k at rn[m'] (m' = -m, and -M/2 maps to itself)
+            float* rp = out_b + (in_pos ? (size_t)(k - p.k_lo) * ncols : 0) - p.m_lo + t;
+            float* rn = out_b + (in_neg ? (size_t)(-k - p.k_lo) * ncols : 0) - p.m_lo - t;
+            sfor<0, P::VALS>([&](auto w) {
+                constexpr int W = decltype(w)::value;
+                constexpr int off = P::TPR * W - (W >= P::VALS / 2 ? M : 0);  // m - t
+                const float2 x = v[w];
+                const float a = sqrtf(fmaf(x.x, x.x, fmaf(x.y, x.y, p.eps))) * invE;
+                if (mbit<W>(rmk.pos)) __stcs(rp + off, a);
+                if (mbit<W>(rmk.neg)) {
+                    float* dst = rn - off;
+                    if constexpr (W == P::VALS / 2) {
+                        if (t == 0) dst = rn + t - M / 2;
+                    }
+                    __stcs(dst, a);
+                }
+            });
+        }
+    }
+}
+
+// ---------------------------------------------------------- fused loss
+// Per cell a2 = Ahat^2 = (|X|^2 + eps) / E^2 and weight w in {0,1,2}:
+//   ISL += w a2;  hard max of a2 over weighted cells;
+//   log-sum-exp of beta a2 kept as (running max mx, sum of exp(beta (a2 - mx)))
+//   plus T = sum w exp(beta (a2 - mx)) a2 for the energy gradient.
+// Per CTA one record {ISL, mx, sum, T} -> workspace.
+__device__ __forceinline__ void lse_rescale(float& mx, float& sum, float& T, float new_mx, float bl2) {
+    if (new_mx > mx) {
+        const float f = exp2f((mx - new_mx) * bl2);
+        sum *= f;
+        T *= f;
+        mx = new_mx;
+    }
+}
+
+__device__ __forceinline__ void lse_merge(float& isl, float& mx, float& sum, float& T, float isl2,
+                                          float mx2, float sum2, float T2, float bl2) {
+    isl += isl2;
+    if (mx2 > mx) {
+        const float f = exp2f((mx - mx2) * bl2);
+        sum = sum * f + sum2;
+        T = T * f + T2;
+        mx = mx2;
+    } else if (mx2 > -CUDART_INF_F) {
+        const float f = exp2f((mx2 - mx) * bl2);
+        sum += sum2 * f;
+        T += T2 * f;
+    }
+}
+
+template <int M, bool HALF>
+__global__ void __launch_bounds__(kThreads, 1) af_loss_kernel(AfParams p) {
+    using P = RowPlan<M>;
+    extern __shared__ __align__(256) unsigned char smem[];
+    float2* s_sm = reinterpret_cast<float2*>(smem);
+    float2* bufs = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(p.N));
+    float* red = reinterpret_cast<float*>(smem + smem_signal_bytes<M>(p.N) + row_buffer_bytes<M>());
+
+    const int tid = threadIdx.x, slot = tid / P::TPR, t = tid % P::TPR;
+    const int b = blockIdx.x / p.tiles, tile = blockIdx.x % p.tiles;
+    const float E = load_signal(p, b, s_sm, red);
+    if (tile == 0 && tid == 0) p.out8[(size_t)b * 8 + 4] = E;
+    const float invE2 = 1.0f / (E * E);
+    const float eps_n = p.eps * invE2;
+    const float bl2 = p.beta * 1.4426950408889634f;  // beta * log2(e)
+    float2* buf = bufs + (size_t)slot * (P::SPLIT ? P::SMEM_ROW / 2 : P::SMEM_ROW);
+    const ColMasks cm = col_masks<M>(p, t);
+    constexpr unsigned long long full_mask = P::VALS == 64 ? ~0ull : ((1ull << P::VALS) - 1ull);
+
+    const int row0 = p.r_lo + tile * p.rows_per_tile;
+    const int row_end = min(row0 + p.rows_per_tile, p.r_hi + 1);
+    constexpr int SLOTS = kThreads / P::TPR;
+    const int iters = (p.rows_per_tile + SLOTS - 1) / SLOTS;
+
+    float isl = 0.0f, mx = -CUDART_INF_F, sum = 0.0f, T = 0.0f;
+    float2 v[P::VALS];
+    for (int it = 0; it < iters; ++it) {
+        const int k = row0 + slot + it * SLOTS;
+        const bool valid = k < row_end;
+        build_lag_row<M, HALF>(v, s_sm, p.N, k, t, valid);
+        row_sync<P::TPR>(slot);
+        row_fft<M, false, HALF, false>(v, buf, t, slot);
+        if (!valid) continue;
+        const RowMasks rmk = row_masks(p, cm, k);
+        if ((rmk.one | rmk.two) == 0ull) continue;
+        // a row whose weights are all equal (every Doppler bin in the window,
+        // no mainlobe cell) skips the per-cell mask tests
+        const bool uniform = rmk.one == full_mask && (rmk.two == 0ull || rmk.two == full_mask);
+        const float wrow = rmk.two != 0ull ? 2.0f : 1.0f;
+        // pass 1: a2, ISL, masked max (a2 overwrites v[w].x; v[w].y = weight)
+        float rmx = -CUDART_INF_F, risl = 0.0f;
+        sfor<0, P::VALS>([&](auto w) {
+            const float2 x = v[w];
+            const float a2 = fmaf(fmaf(x.x, x.x, x.y * x.y), invE2, eps_n);
+            const float wt = uniform ? wrow : mweight<decltype(w)::value>(rmk);
+            risl = fmaf(wt, a2, risl);
+            rmx = fmaxf(rmx, wt > 0.0f ? a2 : -CUDART_INF_F);
+            v[w] = make_float2(a2, wt);
+        });
+        if (rmx == -CUDART_INF_F) continue;
+        isl += risl;
+        lse_rescale(mx, sum, T, rmx, bl2);
+        const float sh = mx * bl2;
+        sfor<0, P::VALS>([&](auto w) {
+            const float a2 = v[w].x, wt = v[w].y;
+            const float e = wt * exp2f(fmaf(a2, bl2, -sh));
+            sum += e;
+            T = fmaf(e, a2, T);
+        });
+    }
+    // CTA reduction in a fixed order: warp xor tree, then warps 0..7
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float i2 = __shfl_xor_sync(0xffffffffu, isl, o);
+        const float m2 = __shfl_xor_sync(0xffffffffu, mx, o);
+        const float s2 = __shfl_xor_sync(0xffffffffu, sum, o);
+        const float t2 = __shfl_xor_sync(0xffffffffu, T, o);
+        lse_merge(isl, mx, sum, T, i2, m2, s2, t2, bl2);
+    }
+    float4* wred = reinterpret_cast<float4*>(red);
+    if ((tid & 31) == 0) wred[tid >> 5] = make_float4(isl, mx, sum, T);
+    __syncthreads();
+    if (tid == 0) {
+        float4 a = wred[0];
+        for (int w = 1; w < kThreads / 32; ++w) {
+            const float4 c = wred[w];
+            lse_merge(a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w, bl2);
+        }
+        p.rec[(size_t)b * p.tiles + tile] = a;
+    }
+}
+
+// ---------------------------------------------------------- backward
+// Per row: recompute X, form the cell adjoint, take the adjoint DFT
+// (conjugate twiddles, unnormalised) and scatter both Wirtinger terms of
+// R[k,n] = s[n] conj(s[n-k]) into this slot's accumulator:
+//   acc[n]   += G_R[n] s[n-k]          (through conj(R), which carries s*[n])
+//   acc[n-k] += conj(G_R[n]) s[n]       (through R, which carries s*[n-k])
+// The two scatters run in separate phases so no two threads of a row update
+// one address at once.  Slots then sum in a fixed order into one partial.
+//
+// Cell adjoint.  dL/dAhat^2 = w (w_isl + w_psl p), p = exp(beta (a2 -
+// PSL_soft)), w the cell weight.  With p0 = exp(-beta PSL_soft), A' = w_isl +
+// w_psl p0 and the row's base weight w_b (the weight every Doppler bin of the
+// row has when the window spans all of them, else 0):
+//   dL/dAhat^2 = w_b A'  +  [(w - w_b) A' + w w_psl (p - p0)].
+// The first term is uniform over the row; its adjoint DFT is exactly
+// w_b A' M R[k,n] / E^2 (the adjoint of an M-point DFT applied to the DFT of
+// a row of support <= M is M times the row), whose scatter is s[p] times a
+// real number: it contributes exactly nothing to dL/dphi, and for dL/ds it
+// is added in closed form, in FP64, by grad_uniform_kernel.  Only the second
+// term goes through the FFT, G = c X with c = [...] / E^2.  This keeps the
+// PSL term, whose softmax weights are ~1/|Omega| (2.4e-7 at N=1024, M=2048),
+// from vanishing next to the ISL weight in FP32, and avoids summing the
+// ISL gradient of full rows (zero for unit modulus, by Parseval) from large
+// cancelling parts.  Per CTA the kernel also sums c a2 for the energy term.
+template <int M, bool HALF>
+__global__ void __launch_bounds__(kThreads, 1) af_backward_kernel(AfParams p) {
+    using P = RowPlan<M>;
+    constexpr int SLOTS = kThreads / P::TPR;
+    extern __shared__ __align__(256) unsigned char smem[];
+    float2* s_sm = reinterpret_cast<float2*>(smem);
+    float2* bufs = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(p.N));
+    float2* acc_all = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(p.N) + row_buffer_bytes<M>());
+    float* red = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(acc_all) +
+                                          (((size_t)SLOTS * p.N * sizeof(float2) + 255) & ~(size_t)255));
+
+    const int tid = threadIdx.x, slot = tid / P::TPR, t = tid % P::TPR;
+    const int b = blockIdx.x / p.tiles, tile = blockIdx.x % p.tiles;
+    for (int i = tid; i < SLOTS * p.N; i += kThreads) acc_all[i] = make_float2(0.0f, 0.0f);
+    const float E = load_signal(p, b, s_sm, red);  // includes __syncthreads
+    const float invE2 = 1.0f / (E * E);
+    const float eps_n = p.eps * invE2;
+    const float bl2 = p.beta * 1.4426950408889634f;
+    const float psl_soft = p.saved8[(size_t)b * 8 + 1];
+    const float sh = psl_soft * bl2;
+    const float p0 = exp2f(-sh);
+    const float cA = fmaf(p.w_psl, p0, p.w_isl) * invE2;  // A' / E^2
+    const float cP = p.w_psl * invE2;
+    float csum = 0.0f;
+    float2* buf = bufs + (size_t)slot * (P::SPLIT ? P::SMEM_ROW / 2 : P::SMEM_ROW);
+    const ColMasks cm = col_masks<M>(p, t);
+    constexpr unsigned long long full_mask = P::VALS == 64 ? ~0ull : ((1ull << P::VALS) - 1ull);
+    float2* acc = acc_all + (size_t)slot * p.N;
+
+    const int row0 = p.r_lo + tile * p.rows_per_tile;
+    const int row_end = min(row0 + p.rows_per_tile, p.r_hi + 1);
+    const int iters = (p.rows_per_tile + SLOTS - 1) / SLOTS;
+
+    float2 v[P::VALS];
+    for (int it = 0; it < iters; ++it) {
+        const int k = row0 + slot + it * SLOTS;
+        const bool valid = k < row_end;
+        build_lag_row<M, HALF>(v, s_sm, p.N, k, t, valid);
+        row_sync<P::TPR>(slot);
+        row_fft<M, false, HALF, false>(v, buf, t, slot);
+        const RowMasks rmk = row_masks(p, cm, k);
+        const bool uniform = rmk.one == full_mask && (rmk.two == 0ull || rmk.two == full_mask);
+        const float wrow = valid ? (rmk.two != 0ull ? 2.0f : (rmk.one != 0ull ? 1.0f : 0.0f)) : 0.0f;
+        const int in_pos = (k >= p.k_lo && k <= p.k_hi) ? 1 : 0;
+        const int in_neg = (k > 0 && -k >= p.k_lo && -k <= p.k_hi) ? 1 : 0;
+        const float wb = (valid && p.full_m) ? (float)(in_pos + in_neg) : 0.0f;
+        sfor<0, P::VALS>([&](auto w) {
+            const float2 x = v[w];
+            const float a2 = fmaf(fmaf(x.x, x.x, x.y * x.y), invE2, eps_n);
+            const float wt = (uniform || !valid) ? wrow : mweight<decltype(w)::value>(rmk);
+            const float pr = exp2f(fmaf(a2, bl2, -sh));
+            const float cpsl = wt > 0.0f ? wt * cP * (pr - p0) : 0.0f;
+            const float c = fmaf(wt - wb, cA, cpsl);
+            csum = fmaf(c, a2, csum);
+            v[w] = make_float2(c * x.x, c * x.y);
+        });
+        row_sync<P::TPR>(slot);  // buffer reads of the forward transform are done
+        row_fft<M, true, false, HALF>(v, buf, t, slot);
+        constexpr int WN = HALF ? P::VALS / 2 : P::VALS;
+        if (valid) {
+            // term through conj(R[k,n]): acc[n] += G_R[k,n] s[n-k]
+            sfor<0, WN>([&](auto w) {
+                const int n = t + P::TPR * decltype(w)::value;
+                if ((unsigned)(n - k) < (unsigned)(p.N - k)) {
+                    const float2 a = acc[n];
+                    acc[n] = cadd(a, cmul(v[w], s_sm[n - k]));
+                }
+            });
+        }
+        row_sync<P::TPR>(slot);
+        if (valid) {
+            // term through R[k,n]: acc[n-k] += conj(G_R[k,n]) s[n]
+            sfor<0, WN>([&](auto w) {
+                const int n = t + P::TPR * decltype(w)::value;
+                if ((unsigned)(n - k) < (unsigned)(p.N - k)) {
+                    const float2 a = acc[n - k];
+                    acc[n - k] = cadd(a, cmulc(s_sm[n], v[w]));
+                }
+            });
+        }
+        row_sync<P::TPR>(slot);
+    }
+    // per-CTA sum of c a2 (fixed order: warp xor tree, then warps in order)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) csum += __shfl_xor_sync(0xffffffffu, csum, o);
+    if ((tid & 31) == 0) red[tid >> 5] = csum;
+    __syncthreads();
+    if (tid == 0) {
+        float s = red[0];
+        for (int w = 1; w < kThreads / 32; ++w) s += red[w];
+        p.csum[(size_t)b * p.tiles + tile] = s;
+    }
+    float2* out = p.gpart + ((size_t)b * p.tiles + tile) * p.N;
+    for (int n = tid; n < p.N; n += kThreads) {
+        float2 a = acc_all[n];
+        for (int s = 1; s < SLOTS; ++s) a = cadd(a, acc_all[(size_t)s * p.N + n]);
+        out[n] = a;
+    }
+}
+
+// ---------------------------------------------------------- host launchers
+template <class K>
+static cudaError_t launch_rows(K kernel, size_t smem, const AfParams& p, cudaStream_t st) {
+    if (smem > kMaxSmem) return cudaErrorInvalidConfiguration;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const long long grid = (long long)p.B * p.tiles;
+    if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    kernel<<<(unsigned)grid, kThreads, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t run_forward_m(const AfParams& p, cudaStream_t st) {
+    const size_t smem = forward_smem<M>(p.N);
+    if (2 * p.N <= M) return launch_rows(af_forward_kernel<M, true>, smem, p, st);
+    return launch_rows(af_forward_kernel<M, false>, smem, p, st);
+}
+template <int M>
+cudaError_t run_loss_m(const AfParams& p, cudaStream_t st) {
+    const size_t smem = forward_smem<M>(p.N);
+    if (2 * p.N <= M) return launch_rows(af_loss_kernel<M, true>, smem, p, st);
+    return launch_rows(af_loss_kernel<M, false>, smem, p, st);
+}
+template <int M>
+cudaError_t run_backward_m(const AfParams& p, cudaStream_t st) {
+    const size_t smem = backward_smem<M>(p.N);
+    if (2 * p.N <= M) return launch_rows(af_backward_kernel<M, true>, smem, p, st);
+    return launch_rows(af_backward_kernel<M, false>, smem, p, st);
+}
+
+}  // namespace graf
+
+#define GRAF_INSTANTIATE_M(M)                                                      \
+    template cudaError_t graf::run_forward_m<M>(const graf::AfParams&, cudaStream_t);  \
+    template cudaError_t graf::run_loss_m<M>(const graf::AfParams&, cudaStream_t);     \
+    template cudaError_t graf::run_backward_m<M>(const graf::AfParams&, cudaStream_t);

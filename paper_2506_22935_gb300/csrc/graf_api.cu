@@ -1,0 +1,175 @@
+// graf_api.cu - the C ABI declared in include/graf.h: argument checks,
+// workspace layout and kernel launches.  No allocation, no host sync.
+#include <cuda_runtime.h>
+
+#include "graf.h"
+#include "graf_kernels.cuh"
+
+using graf::AfParams;
+using graf::Tiling;
+
+namespace {
+
+bool is_pow2(int32_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+graf_status_t check_shape(int32_t B, int32_t N, int32_t M) {
+    if (B < 1 || B > (1 << 20)) return GRAF_ERR_INVALID_ARG;
+    if (!is_pow2(M) || M < GRAF_M_MIN || M > GRAF_M_MAX) return GRAF_ERR_INVALID_ARG;
+    if (N < 1 || N > M) return GRAF_ERR_INVALID_ARG;
+    return GRAF_OK;
+}
+
+graf_status_t check_window(int32_t N, int32_t M, const graf_window_t& w) {
+    if (w.k_lo > w.k_hi || w.m_lo > w.m_hi) return GRAF_ERR_INVALID_ARG;
+    if (w.k_lo < -(N - 1) || w.k_hi > N - 1) return GRAF_ERR_INVALID_ARG;
+    if (w.m_lo < -(M / 2) || w.m_hi > M / 2 - 1) return GRAF_ERR_INVALID_ARG;
+    if (w.k_ml < -1 || w.m_ml < -1) return GRAF_ERR_INVALID_ARG;
+    return GRAF_OK;
+}
+
+graf_status_t check_loss(const graf_loss_t& l) {
+    if (!(l.beta > 0.0f) || !(l.eps >= 0.0f)) return GRAF_ERR_INVALID_ARG;
+    if (!(l.w_psl == l.w_psl) || !(l.w_isl == l.w_isl)) return GRAF_ERR_INVALID_ARG;
+    if (l.beta > 1e30f || l.eps > 1e30f) return GRAF_ERR_INVALID_ARG;
+    return GRAF_OK;
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+AfParams base_params(const void* x, graf_input_t kind, int32_t B, int32_t N, int32_t M,
+                     const graf_window_t& w, const Tiling& T) {
+    AfParams p{};
+    p.x = x;
+    p.kind = kind == GRAF_IN_PHASE ? 1 : 0;
+    p.B = B; p.N = N; p.M = M;
+    p.k_lo = w.k_lo; p.k_hi = w.k_hi; p.m_lo = w.m_lo; p.m_hi = w.m_hi;
+    p.k_ml = w.k_ml; p.m_ml = w.m_ml;
+    p.r_lo = T.r_lo; p.r_hi = T.r_hi;
+    p.rows_per_tile = T.rows_per_tile; p.tiles = T.tiles;
+    p.full_m = (w.m_lo == -(M / 2) && w.m_hi == M / 2 - 1) ? 1 : 0;
+    return p;
+}
+
+graf_status_t cuda_status(cudaError_t e) { return e == cudaSuccess ? GRAF_OK : GRAF_ERR_CUDA; }
+
+size_t loss_ws(int32_t B, const Tiling& T) { return align256((size_t)B * T.tiles * sizeof(float4)); }
+// backward workspace: gradient partials [B][tiles][N] complex64 | per-CTA
+// sums [B][tiles] float | per-waveform FP64 sums [B]
+size_t gpart_bytes(int32_t B, int32_t N, const Tiling& T) {
+    return align256((size_t)B * T.tiles * N * sizeof(float2));
+}
+size_t csum_bytes(int32_t B, const Tiling& T) { return align256((size_t)B * T.tiles * sizeof(float)); }
+size_t backward_ws(int32_t B, int32_t N, const Tiling& T) {
+    return gpart_bytes(B, N, T) + csum_bytes(B, T) + align256((size_t)B * sizeof(double));
+}
+
+graf_status_t check_common(const void* x, graf_input_t kind, int32_t B, int32_t N, int32_t M,
+                           const graf_window_t& w) {
+    if (!x) return GRAF_ERR_INVALID_ARG;
+    if (kind != GRAF_IN_COMPLEX && kind != GRAF_IN_PHASE) return GRAF_ERR_INVALID_ARG;
+    graf_status_t s = check_shape(B, N, M);
+    if (s != GRAF_OK) return s;
+    return check_window(N, M, w);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* graf_status_string(graf_status_t status) {
+    switch (status) {
+        case GRAF_OK: return "GRAF_OK";
+        case GRAF_ERR_INVALID_ARG: return "GRAF_ERR_INVALID_ARG: an argument violates a documented constraint";
+        case GRAF_ERR_UNSUPPORTED: return "GRAF_ERR_UNSUPPORTED: shape not supported by this build";
+        case GRAF_ERR_NOMEM: return "GRAF_ERR_NOMEM: allocation failed";
+        case GRAF_ERR_CUDA: return "GRAF_ERR_CUDA: a CUDA runtime call or kernel launch failed";
+        case GRAF_ERR_TIMEOUT: return "GRAF_ERR_TIMEOUT: a bounded device wait expired";
+        case GRAF_ERR_DEVICE_FLAG: return "GRAF_ERR_DEVICE_FLAG: a kernel raised its error flag";
+        case GRAF_ERR_WORKSPACE: return "GRAF_ERR_WORKSPACE: workspace missing or too small";
+    }
+    return "unknown graf_status_t";
+}
+
+int32_t graf_version(void) { return GRAF_VERSION; }
+
+graf_status_t graf_af_forward(const void* x, graf_input_t kind, int32_t B, int32_t N, int32_t M,
+                              graf_window_t w, float eps, float* af_out, void* stream) {
+    graf_status_t s = check_common(x, kind, B, N, M, w);
+    if (s != GRAF_OK) return s;
+    if (!af_out || !(eps >= 0.0f) || eps > 1e30f) return GRAF_ERR_INVALID_ARG;
+    const Tiling T = graf::make_tiling(B, M, w.k_lo, w.k_hi);
+    AfParams p = base_params(x, kind, B, N, M, w, T);
+    p.eps = eps;
+    p.af_out = af_out;
+    return cuda_status(graf::run_forward(p, static_cast<cudaStream_t>(stream)));
+}
+
+size_t graf_af_loss_workspace_bytes(int32_t B, int32_t N, int32_t M, graf_window_t w) {
+    if (check_shape(B, N, M) != GRAF_OK || check_window(N, M, w) != GRAF_OK) return 0;
+    return loss_ws(B, graf::make_tiling(B, M, w.k_lo, w.k_hi));
+}
+
+graf_status_t graf_af_loss(const void* x, graf_input_t kind, int32_t B, int32_t N, int32_t M,
+                           graf_window_t w, graf_loss_t l, float* out8, void* workspace,
+                           size_t workspace_bytes, void* stream) {
+    graf_status_t s = check_common(x, kind, B, N, M, w);
+    if (s != GRAF_OK) return s;
+    if ((s = check_loss(l)) != GRAF_OK) return s;
+    if (!out8) return GRAF_ERR_INVALID_ARG;
+    const Tiling T = graf::make_tiling(B, M, w.k_lo, w.k_hi);
+    if (!workspace || workspace_bytes < loss_ws(B, T)) return GRAF_ERR_WORKSPACE;
+    if (reinterpret_cast<uintptr_t>(workspace) & 255) return GRAF_ERR_WORKSPACE;
+    AfParams p = base_params(x, kind, B, N, M, w, T);
+    p.eps = l.eps; p.beta = l.beta; p.w_psl = l.w_psl; p.w_isl = l.w_isl;
+    p.rec = static_cast<float4*>(workspace);
+    p.out8 = out8;
+    return cuda_status(graf::run_loss(p, static_cast<cudaStream_t>(stream)));
+}
+
+size_t graf_af_backward_workspace_bytes(int32_t B, int32_t N, int32_t M, graf_window_t w) {
+    if (check_shape(B, N, M) != GRAF_OK || check_window(N, M, w) != GRAF_OK) return 0;
+    const Tiling T = graf::make_tiling(B, M, w.k_lo, w.k_hi);
+    const size_t a = loss_ws(B, T), b = backward_ws(B, N, T);
+    return a > b ? a : b;
+}
+
+graf_status_t graf_af_backward(const void* x, graf_input_t kind, int32_t B, int32_t N, int32_t M,
+                               graf_window_t w, graf_loss_t l, const float* saved8, const float* dL,
+                               graf_c32* grad_s, float* grad_phi, void* workspace,
+                               size_t workspace_bytes, void* stream) {
+    graf_status_t s = check_common(x, kind, B, N, M, w);
+    if (s != GRAF_OK) return s;
+    if ((s = check_loss(l)) != GRAF_OK) return s;
+    if (!saved8 || (!grad_s && !grad_phi)) return GRAF_ERR_INVALID_ARG;
+    if (grad_phi && kind != GRAF_IN_PHASE) return GRAF_ERR_INVALID_ARG;
+    const Tiling T = graf::make_tiling(B, M, w.k_lo, w.k_hi);
+    if (!workspace || workspace_bytes < backward_ws(B, N, T)) return GRAF_ERR_WORKSPACE;
+    if (reinterpret_cast<uintptr_t>(workspace) & 255) return GRAF_ERR_WORKSPACE;
+    AfParams p = base_params(x, kind, B, N, M, w, T);
+    p.eps = l.eps; p.beta = l.beta; p.w_psl = l.w_psl; p.w_isl = l.w_isl;
+    p.saved8 = saved8;
+    unsigned char* ws = static_cast<unsigned char*>(workspace);
+    p.gpart = reinterpret_cast<float2*>(ws);
+    p.csum = reinterpret_cast<float*>(ws + gpart_bytes(B, N, T));
+    p.usum = reinterpret_cast<double*>(ws + gpart_bytes(B, N, T) + csum_bytes(B, T));
+    return cuda_status(graf::run_backward(p, dL, reinterpret_cast<float2*>(grad_s), grad_phi,
+                                          static_cast<cudaStream_t>(stream)));
+}
+
+graf_status_t graf_af_loss_backward(const void* x, graf_input_t kind, int32_t B, int32_t N,
+                                    int32_t M, graf_window_t w, graf_loss_t l, float* out8,
+                                    const float* dL, graf_c32* grad_s, float* grad_phi,
+                                    void* workspace, size_t workspace_bytes, void* stream) {
+    graf_status_t s = check_common(x, kind, B, N, M, w);
+    if (s != GRAF_OK) return s;
+    if ((s = check_loss(l)) != GRAF_OK) return s;
+    if (!out8 || (!grad_s && !grad_phi)) return GRAF_ERR_INVALID_ARG;
+    if (grad_phi && kind != GRAF_IN_PHASE) return GRAF_ERR_INVALID_ARG;
+    if (workspace_bytes < graf_af_backward_workspace_bytes(B, N, M, w)) return GRAF_ERR_WORKSPACE;
+    s = graf_af_loss(x, kind, B, N, M, w, l, out8, workspace, workspace_bytes, stream);
+    if (s != GRAF_OK) return s;
+    return graf_af_backward(x, kind, B, N, M, w, l, out8, dL, grad_s, grad_phi, workspace,
+                            workspace_bytes, stream);
+}
+
+}  // extern "C"

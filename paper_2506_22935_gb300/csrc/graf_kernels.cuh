@@ -1,0 +1,195 @@
+// graf_kernels.cuh - launch parameters and shared device helpers of the
+// ambiguity-function kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+#include "graf_fft.cuh"
+
+namespace graf {
+
+constexpr int kThreads = 256;     // threads per CTA of the row kernels
+constexpr int kSmsTarget = 152;   // GB300 SM count, used to size tiles
+
+// Everything a row kernel needs, passed by value.
+struct AfParams {
+    const void* x;   // [B][N] complex64 or float phases
+    int kind;        // 0 complex, 1 phase
+    int B, N, M;
+    int k_lo, k_hi, m_lo, m_hi, k_ml, m_ml;
+    int r_lo, r_hi;        // k >= 0 rows to transform (negative rows are mirrored)
+    int rows_per_tile, tiles;
+    int full_m;            // window covers every Doppler bin
+    float eps, beta, w_psl, w_isl;
+    float* af_out;         // forward: [B][k_hi-k_lo+1][m_hi-m_lo+1]
+    float4* rec;           // loss: per-CTA records [B][tiles] {isl, max, sum, T}
+    float* out8;           // loss: [B][8] scalars
+    const float* saved8;   // backward: [B][8]
+    float2* gpart;         // backward: per-CTA partial dL/ds* [B][tiles][N]
+    float* csum;           // backward: per-CTA sum of c a2 [B][tiles]
+    double* usum;          // backward (grad_s): per-waveform sum_k w_b(k) (C[k] + eps) [B]
+};
+
+// Row range and tiling shared by the host code (workspace sizes) and launches.
+struct Tiling {
+    int r_lo, r_hi, nrows, slots, rows_per_tile, tiles;
+};
+
+inline int tpr_of(int M) { return M < 64 ? 1 : M / 64; }
+
+constexpr size_t kMaxSmem = 232448;  // opt-in dynamic shared memory per CTA (227 KB)
+constexpr size_t kRedBytes = 1024;   // block-reduction scratch
+
+template <int M>
+__host__ __device__ constexpr size_t smem_signal_bytes(int N) {
+    return ((size_t)N * sizeof(float2) + 255) & ~(size_t)255;
+}
+template <int M>
+__host__ __device__ constexpr size_t row_buffer_bytes() {
+    using P = RowPlan<M>;
+    return (((size_t)P::SMEM_ROW * (P::SPLIT ? sizeof(float) : sizeof(float2)) * (256 / P::TPR)) + 255) &
+           ~(size_t)255;
+}
+template <int M>
+constexpr size_t forward_smem(int N) {
+    return smem_signal_bytes<M>(N) + row_buffer_bytes<M>() + kRedBytes;
+}
+template <int M>
+constexpr size_t backward_smem(int N) {
+    return smem_signal_bytes<M>(N) + row_buffer_bytes<M>() +
+           ((((size_t)(256 / RowPlan<M>::TPR)) * N * sizeof(float2) + 255) & ~(size_t)255) + kRedBytes;
+}
+
+size_t row_kernel_smem(int M, int N, int which);  // which: 0 forward/loss, 2 backward
+template <int M> cudaError_t run_forward_m(const AfParams& p, cudaStream_t st);
+template <int M> cudaError_t run_loss_m(const AfParams& p, cudaStream_t st);
+template <int M> cudaError_t run_backward_m(const AfParams& p, cudaStream_t st);
+cudaError_t run_forward(const AfParams& p, cudaStream_t st);
+cudaError_t run_loss(const AfParams& p, cudaStream_t st);
+cudaError_t run_backward(const AfParams& p, const float* dL, float2* grad_s, float* grad_phi,
+                         cudaStream_t st);
+
+// Rows k >= 0 whose transform serves the window: row k gives delay k and,
+// by |X[-k,m]| = |X[k,-m]|, delay -k.
+inline Tiling make_tiling(int B, int M, int k_lo, int k_hi) {
+    Tiling T;
+    if (k_lo >= 0) {
+        T.r_lo = k_lo; T.r_hi = k_hi;
+    } else if (k_hi <= 0) {
+        T.r_lo = -k_hi; T.r_hi = -k_lo;
+    } else {
+        T.r_lo = 0; T.r_hi = (-k_lo > k_hi) ? -k_lo : k_hi;
+    }
+    T.nrows = T.r_hi - T.r_lo + 1;
+    T.slots = kThreads / tpr_of(M);
+    int rps = 8;
+    while (rps > 1) {
+        long long tiles = (T.nrows + (long long)T.slots * rps - 1) / ((long long)T.slots * rps);
+        if ((long long)B * tiles >= 4LL * kSmsTarget) break;
+        rps /= 2;
+    }
+    T.rows_per_tile = T.slots * rps;
+    T.tiles = (T.nrows + T.rows_per_tile - 1) / T.rows_per_tile;
+    return T;
+}
+
+// Load s[0..N) of waveform b into shared memory (phases -> exp(j phi)) and
+// return E = sum |s|^2, reduced in a fixed order (identical in every CTA).
+__device__ __forceinline__ float load_signal(const AfParams& p, int b, float2* s_sm, float* red) {
+    const int tid = threadIdx.x;
+    float e = 0.0f;
+    if (p.kind == 1) {
+        const float* ph = static_cast<const float*>(p.x) + (size_t)b * p.N;
+        for (int n = tid; n < p.N; n += kThreads) {
+            float sn, cs;
+            sincosf(__ldg(ph + n), &sn, &cs);
+            s_sm[n] = make_float2(cs, sn);
+            e = fmaf(cs, cs, fmaf(sn, sn, e));
+        }
+    } else {
+        const float2* xs = static_cast<const float2*>(p.x) + (size_t)b * p.N;
+        for (int n = tid; n < p.N; n += kThreads) {
+            float2 v = __ldg(xs + n);
+            s_sm[n] = v;
+            e = fmaf(v.x, v.x, fmaf(v.y, v.y, e));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if ((tid & 31) == 0) red[tid >> 5] = e;
+    __syncthreads();
+    float E = 0.0f;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) E += red[w];
+    __syncthreads();
+    return E;
+}
+
+// Doppler index (fftshift order) of register w of thread t.
+template <int M>
+__device__ __forceinline__ int doppler_of(int t, int w) {
+    using P = RowPlan<M>;
+    const int q = t + P::TPR * w;
+    return (w >= P::VALS / 2) ? q - M : q;
+}
+
+// Loss weights.  A transformed cell (k >= 0, Doppler m) stands for (k, m)
+// and, for k > 0, the mirrored (-k, -m); its weight is the number of those in
+// Omega (0, 1 or 2).  The Doppler tests depend only on the thread, so they
+// are packed once per CTA into 64-bit column masks (bit w = register w):
+struct ColMasks {
+    unsigned long long in_m;   // m in [m_lo, m_hi]
+    unsigned long long in_mm;  // mirrored Doppler in [m_lo, m_hi]
+    unsigned long long ml_m;   // |m| <= m_ml
+};
+
+template <int M>
+__device__ __forceinline__ ColMasks col_masks(const AfParams& p, int t) {
+    using P = RowPlan<M>;
+    ColMasks c{0ull, 0ull, 0ull};
+    for (int w = 0; w < P::VALS; ++w) {
+        const int q = t + P::TPR * w;
+        const int m = (w >= P::VALS / 2) ? q - M : q;
+        const int mm = (m == -(M / 2)) ? m : -m;
+        const int am = m < 0 ? -m : m;
+        const unsigned long long bit = 1ull << w;
+        if (m >= p.m_lo && m <= p.m_hi) c.in_m |= bit;
+        if (mm >= p.m_lo && mm <= p.m_hi) c.in_mm |= bit;
+        if (am <= p.m_ml) c.ml_m |= bit;
+    }
+    return c;
+}
+
+// Per-row masks: bit w of `one` = weight >= 1, of `two` = weight 2.  Also the
+// plain window masks of rows k and -k for the forward store.
+struct RowMasks {
+    unsigned long long pos, neg, one, two;
+};
+
+__device__ __forceinline__ RowMasks row_masks(const AfParams& p, const ColMasks& c, int k) {
+    const bool in_pos = (k >= p.k_lo) && (k <= p.k_hi);
+    const bool in_neg = (k > 0) && (-k >= p.k_lo) && (-k <= p.k_hi);
+    const bool ml_row = k <= p.k_ml;  // k >= 0, so |-k| = k too
+    RowMasks r;
+    r.pos = in_pos ? c.in_m : 0ull;
+    r.neg = in_neg ? c.in_mm : 0ull;
+    const unsigned long long keep = ml_row ? ~c.ml_m : ~0ull;
+    r.one = (r.pos | r.neg) & keep;
+    r.two = (r.pos & r.neg) & keep;
+    return r;
+}
+
+template <int W>
+__device__ __forceinline__ bool mbit(unsigned long long m) {
+    if constexpr (W < 32) return (static_cast<unsigned>(m) >> W) & 1u;
+    else return (static_cast<unsigned>(m >> 32) >> (W - 32)) & 1u;
+}
+
+template <int W>
+__device__ __forceinline__ float mweight(const RowMasks& r) {
+    return (mbit<W>(r.one) ? 1.0f : 0.0f) + (mbit<W>(r.two) ? 1.0f : 0.0f);
+}
+
+}  // namespace graf

@@ -1,0 +1,330 @@
+"""Python binding of ``libgraf.so`` (the C ABI in ``include/graf.h``).
+
+Two layers:
+
+* ``graf_*`` functions with the C names and arguments: pure ctypes marshalling
+  of raw device pointers (ints), sizes and structs; they return the status
+  code.  Every step of the computation runs in the library's CUDA kernels.
+* torch conveniences (``af_forward``, ``af_loss``, ``af_backward``,
+  ``af_loss_backward``, ``GrafAFLoss``): allocate outputs and workspaces with
+  torch, pass torch's current stream, and raise on a non-zero status.  Torch
+  is used for device memory and streams only.
+
+There is no CPU fallback: if the library is missing or cannot be loaded, the
+first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgraf.so")
+
+GRAF_OK = 0
+GRAF_IN_COMPLEX = 0
+GRAF_IN_PHASE = 1
+GRAF_LOSS_OUT = 8
+GRAF_M_MIN = 8
+GRAF_M_MAX = 16384
+
+
+class GrafError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {graf_status_string(status)} (status {status})")
+
+
+class graf_window_t(ctypes.Structure):
+    _fields_ = [("k_lo", ctypes.c_int32), ("k_hi", ctypes.c_int32), ("m_lo", ctypes.c_int32),
+                ("m_hi", ctypes.c_int32), ("k_ml", ctypes.c_int32), ("m_ml", ctypes.c_int32)]
+
+
+class graf_loss_t(ctypes.Structure):
+    _fields_ = [("w_psl", ctypes.c_float), ("w_isl", ctypes.c_float), ("beta", ctypes.c_float),
+                ("eps", ctypes.c_float)]
+
+
+_lib = None
+_lock = threading.Lock()
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_sz = ctypes.c_size_t
+
+# C signatures: name -> (restype, argtypes)
+_SIGS = {
+    "graf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "graf_version": (_i32, []),
+    "graf_af_forward": (ctypes.c_int, [_vp, ctypes.c_int, _i32, _i32, _i32, graf_window_t, ctypes.c_float,
+                                       _vp, _vp]),
+    "graf_af_loss_workspace_bytes": (_sz, [_i32, _i32, _i32, graf_window_t]),
+    "graf_af_loss": (ctypes.c_int, [_vp, ctypes.c_int, _i32, _i32, _i32, graf_window_t, graf_loss_t, _vp,
+                                    _vp, _sz, _vp]),
+    "graf_af_backward_workspace_bytes": (_sz, [_i32, _i32, _i32, graf_window_t]),
+    "graf_af_backward": (ctypes.c_int, [_vp, ctypes.c_int, _i32, _i32, _i32, graf_window_t, graf_loss_t,
+                                        _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "graf_af_loss_backward": (ctypes.c_int, [_vp, ctypes.c_int, _i32, _i32, _i32, graf_window_t,
+                                             graf_loss_t, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+}
+
+EXPORTED = tuple(_SIGS)
+
+
+def load(path: str | None = None):
+    """Load libgraf.so (built by ``__graft_entry__.build()``).  Raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise ImportError(f"libgraf.so not found at {p}: run __graft_entry__.build() first "
+                                  "(the CUDA library is required; there is no fallback)")
+            lib = ctypes.CDLL(p)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+# ---------------------------------------------------------------- raw ABI
+def graf_status_string(status: int) -> str:
+    return load().graf_status_string(int(status)).decode()
+
+
+def graf_version() -> int:
+    return load().graf_version()
+
+
+def graf_af_forward(x, kind, B, N, M, w, eps, af_out, stream) -> int:
+    return load().graf_af_forward(x, kind, B, N, M, w, eps, af_out, stream)
+
+
+def graf_af_loss_workspace_bytes(B, N, M, w) -> int:
+    return load().graf_af_loss_workspace_bytes(B, N, M, w)
+
+
+def graf_af_loss(x, kind, B, N, M, w, l, out8, workspace, workspace_bytes, stream) -> int:
+    return load().graf_af_loss(x, kind, B, N, M, w, l, out8, workspace, workspace_bytes, stream)
+
+
+def graf_af_backward_workspace_bytes(B, N, M, w) -> int:
+    return load().graf_af_backward_workspace_bytes(B, N, M, w)
+
+
+def graf_af_backward(x, kind, B, N, M, w, l, saved8, dL, grad_s, grad_phi, workspace, workspace_bytes,
+                     stream) -> int:
+    return load().graf_af_backward(x, kind, B, N, M, w, l, saved8, dL, grad_s, grad_phi, workspace,
+                                   workspace_bytes, stream)
+
+
+def graf_af_loss_backward(x, kind, B, N, M, w, l, out8, dL, grad_s, grad_phi, workspace, workspace_bytes,
+                          stream) -> int:
+    return load().graf_af_loss_backward(x, kind, B, N, M, w, l, out8, dL, grad_s, grad_phi, workspace,
+                                        workspace_bytes, stream)
+
+
+# ---------------------------------------------------------------- helpers
+@dataclass(frozen=True)
+class Window:
+    """Delay/Doppler window and mainlobe box (see ``graf_window_t``)."""
+    k_lo: int
+    k_hi: int
+    m_lo: int
+    m_hi: int
+    k_ml: int = 0
+    m_ml: int = 0
+
+    @staticmethod
+    def full(N: int, M: int, k_ml: int = 0, m_ml: int | None = None) -> "Window":
+        """Every delay and Doppler bin.  Default mainlobe box: k = 0 and
+        |m| < M/N, the zero-delay Doppler mainlobe of a unit-modulus code."""
+        if m_ml is None:
+            m_ml = max(M // N - 1, 0)
+        return Window(-(N - 1), N - 1, -(M // 2), M // 2 - 1, k_ml, m_ml)
+
+    @staticmethod
+    def masked(K: int, Mw: int, k_ml: int = 0, m_ml: int = 0) -> "Window":
+        """|k| <= K, |m| <= Mw, minus the box (default: the origin only)."""
+        return Window(-K, K, -Mw, Mw, k_ml, m_ml)
+
+    def c(self) -> graf_window_t:
+        return graf_window_t(self.k_lo, self.k_hi, self.m_lo, self.m_hi, self.k_ml, self.m_ml)
+
+    def as_tuple(self):
+        return (self.k_lo, self.k_hi, self.m_lo, self.m_hi, self.k_ml, self.m_ml)
+
+
+@dataclass(frozen=True)
+class Loss:
+    """L = w_psl PSL_soft + w_isl ISL with soft-max temperature beta."""
+    w_psl: float = 1.0
+    w_isl: float = 1.0
+    beta: float = 50.0
+    eps: float = 1e-12
+
+    def c(self) -> graf_loss_t:
+        return graf_loss_t(self.w_psl, self.w_isl, self.beta, self.eps)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _prep(x):
+    """-> (tensor, kind, B, N) for complex64 signals or float32 phases, [B,N] or [N]."""
+    torch = _torch()
+    if not x.is_cuda:
+        raise ValueError("graf: input must be a CUDA tensor")
+    if x.dim() == 1:
+        x = x.unsqueeze(0)
+    if x.dim() != 2:
+        raise ValueError("graf: input must be [B, N] or [N]")
+    if x.dtype == torch.complex64:
+        kind = GRAF_IN_COMPLEX
+    elif x.dtype == torch.float32:
+        kind = GRAF_IN_PHASE
+    else:
+        raise ValueError("graf: input must be complex64 (signal) or float32 (phases)")
+    x = x.contiguous()
+    return x, kind, x.shape[0], x.shape[1]
+
+
+def _stream(device):
+    return _torch().cuda.current_stream(device).cuda_stream
+
+
+def _check(st, what):
+    if st != GRAF_OK:
+        raise GrafError(st, what)
+
+
+def _workspace(nbytes, device):
+    torch = _torch()
+    # torch's caching allocator returns 512-byte aligned blocks
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def af_forward(x, M: int, window: Window | None = None, eps: float = 1e-12):
+    """Ahat over the window, float32 [B, k_hi-k_lo+1, m_hi-m_lo+1]."""
+    torch = _torch()
+    x, kind, B, N = _prep(x)
+    w = window or Window.full(N, M)
+    out = torch.empty((B, w.k_hi - w.k_lo + 1, w.m_hi - w.m_lo + 1), dtype=torch.float32, device=x.device)
+    _check(graf_af_forward(x.data_ptr(), kind, B, N, M, w.c(), eps, out.data_ptr(), _stream(x.device)),
+           "graf_af_forward")
+    return out
+
+
+def af_loss(x, M: int, window: Window | None = None, loss: Loss = Loss(), workspace=None):
+    """Loss scalars [B, 8] = (L, PSL_soft, ISL, PSL_hard, E, |Omega|, S_p, 0)."""
+    torch = _torch()
+    x, kind, B, N = _prep(x)
+    w = window or Window.full(N, M)
+    nb = graf_af_loss_workspace_bytes(B, N, M, w.c())
+    if nb == 0:
+        raise GrafError(1, "graf_af_loss_workspace_bytes")
+    ws = workspace if workspace is not None and workspace.numel() >= nb else _workspace(nb, x.device)
+    out = torch.empty((B, GRAF_LOSS_OUT), dtype=torch.float32, device=x.device)
+    _check(graf_af_loss(x.data_ptr(), kind, B, N, M, w.c(), loss.c(), out.data_ptr(), ws.data_ptr(),
+                        ws.numel(), _stream(x.device)), "graf_af_loss")
+    return out
+
+
+def af_backward(x, M: int, window: Window | None, loss: Loss, saved8, dL=None, want: str = "auto",
+                workspace=None):
+    """Gradient w.r.t. the input.  want='phi' (phase input) -> float32 [B,N];
+    want='s' -> complex64 [B,N] (dL/dRe s + j dL/dIm s); 'auto' picks by dtype."""
+    torch = _torch()
+    x, kind, B, N = _prep(x)
+    w = window or Window.full(N, M)
+    if want == "auto":
+        want = "phi" if kind == GRAF_IN_PHASE else "s"
+    nb = graf_af_backward_workspace_bytes(B, N, M, w.c())
+    if nb == 0:
+        raise GrafError(1, "graf_af_backward_workspace_bytes")
+    ws = workspace if workspace is not None and workspace.numel() >= nb else _workspace(nb, x.device)
+    saved8 = saved8.contiguous()
+    dl = None if dL is None else dL.reshape(B).to(torch.float32).contiguous()
+    gs = torch.empty((B, N), dtype=torch.complex64, device=x.device) if want == "s" else None
+    gp = torch.empty((B, N), dtype=torch.float32, device=x.device) if want == "phi" else None
+    _check(graf_af_backward(x.data_ptr(), kind, B, N, M, w.c(), loss.c(), saved8.data_ptr(),
+                            None if dl is None else dl.data_ptr(), None if gs is None else gs.data_ptr(),
+                            None if gp is None else gp.data_ptr(), ws.data_ptr(), ws.numel(),
+                            _stream(x.device)), "graf_af_backward")
+    return gp if want == "phi" else gs
+
+
+def af_loss_backward(x, M: int, window: Window | None = None, loss: Loss = Loss(), dL=None,
+                     workspace=None, out8=None, grad=None):
+    """One forward+backward step; returns (out8 [B,8], grad)."""
+    torch = _torch()
+    x, kind, B, N = _prep(x)
+    w = window or Window.full(N, M)
+    nb = graf_af_backward_workspace_bytes(B, N, M, w.c())
+    if nb == 0:
+        raise GrafError(1, "graf_af_backward_workspace_bytes")
+    ws = workspace if workspace is not None and workspace.numel() >= nb else _workspace(nb, x.device)
+    out8 = out8 if out8 is not None else torch.empty((B, GRAF_LOSS_OUT), dtype=torch.float32, device=x.device)
+    if grad is None:
+        grad = torch.empty((B, N), dtype=torch.float32 if kind == GRAF_IN_PHASE else torch.complex64,
+                           device=x.device)
+    dl = None if dL is None else dL.reshape(B).to(torch.float32).contiguous()
+    gs = grad.data_ptr() if kind == GRAF_IN_COMPLEX else None
+    gp = grad.data_ptr() if kind == GRAF_IN_PHASE else None
+    _check(graf_af_loss_backward(x.data_ptr(), kind, B, N, M, w.c(), loss.c(), out8.data_ptr(),
+                                 None if dl is None else dl.data_ptr(), gs, gp, ws.data_ptr(), ws.numel(),
+                                 _stream(x.device)), "graf_af_loss_backward")
+    return out8, grad
+
+
+def _make_autograd():
+    torch = _torch()
+
+    class GrafAFLoss(torch.autograd.Function):
+        """L(x) per waveform (float32 [B]) with the library's Wirtinger backward.
+
+        x: float32 phases [B, N] or complex64 signals [B, N].  The gradient
+        follows PyTorch's complex convention (dL/dRe + j dL/dIm)."""
+
+        @staticmethod
+        def forward(ctx, x, M, window, loss):
+            out8 = af_loss(x, M, window, loss)
+            ctx.save_for_backward(x, out8)
+            ctx.cfg = (M, window, loss)
+            ctx.mark_non_differentiable(out8)
+            return out8[:, 0].clone(), out8
+
+        @staticmethod
+        def backward(ctx, g_l, g_out8):
+            x, out8 = ctx.saved_tensors
+            M, window, loss = ctx.cfg
+            if g_l is None:
+                return None, None, None, None
+            g = af_backward(x, M, window, loss, out8, dL=g_l)
+            return g.reshape(x.shape), None, None, None
+
+    return GrafAFLoss
+
+
+_autograd_cls = None
+
+
+def GrafAFLoss():
+    """The torch.autograd.Function class (created lazily so importing this
+    module does not import torch)."""
+    global _autograd_cls
+    if _autograd_cls is None:
+        _autograd_cls = _make_autograd()
+    return _autograd_cls
+
+
+def af_loss_autograd(x, M: int, window: Window | None = None, loss: Loss = Loss()):
+    """Differentiable per-waveform loss [B] (and the detached scalars [B, 8])."""
+    xx = x if x.dim() == 2 else x.unsqueeze(0)
+    w = window or Window.full(xx.shape[1], M)
+    return GrafAFLoss().apply(xx, M, w, loss)

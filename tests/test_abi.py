@@ -1,0 +1,111 @@
+"""The C-ABI library loads and exports every symbol include/graf.h declares;
+host-side argument checks and workspace sizing.  No kernel is launched: every
+call here is rejected (or sized) on the host before any CUDA call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2506_22935_gb300 import _build
+from paper_2506_22935_gb300 import graf as g
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return g.load()
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "graf.h")).read()
+    return sorted(set(re.findall(r"GRAF_API[^;{]*?\b(graf_[a-z0-9_]+)\s*\(", text, re.S)))
+
+
+def test_header_declares_binding_names():
+    assert _declared() == sorted(g.EXPORTED)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+
+
+def test_status_strings_and_version(lib):
+    assert g.graf_version() == 1
+    for st in range(8):
+        assert g.graf_status_string(st).startswith("GRAF_")
+    assert "unknown" in g.graf_status_string(99)
+
+
+W = g.Window
+
+
+@pytest.mark.parametrize("B,N,M,w,ok", [
+    (1, 64, 128, W.full(64, 128), True),
+    (256, 1024, 2048, W.full(1024, 2048), True),
+    (1, 1, 8, W(0, 0, -4, 3, 0, 0), True),
+    (1, 64, 100, W(0, 0, 0, 0), False),        # M not a power of two
+    (1, 64, 4, W(0, 0, 0, 0), False),          # M below GRAF_M_MIN
+    (1, 64, 32768, W(0, 0, 0, 0), False),      # M above GRAF_M_MAX
+    (1, 129, 128, W(0, 0, 0, 0), False),       # N > M
+    (0, 64, 128, W(0, 0, 0, 0), False),        # B = 0
+    (1, 64, 128, W(-64, 0, 0, 0), False),      # |k| > N-1
+    (1, 64, 128, W(0, 0, -65, 0), False),      # m < -M/2
+    (1, 64, 128, W(0, 0, 0, 64), False),       # m > M/2-1
+    (1, 64, 128, W(3, 2, 0, 0), False),        # k_lo > k_hi
+    (1, 64, 128, W(0, 0, 0, 0, -2, 0), False),  # box size < -1
+])
+def test_workspace_bytes_validate(lib, B, N, M, w, ok):
+    a = g.graf_af_loss_workspace_bytes(B, N, M, w.c())
+    b = g.graf_af_backward_workspace_bytes(B, N, M, w.c())
+    if ok:
+        assert a > 0 and b >= a and a % 256 == 0 and b % 256 == 0
+    else:
+        assert a == 0 and b == 0
+
+
+def test_workspace_scales_with_batch(lib):
+    w = W.full(1024, 2048)
+    b1 = g.graf_af_backward_workspace_bytes(1, 1024, 2048, w.c())
+    b256 = g.graf_af_backward_workspace_bytes(256, 1024, 2048, w.c())
+    # per-CTA gradient partials B * tiles * N complex64 (1 <= tiles <= rows / 8)
+    # plus per-CTA and per-waveform scalars
+    assert 1024 * 8 <= b1 <= 128 * 1024 * 8 + 4096
+    assert 256 * 1024 * 8 <= b256 <= 256 * 128 * 1024 * 8 + 256 * 128 * 4 + 4096
+
+
+FAKE = 0x1000  # never dereferenced: every call below fails its host checks
+
+
+def test_invalid_arguments_rejected_before_launch(lib):
+    w, l = W.full(64, 128).c(), g.Loss().c()
+    INV, WS = 1, 7
+    assert g.graf_af_forward(None, 1, 1, 64, 128, w, 1e-12, FAKE, None) == INV
+    assert g.graf_af_forward(FAKE, 1, 1, 64, 128, w, 1e-12, None, None) == INV
+    assert g.graf_af_forward(FAKE, 2, 1, 64, 128, w, 1e-12, FAKE, None) == INV
+    assert g.graf_af_forward(FAKE, 1, 1, 64, 128, w, -1.0, FAKE, None) == INV
+    assert g.graf_af_forward(FAKE, 1, 1, 64, 96, w, 1e-12, FAKE, None) == INV
+    bad_beta = g.Loss(1, 1, 0.0, 1e-12).c()
+    assert g.graf_af_loss(FAKE, 1, 1, 64, 128, w, bad_beta, FAKE, FAKE, 1 << 20, None) == INV
+    assert g.graf_af_loss(FAKE, 1, 1, 64, 128, w, l, FAKE, None, 0, None) == WS
+    assert g.graf_af_loss(FAKE, 1, 1, 64, 128, w, l, FAKE, FAKE, 16, None) == WS
+    assert g.graf_af_loss(FAKE, 1, 1, 64, 128, w, l, FAKE, FAKE + 8, 1 << 20, None) == WS
+    # grad_phi needs phase input; at least one gradient output
+    assert g.graf_af_backward(FAKE, 0, 1, 64, 128, w, l, FAKE, None, None, FAKE, FAKE, 1 << 20, None) == INV
+    assert g.graf_af_backward(FAKE, 1, 1, 64, 128, w, l, FAKE, None, None, None, FAKE, 1 << 20, None) == INV
+    assert g.graf_af_backward(FAKE, 1, 1, 64, 128, w, l, None, None, None, FAKE, FAKE, 1 << 20, None) == INV
+    assert g.graf_af_loss_backward(FAKE, 1, 1, 64, 128, w, l, FAKE, None, None, FAKE, FAKE, 16, None) == WS
+
+
+def test_binding_refuses_missing_library(tmp_path):
+    with pytest.raises(ImportError):
+        g._lib_saved = g._lib
+        try:
+            g._lib = None
+            g.load(str(tmp_path / "nope.so"))
+        finally:
+            g._lib = g._lib_saved

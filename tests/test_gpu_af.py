@@ -1,0 +1,251 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (stated by the method's accuracy target): |Ahat_gpu - Ahat_fp64|
+<= 1e-5 absolute on the energy-normalised magnitude; gradients within 1e-4
+relative L2; loss scalars within 1e-5 relative (their fp32 sums run over at
+most a few million cells, a relative rounding of ~1e-6); |Omega| exact."""
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_2506_22935_gb300 import _build, inputs
+from paper_2506_22935_gb300 import graf as g
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+A_TOL = 1e-5
+G_TOL = 1e-4
+L_TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    _build.build()
+    g.load()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+
+
+def _dev():
+    return torch.device("cuda:0")
+
+
+def _signals(kind, B, N, seed):
+    """(numpy input as the GPU sees it, list of complex128 oracle signals)."""
+    if kind == "phase":
+        phi = inputs.random_phases(seed, B, N)
+        return phi, [orc.signal_from_phase(phi[b].astype(np.float64)) for b in range(B)]
+    s = inputs.random_complex(seed, B, N)
+    return s, [s[b].astype(np.complex128) for b in range(B)]
+
+
+def _rel(a, b):
+    d = np.linalg.norm(np.asarray(a) - np.asarray(b))
+    n = np.linalg.norm(np.asarray(b))
+    return d / n if n > 0 else d
+
+
+# --------------------------------------------------------------------- forward
+FWD_CASES = [
+    # N, M, window (None = all delays and Doppler bins)
+    (1, 8, None), (2, 8, None), (3, 8, None), (8, 8, None), (5, 16, None), (16, 16, None),
+    (13, 32, None), (32, 32, None), (31, 64, None), (64, 64, None), (33, 64, None),
+    (100, 256, None), (256, 256, None), (200, 512, (-40, 25, -256, 255)),
+    (300, 1024, (-7, 9, -512, 511)), (700, 1024, (690, 699, -512, 511)),
+    (1024, 2048, (-3, 2, -1024, 1023)), (1024, 2048, (-1023, -1020, -1024, 1023)),
+    (1024, 2048, (5, 9, -100, 37)), (1500, 2048, (-2, 1, -1024, 1023)),
+    (2048, 4096, (-2, 1, -2048, 2047)), (3000, 4096, (2990, 2999, -2048, 2047)),
+    (4096, 8192, (-2, 2, -4096, 4095)), (5000, 8192, (-4999, -4996, -4096, 4095)),
+    (8192, 16384, (-1, 2, -8192, 8191)), (9000, 16384, (8995, 8999, -8192, 8191)),
+]
+
+
+@pytest.mark.parametrize("kind", ["phase", "complex"])
+@pytest.mark.parametrize("N,M,win", FWD_CASES)
+def test_forward_matches_oracle(N, M, win, kind):
+    B, eps = 2, 1e-12
+    x, sigs = _signals(kind, B, N, 1000 + N + M)
+    w = g.Window.full(N, M) if win is None else g.Window(*win)
+    A = g.af_forward(torch.from_numpy(x).to(_dev()), M, w, eps).cpu().numpy()
+    for b in range(B):
+        want = orc.af_ahat(sigs[b], M, w.k_lo, w.k_hi, w.m_lo, w.m_hi, eps)
+        err = np.abs(A[b] - want).max()
+        assert err <= A_TOL, f"max |dAhat| = {err:.3e}"
+
+
+def test_lfm_chirp_n64_m128_forward():
+    """Single LFM chirp, N = 64 (phase pi n^2/64), all 127 delays, M = 128,
+    eps = 1e-12: every cell within 1e-5 of the FP64 oracle."""
+    N, M, eps = 64, 128, 1e-12
+    phi = inputs.lfm_phases(N)
+    w = g.Window.full(N, M)
+    A = g.af_forward(torch.from_numpy(phi).to(_dev()), M, w, eps).cpu().numpy()[0]
+    want = orc.af_ahat(orc.signal_from_phase(phi.astype(np.float64)), M, *w.as_tuple()[:4], eps)
+    assert A.shape == (127, 128)
+    assert np.abs(A - want).max() <= A_TOL
+
+
+# ----------------------------------------------------------- loss and gradient
+LOSS_CASES = [
+    # N, M, window (None = full with the default mainlobe box), loss (w_psl, w_isl, beta)
+    (1, 8, None, (1.0, 1.0, 50.0)),
+    (3, 8, None, (1.0, 1.0, 50.0)),
+    (8, 8, None, (1.0, 1.0, 5.0)),
+    (13, 32, None, (1.0, 0.0, 50.0)),
+    (13, 32, None, (0.0, 1.0, 50.0)),
+    (16, 16, (-4, 9, -8, 7, 1, 2), (0.7, 0.3, 30.0)),
+    (31, 64, (0, 30, -10, 31, 0, 0), (1.0, 1.0, 50.0)),
+    (64, 128, None, (1.0, 1.0, 50.0)),
+    (64, 128, (-20, 20, -16, 16, 0, 0), (0.0, 1.0, 50.0)),
+    (100, 256, (-99, -3, -128, 127, 0, 0), (1.0, 1.0, 500.0)),
+    (256, 512, None, (1.0, 1.0, 50.0)),
+    (200, 256, None, (1.0, 1.0, 50.0)),
+    (128, 1024, (-30, 30, -100, 100, 0, 0), (1.0, 1.0, 50.0)),
+    (256, 2048, (-40, 40, -64, 64, 0, 0), (1.0, 1.0, 50.0)),
+    (1024, 2048, (-12, 12, -1024, 1023, 0, 1), (1.0, 1.0, 50.0)),
+    (512, 4096, (-8, 8, -256, 256, 0, 0), (0.0, 1.0, 50.0)),
+    (1024, 8192, (-4, 4, -256, 256, 0, 0), (0.0, 1.0, 50.0)),
+    (2048, 16384, (-2, 3, -300, 300, 0, 0), (1.0, 1.0, 50.0)),
+]
+
+
+def _loss_setup(N, M, win, lp):
+    w = g.Window.full(N, M) if win is None else g.Window(*win)
+    loss = g.Loss(lp[0], lp[1], lp[2], 1e-12)
+    return w, loss
+
+
+def _check_scalars(got, want):
+    for i in (0, 1, 2, 3):
+        assert abs(got[i] - want[i]) <= L_TOL * max(abs(want[i]), 1e-6), (i, got, want)
+    assert abs(got[4] - want[4]) <= 1e-6 * want[4]
+    assert got[5] == want[5]
+    assert abs(got[6] - want[6]) <= 1e-4 * max(abs(want[6]), 1e-8), (got, want)
+
+
+@pytest.mark.parametrize("kind", ["phase", "complex"])
+@pytest.mark.parametrize("N,M,win,lp", LOSS_CASES)
+def test_loss_and_gradient_match_oracle(N, M, win, lp, kind):
+    B = 2
+    x, sigs = _signals(kind, B, N, 2000 + N + M)
+    w, loss = _loss_setup(N, M, win, lp)
+    xt = torch.from_numpy(x).to(_dev())
+    out8 = g.af_loss(xt, M, w, loss).cpu().numpy()
+    out8b, grad = g.af_loss_backward(xt, M, w, loss)
+    out8b, grad = out8b.cpu().numpy(), grad.cpu().numpy()
+    assert np.array_equal(out8, out8b)
+    for b in range(B):
+        gs, gphi, want = orc.grad(sigs[b], M, w.as_tuple(), loss.w_psl, loss.w_isl, loss.beta, loss.eps)
+        _check_scalars(out8[b], want)
+        ref = gphi if kind == "phase" else gs
+        if np.linalg.norm(ref) < 1e-9:  # e.g. N = 1 with phase input: the loss is constant
+            assert np.abs(grad[b]).max() < 1e-6
+        else:
+            assert _rel(grad[b], ref) <= G_TOL, f"grad rel L2 {_rel(grad[b], ref):.3e}"
+
+
+def test_complex_gradient_from_phase_input_matches_oracle():
+    """grad_s for phase input (both outputs requested through the raw ABI)."""
+    N, M, B = 40, 128, 3
+    phi, sigs = _signals("phase", B, N, 77)
+    w, loss = g.Window.full(N, M), g.Loss()
+    xt = torch.from_numpy(phi).to(_dev())
+    out8 = g.af_loss(xt, M, w, loss)
+    nb = g.graf_af_backward_workspace_bytes(B, N, M, w.c())
+    ws = torch.empty(nb, dtype=torch.uint8, device=_dev())
+    gs = torch.empty((B, N), dtype=torch.complex64, device=_dev())
+    gp = torch.empty((B, N), dtype=torch.float32, device=_dev())
+    st = g.graf_af_backward(xt.data_ptr(), g.GRAF_IN_PHASE, B, N, M, w.c(), loss.c(), out8.data_ptr(), None,
+                            gs.data_ptr(), gp.data_ptr(), ws.data_ptr(), nb,
+                            torch.cuda.current_stream().cuda_stream)
+    assert st == 0
+    gs, gp = gs.cpu().numpy(), gp.cpu().numpy()
+    for b in range(B):
+        rs, rp, _ = orc.grad(sigs[b], M, w.as_tuple(), loss.w_psl, loss.w_isl, loss.beta, loss.eps)
+        assert _rel(gs[b], rs) <= G_TOL and _rel(gp[b], rp) <= G_TOL
+
+
+def test_upstream_gradient_scales_and_autograd():
+    N, M, B = 50, 128, 3
+    phi, sigs = _signals("phase", B, N, 91)
+    w, loss = g.Window.full(N, M), g.Loss(1.0, 0.5, 20.0, 1e-12)
+    x = torch.from_numpy(phi).to(_dev()).requires_grad_(True)
+    Lb, out8 = g.af_loss_autograd(x, M, w, loss)
+    coef = torch.tensor([1.0, -2.5, 0.25], device=_dev())
+    (Lb * coef).sum().backward()
+    got = x.grad.cpu().numpy()
+    for b in range(B):
+        _, rp, o8 = orc.grad(sigs[b], M, w.as_tuple(), loss.w_psl, loss.w_isl, loss.beta, loss.eps)
+        assert abs(Lb[b].item() - o8[0]) <= L_TOL * abs(o8[0])
+        assert _rel(got[b], coef[b].item() * rp) <= G_TOL
+
+
+def test_empty_sidelobe_region_gives_zero_loss_and_gradient():
+    N, M = 20, 64
+    phi, _ = _signals("phase", 2, N, 5)
+    w = g.Window(-1, 1, -2, 2, 1, 2)  # window == mainlobe box
+    out8, grad = g.af_loss_backward(torch.from_numpy(phi).to(_dev()), M, w, g.Loss())
+    out8, grad = out8.cpu().numpy(), grad.cpu().numpy()
+    assert np.all(out8[:, [0, 1, 2, 3, 5, 6]] == 0.0)
+    assert np.all(grad == 0.0)
+
+
+def test_deterministic_and_stream_ordered():
+    N, M, B = 300, 1024, 5
+    phi, _ = _signals("phase", B, N, 8)
+    x = torch.from_numpy(phi).to(_dev())
+    w, loss = g.Window.full(N, M), g.Loss()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        o1, g1 = g.af_loss_backward(x, M, w, loss)
+        o2, g2 = g.af_loss_backward(x, M, w, loss)
+    s.synchronize()
+    assert torch.equal(o1, o2) and torch.equal(g1, g2)
+
+
+def test_large_batch_small_waveforms():
+    N, M, B = 24, 64, 1000
+    phi, sigs = _signals("phase", B, N, 9)
+    w, loss = g.Window.full(N, M), g.Loss()
+    out8, grad = g.af_loss_backward(torch.from_numpy(phi).to(_dev()), M, w, loss)
+    out8, grad = out8.cpu().numpy(), grad.cpu().numpy()
+    for b in (0, 1, 517, 999):
+        _, rp, o8 = orc.grad(sigs[b], M, w.as_tuple(), loss.w_psl, loss.w_isl, loss.beta, loss.eps)
+        _check_scalars(out8[b], o8)
+        assert _rel(grad[b], rp) <= G_TOL
+
+
+# ------------------------------------------------------------------ full size
+def test_full_size_batch_n1024_m2048():
+    """256 random polyphase codes, N = 1024, M = 2048, all 2047 delays, PSL
+    (log-sum-exp, beta = 50) + ISL, forward + backward w.r.t. phases, in the
+    launch configuration the bench times.  Waveform 0 is checked against the
+    oracle in full; every waveform against the phase-invariance identity
+    sum_p dL/dphi[p] = 0 and E = N; sampled AF cells of four waveforms
+    against the oracle cell by cell."""
+    B, N, M = 256, 1024, 2048
+    phi = inputs.random_phases(inputs.SEED_BASE + 2, B, N)
+    x = torch.from_numpy(phi).to(_dev())
+    w, loss = g.Window.full(N, M), g.Loss(1.0, 1.0, 50.0, 1e-12)
+    out8, grad = g.af_loss_backward(x, M, w, loss)
+    out8, grad = out8.cpu().numpy(), grad.cpu().numpy()
+    assert np.all(np.isfinite(out8)) and np.all(np.isfinite(grad))
+    assert np.all(np.abs(out8[:, 4] - N) <= 1e-3)
+    sums = np.abs(grad.sum(axis=1)) / np.linalg.norm(grad, axis=1)
+    assert sums.max() <= 1e-4
+    s0 = orc.signal_from_phase(phi[0].astype(np.float64))
+    _, rp, o8 = orc.grad(s0, M, w.as_tuple(), loss.w_psl, loss.w_isl, loss.beta, loss.eps)
+    _check_scalars(out8[0], o8)
+    assert _rel(grad[0], rp) <= G_TOL
+    rng = np.random.default_rng(0)
+    sub = [0, 1, 128, 255]
+    A = g.af_forward(x[sub], M, w, loss.eps).cpu().numpy()
+    for i, b in enumerate(sub):
+        ks = rng.integers(-(N - 1), N, 64)
+        ms = rng.integers(-(M // 2), M // 2, 64)
+        want = orc.af_cells(orc.signal_from_phase(phi[b].astype(np.float64)), M, ks, ms, loss.eps)
+        got = A[i][ks + N - 1, ms + M // 2]
+        assert np.abs(got - want).max() <= A_TOL
+        # volume identity: sum of Ahat^2 over all cells = M + eps * cells / E^2
+        assert abs(float(np.sum(A[i].astype(np.float64) ** 2)) - M) <= 1e-3 * M
