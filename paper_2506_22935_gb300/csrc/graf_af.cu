@@ -88,13 +88,6 @@ __device__ __forceinline__ float2 signal_at(const AfParams& p, int b, int n) {
     return static_cast<const float2*>(p.x)[(size_t)b * p.N + n];
 }
 
-// Base weight of transformed row k (see the backward kernel): every Doppler
-// bin of rows k and -k that lies in the window, when the window spans all bins.
-__device__ __forceinline__ int base_weight(const AfParams& p, int k) {
-    if (!p.full_m) return 0;
-    return ((k >= p.k_lo && k <= p.k_hi) ? 1 : 0) + ((k > 0 && -k >= p.k_lo && -k <= p.k_hi) ? 1 : 0);
-}
-
 // dL/ds* of the FFT part = sum over tiles (fixed order).  grad_phi =
 // 2 Im(dL/ds* conj(s)): the row-uniform part and the energy terms are s[n]
 // times real numbers and contribute nothing to it.
@@ -112,7 +105,8 @@ __global__ void grad_phi_kernel(AfParams p, const float* dL, float* grad_phi) {
 }
 
 // Per waveform, in FP64: U = sum_k w_b(k) (C[k] + eps) over the transformed
-// rows, C[k] = sum_n |s[n]|^2 |s[n-k]|^2 (Parseval: sum_m |X[k,m]|^2 = M C[k]).
+// rows, C[k] = sum_n |s[n]|^2 |s[n-k]|^2 (Parseval: sum_m |X[k,m]|^2 = M C[k]),
+// and E = sum_n |s[n]|^2 -> usum[2b], usum[2b+1].
 __global__ void uniform_sum_kernel(AfParams p) {
     extern __shared__ double a_sm[];
     __shared__ double red[32];
@@ -130,14 +124,27 @@ __global__ void uniform_sum_kernel(AfParams p) {
         for (int n = k; n < p.N; ++n) c += a_sm[n] * a_sm[n - k];
         acc += wb * (c + (double)p.eps);
     }
+    // E in FP64 from the same |s|^2, so the closed form cancels exactly
+    double e = 0.0;
+    for (int n = threadIdx.x; n < p.N; n += blockDim.x) e += a_sm[n];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    for (int o = 16; o > 0; o >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        e += __shfl_xor_sync(0xffffffffu, e, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5] = acc;
+        red[16 + (threadIdx.x >> 5)] = e;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < (int)(blockDim.x / 32); ++w) s += red[w];
-        p.usum[b] = s;
+        double s = 0.0, es = 0.0;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) {
+            s += red[w];
+            es += red[16 + w];
+        }
+        p.usum[2 * b] = s;
+        p.usum[2 * b + 1] = es;
     }
 }
 
@@ -166,7 +173,7 @@ __global__ void grad_s_kernel(AfParams p, const float* dL, float2* grad_s, float
     for (int i = 0; i < p.tiles; ++i) cs += p.csum[(size_t)b * p.tiles + i];
     const float2 s = signal_at(p, b, n);
     const float* sv = p.saved8 + (size_t)b * 8;
-    const double E = sv[4];
+    const double E = p.usum[2 * b + 1];
     const float bl2 = p.beta * 1.4426950408889634f;
     const float p0 = exp2f(-(sv[1] * bl2));
     const double Ap = (double)fmaf(p.w_psl, p0, p.w_isl);
@@ -179,8 +186,17 @@ __global__ void grad_s_kernel(AfParams p, const float* dL, float2* grad_s, float
         if (n + k < p.N) t += a_sm[n + k];
         corr += wb * t;
     }
-    const double gu = Ap * (double)p.M * (corr / (E * E) - 2.0 * p.usum[b] / (E * E * E));
-    const double coef = -2.0 * E * cs + gu;  // real multiplier of s[n]
+    const double gu = Ap * (double)p.M * (corr / (E * E) - 2.0 * p.usum[2 * b] / (E * E * E));
+    // origin cell, left out of the FFT part: its exact total is -2 eps c00 s / E
+    double c00 = 0.0;
+    if (p.k_lo <= 0 && p.k_hi >= 0 && p.m_lo <= 0 && p.m_hi >= 0) {
+        const int w00 = (p.k_ml >= 0 && p.m_ml >= 0) ? 0 : 1;
+        const double a00 = 1.0 + (double)p.eps / (E * E);
+        const double pr = exp((double)p.beta * (a00 - (double)sv[1]));
+        c00 = ((w00 - base_weight(p, 0)) * Ap + (w00 > 0 ? w00 * (double)p.w_psl * (pr - (double)p0) : 0.0)) /
+              (E * E);
+    }
+    const double coef = -2.0 * E * cs + gu - 2.0 * (double)p.eps * c00 / E;  // real multiplier of s[n]
     const double scale = 2.0 * (dL ? (double)dL[b] : 1.0);
     grad_s[(size_t)b * p.N + n] = make_float2((float)(scale * (g.x + coef * s.x)),
                                               (float)(scale * (g.y + coef * s.y)));
@@ -206,7 +222,11 @@ __global__ void grad_s_kernel(AfParams p, const float* dL, float2* grad_s, float
 
 template <int M>
 static size_t smem_need_m(int N, int which) {
-    return which == 2 ? backward_smem<M>(N) : forward_smem<M>(N);
+    if (which == 2) {
+        const int a = backward_acc_copies<M>(N);
+        return a ? backward_smem<M>(N, a) : (size_t)-1;
+    }
+    return forward_smem<M>(N);
 }
 static size_t smem_need(int M, int N, int which) {
     switch (M) {
@@ -227,6 +247,24 @@ static size_t smem_need(int M, int N, int which) {
 }
 
 size_t row_kernel_smem(int M, int N, int which) { return smem_need(M, N, which); }
+
+int acc_copies_for(int M, int N) {
+    switch (M) {
+        case 8: return backward_acc_copies<8>(N);
+        case 16: return backward_acc_copies<16>(N);
+        case 32: return backward_acc_copies<32>(N);
+        case 64: return backward_acc_copies<64>(N);
+        case 128: return backward_acc_copies<128>(N);
+        case 256: return backward_acc_copies<256>(N);
+        case 512: return backward_acc_copies<512>(N);
+        case 1024: return backward_acc_copies<1024>(N);
+        case 2048: return backward_acc_copies<2048>(N);
+        case 4096: return backward_acc_copies<4096>(N);
+        case 8192: return backward_acc_copies<8192>(N);
+        case 16384: return backward_acc_copies<16384>(N);
+        default: return 0;
+    }
+}
 
 cudaError_t run_forward(const AfParams& p, cudaStream_t st) { GRAF_DISPATCH_M(run_forward_m, p.M, p, st) }
 cudaError_t run_loss(const AfParams& p, cudaStream_t st) {

@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(kThreads, 1) af_loss_kernel(AfParams p) {
 // w_b A' M R[k,n] / E^2 (the adjoint of an M-point DFT applied to the DFT of
 // a row of support <= M is M times the row), whose scatter is s[p] times a
 // real number: it contributes exactly nothing to dL/dphi, and for dL/ds it
-// is added in closed form, in FP64, by grad_uniform_kernel.  Only the second
+// is added in closed form, in FP64, by grad_s_kernel.  Only the second
 // term goes through the FFT, G = c X with c = [...] / E^2.  This keeps the
 // PSL term, whose softmax weights are ~1/|Omega| (2.4e-7 at N=1024, M=2048),
 // from vanishing next to the ISL weight in FP32, and avoids summing the
@@ -240,11 +240,11 @@ __global__ void __launch_bounds__(kThreads, 1) af_backward_kernel(AfParams p) {
     float2* bufs = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(p.N));
     float2* acc_all = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(p.N) + row_buffer_bytes<M>());
     float* red = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(acc_all) +
-                                          (((size_t)SLOTS * p.N * sizeof(float2) + 255) & ~(size_t)255));
+                                          (((size_t)p.acc_copies * p.N * sizeof(float2) + 255) & ~(size_t)255));
 
     const int tid = threadIdx.x, slot = tid / P::TPR, t = tid % P::TPR;
     const int b = blockIdx.x / p.tiles, tile = blockIdx.x % p.tiles;
-    for (int i = tid; i < SLOTS * p.N; i += kThreads) acc_all[i] = make_float2(0.0f, 0.0f);
+    for (int i = tid; i < p.acc_copies * p.N; i += kThreads) acc_all[i] = make_float2(0.0f, 0.0f);
     const float E = load_signal(p, b, s_sm, red);  // includes __syncthreads
     const float invE2 = 1.0f / (E * E);
     const float eps_n = p.eps * invE2;
@@ -258,7 +258,10 @@ __global__ void __launch_bounds__(kThreads, 1) af_backward_kernel(AfParams p) {
     float2* buf = bufs + (size_t)slot * (P::SPLIT ? P::SMEM_ROW / 2 : P::SMEM_ROW);
     const ColMasks cm = col_masks<M>(p, t);
     constexpr unsigned long long full_mask = P::VALS == 64 ? ~0ull : ((1ull << P::VALS) - 1ull);
-    float2* acc = acc_all + (size_t)slot * p.N;
+    // slots sharing an accumulator (when shared memory is short) take turns
+    const int turns = SLOTS / p.acc_copies;
+    const int my_turn = slot / p.acc_copies;
+    float2* acc = acc_all + (size_t)(slot % p.acc_copies) * p.N;
 
     const int row0 = p.r_lo + tile * p.rows_per_tile;
     const int row_end = min(row0 + p.rows_per_tile, p.r_hi + 1);
@@ -267,31 +270,37 @@ __global__ void __launch_bounds__(kThreads, 1) af_backward_kernel(AfParams p) {
     float2 v[P::VALS];
     for (int it = 0; it < iters; ++it) {
         const int k = row0 + slot + it * SLOTS;
-        const bool valid = k < row_end;
+        // row 0 is R[0,n] = |s[n]|^2: it does not depend on the phases
+        const bool valid = k < row_end && !(p.phase_only && k == 0);
         build_lag_row<M, HALF>(v, s_sm, p.N, k, t, valid);
         row_sync<P::TPR>(slot);
         row_fft<M, false, HALF, false>(v, buf, t, slot);
         const RowMasks rmk = row_masks(p, cm, k);
         const bool uniform = rmk.one == full_mask && (rmk.two == 0ull || rmk.two == full_mask);
         const float wrow = valid ? (rmk.two != 0ull ? 2.0f : (rmk.one != 0ull ? 1.0f : 0.0f)) : 0.0f;
-        const int in_pos = (k >= p.k_lo && k <= p.k_hi) ? 1 : 0;
-        const int in_neg = (k > 0 && -k >= p.k_lo && -k <= p.k_hi) ? 1 : 0;
-        const float wb = (valid && p.full_m) ? (float)(in_pos + in_neg) : 0.0f;
+        const float wb = valid ? (float)base_weight(p, k) : 0.0f;
         sfor<0, P::VALS>([&](auto w) {
             const float2 x = v[w];
             const float a2 = fmaf(fmaf(x.x, x.x, x.y * x.y), invE2, eps_n);
             const float wt = (uniform || !valid) ? wrow : mweight<decltype(w)::value>(rmk);
             const float pr = exp2f(fmaf(a2, bl2, -sh));
             const float cpsl = wt > 0.0f ? wt * cP * (pr - p0) : 0.0f;
-            const float c = fmaf(wt - wb, cA, cpsl);
+            float c = fmaf(wt - wb, cA, cpsl);
+            // the origin X[0,0] = E: its scatter (2 E c s) and energy term
+            // (-2 E c a2 s) cancel to -2 eps c s / E, added in closed form by
+            // grad_s_kernel; leaving it out here avoids the cancellation
+            if constexpr (decltype(w)::value == 0) {
+                if (k == 0 && t == 0) c = 0.0f;
+            }
             csum = fmaf(c, a2, csum);
             v[w] = make_float2(c * x.x, c * x.y);
         });
         row_sync<P::TPR>(slot);  // buffer reads of the forward transform are done
         row_fft<M, true, false, HALF>(v, buf, t, slot);
         constexpr int WN = HALF ? P::VALS / 2 : P::VALS;
-        if (valid) {
-            // term through conj(R[k,n]): acc[n] += G_R[k,n] s[n-k]
+        // term through conj(R[k,n]): acc[n] += G_R[k,n] s[n-k]
+        auto scatter_a = [&]() {
+            if (!valid) return;
             sfor<0, WN>([&](auto w) {
                 const int n = t + P::TPR * decltype(w)::value;
                 if ((unsigned)(n - k) < (unsigned)(p.N - k)) {
@@ -299,10 +308,10 @@ __global__ void __launch_bounds__(kThreads, 1) af_backward_kernel(AfParams p) {
                     acc[n] = cadd(a, cmul(v[w], s_sm[n - k]));
                 }
             });
-        }
-        row_sync<P::TPR>(slot);
-        if (valid) {
-            // term through R[k,n]: acc[n-k] += conj(G_R[k,n]) s[n]
+        };
+        // term through R[k,n]: acc[n-k] += conj(G_R[k,n]) s[n]
+        auto scatter_b = [&]() {
+            if (!valid) return;
             sfor<0, WN>([&](auto w) {
                 const int n = t + P::TPR * decltype(w)::value;
                 if ((unsigned)(n - k) < (unsigned)(p.N - k)) {
@@ -310,8 +319,22 @@ __global__ void __launch_bounds__(kThreads, 1) af_backward_kernel(AfParams p) {
                     acc[n - k] = cadd(a, cmulc(s_sm[n], v[w]));
                 }
             });
+        };
+        if (turns == 1) {
+            scatter_a();
+            row_sync<P::TPR>(slot);
+            scatter_b();
+            row_sync<P::TPR>(slot);
+        } else {
+            for (int tt = 0; tt < turns; ++tt) {
+                if (tt == my_turn) scatter_a();
+                __syncthreads();
+            }
+            for (int tt = 0; tt < turns; ++tt) {
+                if (tt == my_turn) scatter_b();
+                __syncthreads();
+            }
         }
-        row_sync<P::TPR>(slot);
     }
     // per-CTA sum of c a2 (fixed order: warp xor tree, then warps in order)
 #pragma unroll
@@ -326,7 +349,7 @@ __global__ void __launch_bounds__(kThreads, 1) af_backward_kernel(AfParams p) {
     float2* out = p.gpart + ((size_t)b * p.tiles + tile) * p.N;
     for (int n = tid; n < p.N; n += kThreads) {
         float2 a = acc_all[n];
-        for (int s = 1; s < SLOTS; ++s) a = cadd(a, acc_all[(size_t)s * p.N + n]);
+        for (int s = 1; s < p.acc_copies; ++s) a = cadd(a, acc_all[(size_t)s * p.N + n]);
         out[n] = a;
     }
 }
@@ -357,7 +380,8 @@ cudaError_t run_loss_m(const AfParams& p, cudaStream_t st) {
 }
 template <int M>
 cudaError_t run_backward_m(const AfParams& p, cudaStream_t st) {
-    const size_t smem = backward_smem<M>(p.N);
+    if (p.acc_copies < 1 || (256 / RowPlan<M>::TPR) % p.acc_copies) return cudaErrorInvalidConfiguration;
+    const size_t smem = backward_smem<M>(p.N, p.acc_copies);
     if (2 * p.N <= M) return launch_rows(af_backward_kernel<M, true>, smem, p, st);
     return launch_rows(af_backward_kernel<M, false>, smem, p, st);
 }

@@ -54,13 +54,13 @@ graf_status_t cuda_status(cudaError_t e) { return e == cudaSuccess ? GRAF_OK : G
 
 size_t loss_ws(int32_t B, const Tiling& T) { return align256((size_t)B * T.tiles * sizeof(float4)); }
 // backward workspace: gradient partials [B][tiles][N] complex64 | per-CTA
-// sums [B][tiles] float | per-waveform FP64 sums [B]
+// sums [B][tiles] float | per-waveform FP64 sums [B][2]
 size_t gpart_bytes(int32_t B, int32_t N, const Tiling& T) {
     return align256((size_t)B * T.tiles * N * sizeof(float2));
 }
 size_t csum_bytes(int32_t B, const Tiling& T) { return align256((size_t)B * T.tiles * sizeof(float)); }
 size_t backward_ws(int32_t B, int32_t N, const Tiling& T) {
-    return gpart_bytes(B, N, T) + csum_bytes(B, T) + align256((size_t)B * sizeof(double));
+    return gpart_bytes(B, N, T) + csum_bytes(B, T) + align256((size_t)2 * B * sizeof(double));
 }
 
 graf_status_t check_common(const void* x, graf_input_t kind, int32_t B, int32_t N, int32_t M,
@@ -97,6 +97,7 @@ graf_status_t graf_af_forward(const void* x, graf_input_t kind, int32_t B, int32
     graf_status_t s = check_common(x, kind, B, N, M, w);
     if (s != GRAF_OK) return s;
     if (!af_out || !(eps >= 0.0f) || eps > 1e30f) return GRAF_ERR_INVALID_ARG;
+    if (graf::row_kernel_smem(M, N, 0) > graf::kMaxSmem) return GRAF_ERR_UNSUPPORTED;
     const Tiling T = graf::make_tiling(B, M, w.k_lo, w.k_hi);
     AfParams p = base_params(x, kind, B, N, M, w, T);
     p.eps = eps;
@@ -116,6 +117,7 @@ graf_status_t graf_af_loss(const void* x, graf_input_t kind, int32_t B, int32_t 
     if (s != GRAF_OK) return s;
     if ((s = check_loss(l)) != GRAF_OK) return s;
     if (!out8) return GRAF_ERR_INVALID_ARG;
+    if (graf::row_kernel_smem(M, N, 0) > graf::kMaxSmem) return GRAF_ERR_UNSUPPORTED;
     const Tiling T = graf::make_tiling(B, M, w.k_lo, w.k_hi);
     if (!workspace || workspace_bytes < loss_ws(B, T)) return GRAF_ERR_WORKSPACE;
     if (reinterpret_cast<uintptr_t>(workspace) & 255) return GRAF_ERR_WORKSPACE;
@@ -152,6 +154,9 @@ graf_status_t graf_af_backward(const void* x, graf_input_t kind, int32_t B, int3
     p.gpart = reinterpret_cast<float2*>(ws);
     p.csum = reinterpret_cast<float*>(ws + gpart_bytes(B, N, T));
     p.usum = reinterpret_cast<double*>(ws + gpart_bytes(B, N, T) + csum_bytes(B, T));
+    p.phase_only = (kind == GRAF_IN_PHASE && grad_s == nullptr) ? 1 : 0;
+    p.acc_copies = graf::acc_copies_for(M, N);
+    if (p.acc_copies < 1) return GRAF_ERR_UNSUPPORTED;
     return cuda_status(graf::run_backward(p, dL, reinterpret_cast<float2*>(grad_s), grad_phi,
                                           static_cast<cudaStream_t>(stream)));
 }

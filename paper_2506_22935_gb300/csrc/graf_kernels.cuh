@@ -29,8 +29,19 @@ struct AfParams {
     const float* saved8;   // backward: [B][8]
     float2* gpart;         // backward: per-CTA partial dL/ds* [B][tiles][N]
     float* csum;           // backward: per-CTA sum of c a2 [B][tiles]
-    double* usum;          // backward (grad_s): per-waveform sum_k w_b(k) (C[k] + eps) [B]
+    double* usum;          // backward (grad_s): per waveform {sum_k w_b(k) (C[k] + eps), E} [B][2]
+    int phase_only;        // backward: only dL/dphi is wanted (row k = 0 contributes nothing)
+    int acc_copies;        // backward: gradient accumulators per CTA (divides the slot count)
 };
+
+// Base weight w_b(k) of transformed row k >= 0 (see the backward kernel): the
+// weight every Doppler bin of rows k and -k carries when the window spans all
+// bins, unless the mainlobe box takes half the row or more; otherwise 0.
+__host__ __device__ inline int base_weight(const AfParams& p, int k) {
+    if (!p.full_m) return 0;
+    if (k <= p.k_ml && 2 * p.m_ml + 1 > p.M / 2) return 0;
+    return ((k >= p.k_lo && k <= p.k_hi) ? 1 : 0) + ((k > 0 && -k >= p.k_lo && -k <= p.k_hi) ? 1 : 0);
+}
 
 // Row range and tiling shared by the host code (workspace sizes) and launches.
 struct Tiling {
@@ -57,12 +68,21 @@ constexpr size_t forward_smem(int N) {
     return smem_signal_bytes<M>(N) + row_buffer_bytes<M>() + kRedBytes;
 }
 template <int M>
-constexpr size_t backward_smem(int N) {
+constexpr size_t backward_smem(int N, int acc_copies) {
     return smem_signal_bytes<M>(N) + row_buffer_bytes<M>() +
-           ((((size_t)(256 / RowPlan<M>::TPR)) * N * sizeof(float2) + 255) & ~(size_t)255) + kRedBytes;
+           (((size_t)acc_copies * N * sizeof(float2) + 255) & ~(size_t)255) + kRedBytes;
+}
+// Largest power-of-two number of gradient accumulators (<= slots) that fits
+// in shared memory; 0 if even one does not.
+template <int M>
+int backward_acc_copies(int N) {
+    for (int a = 256 / RowPlan<M>::TPR; a >= 1; a /= 2)
+        if (backward_smem<M>(N, a) <= kMaxSmem) return a;
+    return 0;
 }
 
 size_t row_kernel_smem(int M, int N, int which);  // which: 0 forward/loss, 2 backward
+int acc_copies_for(int M, int N);                  // backward accumulators, 0 = unsupported
 template <int M> cudaError_t run_forward_m(const AfParams& p, cudaStream_t st);
 template <int M> cudaError_t run_loss_m(const AfParams& p, cudaStream_t st);
 template <int M> cudaError_t run_backward_m(const AfParams& p, cudaStream_t st);
