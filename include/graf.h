@@ -163,6 +163,32 @@ GRAF_API graf_status_t graf_af_loss_backward(const void* x, graf_input_t kind, i
                                     const float* dL, graf_c32* grad_s, float* grad_phi,
                                     void* workspace, size_t workspace_bytes, void* stream);
 
+/*
+ * graf_af_loss_backward_noalloc - graf_af_loss_backward without a caller
+ * workspace, for callers that cannot allocate device memory (a processing
+ * loop whose memory map is fixed at start-up, a host framework whose pool
+ * owns all device memory and lends none to plug-ins, code that cannot take
+ * cudaMalloc's device synchronisation).  The paper has no counterpart: it is
+ * an integration aid of this library.
+ *   Arguments and results as graf_af_loss_backward, minus the workspace.
+ *   Scratch: a fixed device array of GRAF_NOALLOC_SCRATCH_BYTES (64 MiB)
+ *   inside the library, present on every GPU that loads it until the process
+ *   exits.  A shape whose graf_af_backward_workspace_bytes() exceeds it
+ *   returns GRAF_ERR_WORKSPACE; invalid arguments return
+ *   GRAF_ERR_INVALID_ARG.  Nothing is allocated or freed.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   All calls share the one array and it keeps the last call's contents:
+ *   calls that can overlap on the GPU (different streams, or several host
+ *   threads) race on it and must be serialised by the caller.
+ */
+#define GRAF_NOALLOC_SCRATCH_BYTES (64u << 20)
+GRAF_API graf_status_t graf_af_loss_backward_noalloc(const void* x, graf_input_t kind, int32_t B,
+                                                     int32_t N, int32_t M, graf_window_t w,
+                                                     graf_loss_t l, float* out8, const float* dL,
+                                                     graf_c32* grad_s, float* grad_phi, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -67,6 +67,8 @@ _SIGS = {
                                         _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "graf_af_loss_backward": (ctypes.c_int, [_vp, ctypes.c_int, _i32, _i32, _i32, graf_window_t,
                                              graf_loss_t, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "graf_af_loss_backward_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, _i32, _i32, _i32, graf_window_t,
+                                                     graf_loss_t, _vp, _vp, _vp, _vp, _vp]),
 }
 
 EXPORTED = tuple(_SIGS)
@@ -125,6 +127,13 @@ def graf_af_loss_backward(x, kind, B, N, M, w, l, out8, dL, grad_s, grad_phi, wo
                           stream) -> int:
     return load().graf_af_loss_backward(x, kind, B, N, M, w, l, out8, dL, grad_s, grad_phi, workspace,
                                         workspace_bytes, stream)
+
+
+def graf_af_loss_backward_noalloc(x, kind, B, N, M, w, l, out8, dL, grad_s, grad_phi, stream) -> int:
+    """graf_af_loss_backward on the library's fixed scratch array (no workspace
+    argument, nothing allocated): for callers that cannot allocate device
+    memory.  Calls that may overlap on the GPU must be serialised."""
+    return load().graf_af_loss_backward_noalloc(x, kind, B, N, M, w, l, out8, dL, grad_s, grad_phi, stream)
 
 
 # ---------------------------------------------------------------- helpers
