@@ -61,13 +61,14 @@ __global__ void loss_finalize_kernel(AfParams p, float* out8) {
             T += t2 * f;
         }
     }
+    double psl_soft = 0.0;
     if (lane == 0) {
         float* o = out8 + (size_t)b * 8;
         const double cnt = (double)omega_count(p);
         if (mx == -CUDART_INF || z <= 0.0) {
             o[0] = 0.0f; o[1] = 0.0f; o[2] = 0.0f; o[3] = 0.0f; o[6] = 0.0f;
         } else {
-            const double psl_soft = mx + log(z) / beta;
+            psl_soft = mx + log(z) / beta;
             o[0] = (float)(p.w_psl * psl_soft + p.w_isl * isl);
             o[1] = (float)psl_soft;
             o[2] = (float)isl;
@@ -76,6 +77,18 @@ __global__ void loss_finalize_kernel(AfParams p, float* out8) {
         }
         o[5] = (float)cnt;
         o[7] = 0.0f;
+    }
+    // fused loss + gradient: per-CTA factor that turns a partial accumulated
+    // with the CTA's shift mx_cta into the true remainder, exp(beta (mx_cta -
+    // PSL_soft)) on the PSL path, 1 on the ISL-only path
+    if (p.scale) {
+        psl_soft = __shfl_sync(0xffffffffu, psl_soft, 0);
+        for (int i = lane; i < p.tiles; i += 32) {
+            const float m = p.rec[(size_t)b * p.tiles + i].y;
+            float f = 1.0f;
+            if (p.w_psl != 0.0f) f = m > -CUDART_INF_F ? (float)exp(beta * ((double)m - psl_soft)) : 0.0f;
+            p.scale[(size_t)b * p.tiles + i] = f;
+        }
     }
 }
 
@@ -88,17 +101,39 @@ __device__ __forceinline__ float2 signal_at(const AfParams& p, int b, int n) {
     return static_cast<const float2*>(p.x)[(size_t)b * p.N + n];
 }
 
-// dL/ds* of the FFT part = sum over tiles (fixed order).  grad_phi =
-// 2 Im(dL/ds* conj(s)): the row-uniform part and the energy terms are s[n]
-// times real numbers and contribute nothing to it.
+// dL/ds* of the FFT part: scaled sum of the per-CTA partials of the first
+// set plus the unscaled second set (deferred rows), in a fixed order; the
+// same for the per-CTA sums of c a2.
+__device__ __forceinline__ float2 sum_partials(const AfParams& p, int b, int n, double* cs) {
+    const float2* g1 = p.gpart + (size_t)b * p.tiles * p.N + n;
+    float2 g = make_float2(0.0f, 0.0f);
+    double c = 0.0;
+    for (int i = 0; i < p.tiles; ++i) {
+        const float f = p.scale ? p.scale[(size_t)b * p.tiles + i] : 1.0f;
+        const float2 a = g1[(size_t)i * p.N];
+        g.x = fmaf(f, a.x, g.x);
+        g.y = fmaf(f, a.y, g.y);
+        if (cs) c += (double)f * p.csum[(size_t)b * p.tiles + i];
+    }
+    if (p.gpart2) {
+        const float2* g2 = p.gpart2 + (size_t)b * p.tiles2 * p.N + n;
+        for (int i = 0; i < p.tiles2; ++i) {
+            g = cadd(g, g2[(size_t)i * p.N]);
+            if (cs) c += p.csum2[(size_t)b * p.tiles2 + i];
+        }
+    }
+    if (cs) *cs = c;
+    return g;
+}
+
+// grad_phi = 2 Im(dL/ds* conj(s)): the row-uniform part and the energy terms
+// are s[n] times real numbers and contribute nothing to it.
 __global__ void grad_phi_kernel(AfParams p, const float* dL, float* grad_phi) {
     const int nblk = (p.N + blockDim.x - 1) / blockDim.x;
     const int b = blockIdx.x / nblk;
     const int n = (blockIdx.x % nblk) * blockDim.x + threadIdx.x;
     if (n >= p.N) return;
-    const float2* gp = p.gpart + (size_t)b * p.tiles * p.N + n;
-    float2 g = gp[0];
-    for (int i = 1; i < p.tiles; ++i) g = cadd(g, gp[(size_t)i * p.N]);
+    const float2 g = sum_partials(p, b, n, nullptr);
     const float2 s = signal_at(p, b, n);
     const float scale = 2.0f * (dL ? dL[b] : 1.0f);
     grad_phi[(size_t)b * p.N + n] = scale * (g.y * s.x - g.x * s.y);
@@ -166,16 +201,13 @@ __global__ void grad_s_kernel(AfParams p, const float* dL, float2* grad_s, float
     __syncthreads();
     const int n = n0 + threadIdx.x;
     if (n >= p.N) return;
-    const float2* gp = p.gpart + (size_t)b * p.tiles * p.N + n;
-    float2 g = gp[0];
-    for (int i = 1; i < p.tiles; ++i) g = cadd(g, gp[(size_t)i * p.N]);
     double cs = 0.0;
-    for (int i = 0; i < p.tiles; ++i) cs += p.csum[(size_t)b * p.tiles + i];
+    const float2 g = sum_partials(p, b, n, &cs);
     const float2 s = signal_at(p, b, n);
     const float* sv = p.saved8 + (size_t)b * 8;
     const double E = p.usum[2 * b + 1];
     const float bl2 = p.beta * 1.4426950408889634f;
-    const float p0 = exp2f(-(sv[1] * bl2));
+    const float p0 = ex2a(-(sv[1] * bl2));
     const double Ap = (double)fmaf(p.w_psl, p0, p.w_isl);
     double corr = 0.0;
     for (int k = p.r_lo; k <= p.r_hi; ++k) {
@@ -285,10 +317,31 @@ cudaError_t run_loss(const AfParams& p, cudaStream_t st) {
         default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
-    const int wpb = 4;
-    loss_finalize_kernel<<<(p.B + wpb - 1) / wpb, 32 * wpb, 0, st>>>(p, p.out8);
+    return run_finalize(p, st);
+}
+cudaError_t run_grad_reduce(const AfParams& p, const float* dL, float2* grad_s, float* grad_phi,
+                            cudaStream_t st) {
+    cudaError_t e;
+    const long long grid = (long long)((p.N + 255) / 256) * p.B;
+    if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    if (!grad_s) {
+        grad_phi_kernel<<<(unsigned)grid, 256, 0, st>>>(p, dL, grad_phi);
+        return cudaGetLastError();
+    }
+    const size_t sm = (size_t)p.N * sizeof(double);
+    if (sm > 48 * 1024) {
+        e = cudaFuncSetAttribute(uniform_sum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(grad_s_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    uniform_sum_kernel<<<p.B, 256, sm, st>>>(p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    grad_s_kernel<<<(unsigned)grid, 256, sm, st>>>(p, dL, grad_s, grad_phi);
     return cudaGetLastError();
 }
+
 cudaError_t run_backward(const AfParams& p, const float* dL, float2* grad_s, float* grad_phi,
                          cudaStream_t st) {
     cudaError_t e;
@@ -307,24 +360,15 @@ cudaError_t run_backward(const AfParams& p, const float* dL, float2* grad_s, flo
         case 16384: e = run_backward_m<16384>(p, st); break;
         default: return cudaErrorInvalidValue;
     }
-    if (e != cudaSuccess) return e;
-    const long long grid = (long long)((p.N + 255) / 256) * p.B;
-    if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    if (!grad_s) {
-        grad_phi_kernel<<<(unsigned)grid, 256, 0, st>>>(p, dL, grad_phi);
-        return cudaGetLastError();
-    }
-    const size_t sm = (size_t)p.N * sizeof(double);
-    if (sm > 48 * 1024) {
-        e = cudaFuncSetAttribute(uniform_sum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(grad_s_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-    }
-    uniform_sum_kernel<<<p.B, 256, sm, st>>>(p);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    grad_s_kernel<<<(unsigned)grid, 256, sm, st>>>(p, dL, grad_s, grad_phi);
+    if (e != cudaSuccess || !(grad_s || grad_phi)) return e;
+    return run_grad_reduce(p, dL, grad_s, grad_phi, st);
+}
+
+cudaError_t run_fused(const AfParams& p, cudaStream_t st) { GRAF_DISPATCH_M(run_fused_m, p.M, p, st) }
+
+cudaError_t run_finalize(const AfParams& p, cudaStream_t st) {
+    const int wpb = 4;
+    loss_finalize_kernel<<<(p.B + wpb - 1) / wpb, 32 * wpb, 0, st>>>(p, p.out8);
     return cudaGetLastError();
 }
 

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kThreads, 1) af_forward_kernel(AfParams p) {
 // Per CTA one record {ISL, mx, sum, T} -> workspace.
 __device__ __forceinline__ void lse_rescale(float& mx, float& sum, float& T, float new_mx, float bl2) {
     if (new_mx > mx) {
-        const float f = exp2f((mx - new_mx) * bl2);
+        const float f = ex2a((mx - new_mx) * bl2);
         sum *= f;
         T *= f;
         mx = new_mx;
@@ -114,12 +114,12 @@ __device__ __forceinline__ void lse_merge(float& isl, float& mx, float& sum, flo
                                           float mx2, float sum2, float T2, float bl2) {
     isl += isl2;
     if (mx2 > mx) {
-        const float f = exp2f((mx - mx2) * bl2);
+        const float f = ex2a((mx - mx2) * bl2);
         sum = sum * f + sum2;
         T = T * f + T2;
         mx = mx2;
     } else if (mx2 > -CUDART_INF_F) {
-        const float f = exp2f((mx2 - mx) * bl2);
+        const float f = ex2a((mx2 - mx) * bl2);
         sum += sum2 * f;
         T += T2 * f;
     }
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(kThreads, 1) af_loss_kernel(AfParams p) {
         const float sh = mx * bl2;
         sfor<0, P::VALS>([&](auto w) {
             const float a2 = v[w].x, wt = v[w].y;
-            const float e = wt * exp2f(fmaf(a2, bl2, -sh));
+            const float e = wt * ex2a(fmaf(a2, bl2, -sh));
             sum += e;
             T = fmaf(e, a2, T);
         });
@@ -231,6 +231,78 @@ __global__ void __launch_bounds__(kThreads, 1) af_loss_kernel(AfParams p) {
 // from vanishing next to the ISL weight in FP32, and avoids summing the
 // ISL gradient of full rows (zero for unit modulus, by Parseval) from large
 // cancelling parts.  Per CTA the kernel also sums c a2 for the energy term.
+// Scatter both Wirtinger terms of R[k,n] = s[n] conj(s[n-k]) for row k from
+// G_R (in v, natural strided layout) into the slot's accumulator:
+//   acc[n]   += G_R[n] s[n-k]     (through conj(R), which carries s*[n])
+//   acc[n-k] += conj(G_R[n]) s[n]  (through R, which carries s*[n-k])
+// in two phases so no two threads of a row update one address at once.
+// Slots that share an accumulator (turns > 1) take turns, CTA-wide.
+template <int M, bool HALF>
+__device__ __forceinline__ void scatter_row(const float2* v, float2* acc, const float2* s_sm, int N,
+                                            int k, int t, bool active, int slot, int turns,
+                                            int my_turn) {
+    using P = RowPlan<M>;
+    constexpr int WN = HALF ? P::VALS / 2 : P::VALS;
+    auto scatter_a = [&]() {
+        if (!active) return;
+        sfor<0, WN>([&](auto w) {
+            const int n = t + P::TPR * decltype(w)::value;
+            if ((unsigned)(n - k) < (unsigned)(N - k)) {
+                const float2 a = acc[n];
+                acc[n] = cadd(a, cmul(v[w], s_sm[n - k]));
+            }
+        });
+    };
+    auto scatter_b = [&]() {
+        if (!active) return;
+        sfor<0, WN>([&](auto w) {
+            const int n = t + P::TPR * decltype(w)::value;
+            if ((unsigned)(n - k) < (unsigned)(N - k)) {
+                const float2 a = acc[n - k];
+                acc[n - k] = cadd(a, cmulc(s_sm[n], v[w]));
+            }
+        });
+    };
+    if (turns == 1) {
+        scatter_a();
+        row_sync<P::TPR>(slot);
+        scatter_b();
+        row_sync<P::TPR>(slot);
+    } else {
+        for (int tt = 0; tt < turns; ++tt) {
+            if (tt == my_turn) scatter_a();
+            __syncthreads();
+        }
+        for (int tt = 0; tt < turns; ++tt) {
+            if (tt == my_turn) scatter_b();
+            __syncthreads();
+        }
+    }
+}
+
+// Per-CTA partial sums of the gradient accumulators and one scalar, in a
+// fixed order (warp xor tree, then warps in order).
+template <int M>
+__device__ __forceinline__ void write_grad_partial(const AfParams& p, const float2* acc_all, float* red,
+                                                   float cs, int b, int tile) {
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
+    if ((tid & 31) == 0) red[tid >> 5] = cs;
+    __syncthreads();
+    if (tid == 0) {
+        float s = red[0];
+        for (int w = 1; w < kThreads / 32; ++w) s += red[w];
+        p.csum[(size_t)b * p.tiles + tile] = s;
+    }
+    float2* out = p.gpart + ((size_t)b * p.tiles + tile) * p.N;
+    for (int n = tid; n < p.N; n += kThreads) {
+        float2 a = acc_all[n];
+        for (int s = 1; s < p.acc_copies; ++s) a = cadd(a, acc_all[(size_t)s * p.N + n]);
+        out[n] = a;
+    }
+}
+
 template <int M, bool HALF>
 __global__ void __launch_bounds__(kThreads, 1) af_backward_kernel(AfParams p) {
     using P = RowPlan<M>;
@@ -251,7 +323,7 @@ __global__ void __launch_bounds__(kThreads, 1) af_backward_kernel(AfParams p) {
     const float bl2 = p.beta * 1.4426950408889634f;
     const float psl_soft = p.saved8[(size_t)b * 8 + 1];
     const float sh = psl_soft * bl2;
-    const float p0 = exp2f(-sh);
+    const float p0 = ex2a(-sh);
     const float cA = fmaf(p.w_psl, p0, p.w_isl) * invE2;  // A' / E^2
     const float cP = p.w_psl * invE2;
     float csum = 0.0f;
@@ -283,7 +355,7 @@ __global__ void __launch_bounds__(kThreads, 1) af_backward_kernel(AfParams p) {
             const float2 x = v[w];
             const float a2 = fmaf(fmaf(x.x, x.x, x.y * x.y), invE2, eps_n);
             const float wt = (uniform || !valid) ? wrow : mweight<decltype(w)::value>(rmk);
-            const float pr = exp2f(fmaf(a2, bl2, -sh));
+            const float pr = ex2a(fmaf(a2, bl2, -sh));
             const float cpsl = wt > 0.0f ? wt * cP * (pr - p0) : 0.0f;
             float c = fmaf(wt - wb, cA, cpsl);
             // the origin X[0,0] = E: its scatter (2 E c s) and energy term
@@ -297,61 +369,160 @@ __global__ void __launch_bounds__(kThreads, 1) af_backward_kernel(AfParams p) {
         });
         row_sync<P::TPR>(slot);  // buffer reads of the forward transform are done
         row_fft<M, true, false, HALF>(v, buf, t, slot);
-        constexpr int WN = HALF ? P::VALS / 2 : P::VALS;
-        // term through conj(R[k,n]): acc[n] += G_R[k,n] s[n-k]
-        auto scatter_a = [&]() {
-            if (!valid) return;
-            sfor<0, WN>([&](auto w) {
-                const int n = t + P::TPR * decltype(w)::value;
-                if ((unsigned)(n - k) < (unsigned)(p.N - k)) {
-                    const float2 a = acc[n];
-                    acc[n] = cadd(a, cmul(v[w], s_sm[n - k]));
-                }
-            });
-        };
-        // term through R[k,n]: acc[n-k] += conj(G_R[k,n]) s[n]
-        auto scatter_b = [&]() {
-            if (!valid) return;
-            sfor<0, WN>([&](auto w) {
-                const int n = t + P::TPR * decltype(w)::value;
-                if ((unsigned)(n - k) < (unsigned)(p.N - k)) {
-                    const float2 a = acc[n - k];
-                    acc[n - k] = cadd(a, cmulc(s_sm[n], v[w]));
-                }
-            });
-        };
-        if (turns == 1) {
-            scatter_a();
-            row_sync<P::TPR>(slot);
-            scatter_b();
-            row_sync<P::TPR>(slot);
-        } else {
-            for (int tt = 0; tt < turns; ++tt) {
-                if (tt == my_turn) scatter_a();
-                __syncthreads();
-            }
-            for (int tt = 0; tt < turns; ++tt) {
-                if (tt == my_turn) scatter_b();
-                __syncthreads();
-            }
-        }
+        scatter_row<M, HALF>(v, acc, s_sm, p.N, k, t, valid, slot, turns, my_turn);
     }
-    // per-CTA sum of c a2 (fixed order: warp xor tree, then warps in order)
+    write_grad_partial<M>(p, acc_all, red, csum, b, tile);
+}
+
+// ---------------------------------------------------------- fused loss + gradient
+// One pass per row: lag product, forward DFT, loss partials and, for rows
+// whose weights are uniform over the row, the gradient remainder of the split
+// adjoint (see af_backward_kernel) -- no recomputation, no stored AF.
+//
+// The PSL term needs p - p0 = (exp(beta a2) - 1) / Z with Z = sum_Omega
+// exp(beta Ahat^2) unknown until every row is done.  The kernel keeps a
+// CTA-uniform log-sum-exp shift mx (the largest weighted a2 seen so far),
+// forms c = w (e - e0) w_psl / E^2 with e = exp(beta (a2 - mx)), e0 =
+// exp(-beta mx), and when mx grows rescales everything accumulated so far
+// by exp(beta (mx_old - mx_new)).  The finalisation then gives each CTA the
+// factor exp(beta (mx_cta - PSL_soft)) that turns its partial into the true
+// remainder.  With w_psl = 0 the remainder is c = (w - w_b) w_isl / E^2,
+// independent of the shift, and every row is fused.
+//
+// Rows r_lo..defer_hi (those holding mainlobe-box cells, whose weights are
+// not uniform) contribute loss partials only; af_backward_kernel adds their
+// gradient once PSL_soft is known.
+template <int M, bool HALF>
+__global__ void __launch_bounds__(kThreads, 1) af_fused_kernel(AfParams p) {
+    using P = RowPlan<M>;
+    constexpr int SLOTS = kThreads / P::TPR;
+    constexpr int NW = kThreads / 32;
+    extern __shared__ __align__(256) unsigned char smem[];
+    float2* s_sm = reinterpret_cast<float2*>(smem);
+    float2* bufs = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(p.N));
+    float2* acc_all = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(p.N) + row_buffer_bytes<M>());
+    float* red = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(acc_all) +
+                                          (((size_t)p.acc_copies * p.N * sizeof(float2) + 255) & ~(size_t)255));
+    float* red_max = red + 64;  // [2][NW], double-buffered by row iteration
+
+    const int tid = threadIdx.x, slot = tid / P::TPR, t = tid % P::TPR;
+    const int b = blockIdx.x / p.tiles, tile = blockIdx.x % p.tiles;
+    for (int i = tid; i < p.acc_copies * p.N; i += kThreads) acc_all[i] = make_float2(0.0f, 0.0f);
+    const float E = load_signal(p, b, s_sm, red);  // includes __syncthreads
+    if (tile == 0 && tid == 0) p.out8[(size_t)b * 8 + 4] = E;
+    const float invE2 = 1.0f / (E * E);
+    const float eps_n = p.eps * invE2;
+    const float bl2 = p.beta * 1.4426950408889634f;  // beta * log2(e)
+    const bool psl_mode = p.w_psl != 0.0f;
+    const float cP = p.w_psl * invE2;
+    const float cI = p.w_isl * invE2;
+    float2* buf = bufs + (size_t)slot * (P::SPLIT ? P::SMEM_ROW / 2 : P::SMEM_ROW);
+    const ColMasks cm = col_masks<M>(p, t);
+    constexpr unsigned long long full_mask = P::VALS == 64 ? ~0ull : ((1ull << P::VALS) - 1ull);
+    const int turns = SLOTS / p.acc_copies;
+    const int my_turn = slot / p.acc_copies;
+    float2* acc = acc_all + (size_t)(slot % p.acc_copies) * p.N;
+
+    const int row0 = p.r_lo + tile * p.rows_per_tile;
+    const int row_end = min(row0 + p.rows_per_tile, p.r_hi + 1);
+    const int iters = (p.rows_per_tile + SLOTS - 1) / SLOTS;
+
+    float isl = 0.0f, zs = 0.0f, ts = 0.0f, cs = 0.0f;
+    float mx = -CUDART_INF_F;  // CTA-uniform shift (in a2 units)
+    float2 v[P::VALS];
+    for (int it = 0; it < iters; ++it) {
+        const int k = row0 + slot + it * SLOTS;
+        const bool valid = k < row_end;
+        const bool grad_row = valid && k > p.defer_hi && !(p.phase_only && k == 0);
+        build_lag_row<M, HALF>(v, s_sm, p.N, k, t, valid);
+        row_sync<P::TPR>(slot);
+        row_fft<M, false, HALF, false>(v, buf, t, slot);
+        const RowMasks rmk = row_masks(p, cm, k);
+        const bool uniform = !valid || (rmk.one == full_mask && (rmk.two == 0ull || rmk.two == full_mask));
+        const float wrow = valid ? (rmk.two != 0ull ? 2.0f : (rmk.one != 0ull ? 1.0f : 0.0f)) : 0.0f;
+        const float wb = valid ? (float)base_weight(p, k) : 0.0f;
+        // pass 1: largest weighted a2 of this thread, then of the CTA
+        float tmx = -CUDART_INF_F;
+        sfor<0, P::VALS>([&](auto w) {
+            const float2 x = v[w];
+            const float a2 = fmaf(fmaf(x.x, x.x, x.y * x.y), invE2, eps_n);
+            const float wt = uniform ? wrow : mweight<decltype(w)::value>(rmk);
+            tmx = fmaxf(tmx, wt > 0.0f ? a2 : -CUDART_INF_F);
+        });
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) csum += __shfl_xor_sync(0xffffffffu, csum, o);
-    if ((tid & 31) == 0) red[tid >> 5] = csum;
+        for (int o = 16; o > 0; o >>= 1) tmx = fmaxf(tmx, __shfl_xor_sync(0xffffffffu, tmx, o));
+        float* rm = red_max + (it & 1) * NW;
+        if ((tid & 31) == 0) rm[tid >> 5] = tmx;
+        __syncthreads();
+        float cmx = rm[0];
+#pragma unroll
+        for (int w = 1; w < NW; ++w) cmx = fmaxf(cmx, rm[w]);
+        if (cmx > mx) {  // CTA-uniform
+            const float f = ex2a((mx - cmx) * bl2);  // 0 while mx = -inf
+            zs *= f;
+            ts *= f;
+            if (psl_mode) {
+                cs *= f;
+                if (mx > -CUDART_INF_F) {
+                    for (int i = tid; i < p.acc_copies * p.N; i += kThreads) {
+                        const float2 a = acc_all[i];
+                        acc_all[i] = make_float2(a.x * f, a.y * f);
+                    }
+                    __syncthreads();
+                }
+            }
+            mx = cmx;
+        }
+        // pass 2: loss partials and the gradient remainder c X
+        const float sh = mx * bl2;
+        const float e0 = ex2a(-sh);
+        float risl = 0.0f;
+        sfor<0, P::VALS>([&](auto w) {
+            const float2 x = v[w];
+            const float a2 = fmaf(fmaf(x.x, x.x, x.y * x.y), invE2, eps_n);
+            const float wt = uniform ? wrow : mweight<decltype(w)::value>(rmk);
+            const float e = wt > 0.0f ? ex2a(fmaf(a2, bl2, -sh)) : 0.0f;
+            const float we = wt * e;
+            risl = fmaf(wt, a2, risl);
+            zs += we;
+            ts = fmaf(we, a2, ts);
+            float c = 0.0f;
+            if (grad_row) c = psl_mode ? wt * (e - e0) * cP : (wt - wb) * cI;
+            cs = fmaf(c, a2, cs);
+            v[w] = make_float2(c * x.x, c * x.y);
+        });
+        isl += risl;
+        if constexpr (P::TPR >= 32) {
+            if (grad_row) {  // slot-uniform: the slot is one or more whole warps
+                row_sync<P::TPR>(slot);
+                row_fft<M, true, false, HALF>(v, buf, t, slot);
+            }
+        } else {
+            row_sync<P::TPR>(slot);
+            row_fft<M, true, false, HALF>(v, buf, t, slot);
+        }
+        scatter_row<M, HALF>(v, acc, s_sm, p.N, k, t, grad_row, slot, turns, my_turn);
+    }
+    // loss record {ISL, mx, sum e, sum e a2} with the CTA-uniform shift: plain sums
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        isl += __shfl_xor_sync(0xffffffffu, isl, o);
+        zs += __shfl_xor_sync(0xffffffffu, zs, o);
+        ts += __shfl_xor_sync(0xffffffffu, ts, o);
+    }
+    float4* wred = reinterpret_cast<float4*>(red + 128);
+    if ((tid & 31) == 0) wred[tid >> 5] = make_float4(isl, mx, zs, ts);
     __syncthreads();
     if (tid == 0) {
-        float s = red[0];
-        for (int w = 1; w < kThreads / 32; ++w) s += red[w];
-        p.csum[(size_t)b * p.tiles + tile] = s;
+        float4 a = wred[0];
+        for (int w = 1; w < NW; ++w) {
+            a.x += wred[w].x;
+            a.z += wred[w].z;
+            a.w += wred[w].w;
+        }
+        p.rec[(size_t)b * p.tiles + tile] = a;
     }
-    float2* out = p.gpart + ((size_t)b * p.tiles + tile) * p.N;
-    for (int n = tid; n < p.N; n += kThreads) {
-        float2 a = acc_all[n];
-        for (int s = 1; s < p.acc_copies; ++s) a = cadd(a, acc_all[(size_t)s * p.N + n]);
-        out[n] = a;
-    }
+    write_grad_partial<M>(p, acc_all, red, cs, b, tile);
 }
 
 // ---------------------------------------------------------- host launchers
@@ -386,9 +557,20 @@ cudaError_t run_backward_m(const AfParams& p, cudaStream_t st) {
     return launch_rows(af_backward_kernel<M, false>, smem, p, st);
 }
 
+// The fused kernel is instantiated without the N <= M/2 pruning: with it the
+// register allocation of the two transforms plus the epilogue spills, without
+// it nothing of note spills, and the pruning saves only ~5% of the butterflies.
+template <int M>
+cudaError_t run_fused_m(const AfParams& p, cudaStream_t st) {
+    if (p.acc_copies < 1 || (256 / RowPlan<M>::TPR) % p.acc_copies) return cudaErrorInvalidConfiguration;
+    const size_t smem = backward_smem<M>(p.N, p.acc_copies);
+    return launch_rows(af_fused_kernel<M, false>, smem, p, st);
+}
+
 }  // namespace graf
 
 #define GRAF_INSTANTIATE_M(M)                                                      \
     template cudaError_t graf::run_forward_m<M>(const graf::AfParams&, cudaStream_t);  \
     template cudaError_t graf::run_loss_m<M>(const graf::AfParams&, cudaStream_t);     \
-    template cudaError_t graf::run_backward_m<M>(const graf::AfParams&, cudaStream_t);
+    template cudaError_t graf::run_backward_m<M>(const graf::AfParams&, cudaStream_t); \
+    template cudaError_t graf::run_fused_m<M>(const graf::AfParams&, cudaStream_t);

@@ -63,6 +63,43 @@ size_t backward_ws(int32_t B, int32_t N, const Tiling& T) {
     return gpart_bytes(B, N, T) + csum_bytes(B, T) + align256((size_t)2 * B * sizeof(double));
 }
 
+// Fused loss + gradient (graf_af_loss_backward).  PSL path: rows holding
+// mainlobe-box cells are deferred to the recomputing backward kernel; the
+// ISL-only path fuses every row.  The PSL path needs a window spanning every
+// Doppler bin (otherwise no row is uniform and the two-kernel path runs).
+struct FusedPlan {
+    bool fused;
+    Tiling T1;           // all transformed rows
+    int defer_hi;        // -1: none
+    bool deferred_launch;
+    Tiling T2;           // deferred rows that need a gradient
+};
+
+FusedPlan fused_plan(int32_t B, int32_t N, int32_t M, const graf_window_t& w, bool psl, bool phase_only) {
+    FusedPlan f{};
+    const bool full_m = (w.m_lo == -(M / 2) && w.m_hi == M / 2 - 1);
+    f.T1 = graf::make_tiling(B, M, w.k_lo, w.k_hi);
+    f.fused = !psl || full_m;
+    f.defer_hi = -1;
+    f.deferred_launch = false;
+    if (f.fused && psl && w.k_ml >= 0 && w.m_ml >= 0 && w.k_ml >= f.T1.r_lo) {
+        f.defer_hi = w.k_ml < f.T1.r_hi ? w.k_ml : f.T1.r_hi;
+        const int lo = (phase_only && f.T1.r_lo == 0) ? 1 : f.T1.r_lo;  // row 0: no phase gradient
+        if (lo <= f.defer_hi) {
+            f.deferred_launch = true;
+            f.T2 = graf::make_tiling_rows(B, M, lo, f.defer_hi);
+        }
+    }
+    (void)N;
+    return f;
+}
+
+size_t fused_ws(int32_t B, int32_t N, const FusedPlan& f) {
+    size_t s = loss_ws(B, f.T1) + csum_bytes(B, f.T1) /* scale */ + csum_bytes(B, f.T1) + gpart_bytes(B, N, f.T1);
+    if (f.deferred_launch) s += gpart_bytes(B, N, f.T2) + csum_bytes(B, f.T2);
+    return s + align256((size_t)2 * B * sizeof(double));
+}
+
 graf_status_t check_common(const void* x, graf_input_t kind, int32_t B, int32_t N, int32_t M,
                            const graf_window_t& w) {
     if (!x) return GRAF_ERR_INVALID_ARG;
@@ -131,8 +168,16 @@ graf_status_t graf_af_loss(const void* x, graf_input_t kind, int32_t B, int32_t 
 size_t graf_af_backward_workspace_bytes(int32_t B, int32_t N, int32_t M, graf_window_t w) {
     if (check_shape(B, N, M) != GRAF_OK || check_window(N, M, w) != GRAF_OK) return 0;
     const Tiling T = graf::make_tiling(B, M, w.k_lo, w.k_hi);
-    const size_t a = loss_ws(B, T), b = backward_ws(B, N, T);
-    return a > b ? a : b;
+    size_t s = loss_ws(B, T);
+    const size_t b = backward_ws(B, N, T);
+    if (b > s) s = b;
+    // the fused path's needs for any loss weights and gradient outputs
+    for (int psl = 0; psl < 2; ++psl)
+        for (int po = 0; po < 2; ++po) {
+            const size_t f = fused_ws(B, N, fused_plan(B, N, M, w, psl != 0, po != 0));
+            if (f > s) s = f;
+        }
+    return s;
 }
 
 graf_status_t graf_af_backward(const void* x, graf_input_t kind, int32_t B, int32_t N, int32_t M,
@@ -170,11 +215,64 @@ graf_status_t graf_af_loss_backward(const void* x, graf_input_t kind, int32_t B,
     if ((s = check_loss(l)) != GRAF_OK) return s;
     if (!out8 || (!grad_s && !grad_phi)) return GRAF_ERR_INVALID_ARG;
     if (grad_phi && kind != GRAF_IN_PHASE) return GRAF_ERR_INVALID_ARG;
-    if (workspace_bytes < graf_af_backward_workspace_bytes(B, N, M, w)) return GRAF_ERR_WORKSPACE;
-    s = graf_af_loss(x, kind, B, N, M, w, l, out8, workspace, workspace_bytes, stream);
-    if (s != GRAF_OK) return s;
-    return graf_af_backward(x, kind, B, N, M, w, l, out8, dL, grad_s, grad_phi, workspace,
-                            workspace_bytes, stream);
+    if (!workspace || workspace_bytes < graf_af_backward_workspace_bytes(B, N, M, w)) return GRAF_ERR_WORKSPACE;
+    if (reinterpret_cast<uintptr_t>(workspace) & 255) return GRAF_ERR_WORKSPACE;
+    const int acc = graf::acc_copies_for(M, N);
+    if (acc < 1) return GRAF_ERR_UNSUPPORTED;
+    const bool phase_only = kind == GRAF_IN_PHASE && grad_s == nullptr;
+    const FusedPlan f = fused_plan(B, N, M, w, l.w_psl != 0.0f, phase_only);
+    if (!f.fused) {
+        s = graf_af_loss(x, kind, B, N, M, w, l, out8, workspace, workspace_bytes, stream);
+        if (s != GRAF_OK) return s;
+        return graf_af_backward(x, kind, B, N, M, w, l, out8, dL, grad_s, grad_phi, workspace,
+                                workspace_bytes, stream);
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned char* ws = static_cast<unsigned char*>(workspace);
+    AfParams p = base_params(x, kind, B, N, M, w, f.T1);
+    p.eps = l.eps; p.beta = l.beta; p.w_psl = l.w_psl; p.w_isl = l.w_isl;
+    p.out8 = out8;
+    p.saved8 = out8;
+    p.phase_only = phase_only ? 1 : 0;
+    p.acc_copies = acc;
+    p.defer_hi = f.defer_hi;
+    p.rec = reinterpret_cast<float4*>(ws);
+    ws += loss_ws(B, f.T1);
+    p.scale = reinterpret_cast<float*>(ws);
+    ws += csum_bytes(B, f.T1);
+    p.csum = reinterpret_cast<float*>(ws);
+    ws += csum_bytes(B, f.T1);
+    p.gpart = reinterpret_cast<float2*>(ws);
+    ws += gpart_bytes(B, N, f.T1);
+    float2* gpart2 = nullptr;
+    float* csum2 = nullptr;
+    if (f.deferred_launch) {
+        gpart2 = reinterpret_cast<float2*>(ws);
+        ws += gpart_bytes(B, N, f.T2);
+        csum2 = reinterpret_cast<float*>(ws);
+        ws += csum_bytes(B, f.T2);
+    }
+    p.usum = reinterpret_cast<double*>(ws);
+    cudaError_t e = graf::run_fused(p, st);
+    if (e == cudaSuccess) e = graf::run_finalize(p, st);
+    if (e == cudaSuccess && f.deferred_launch) {
+        AfParams q = p;
+        q.r_lo = f.T2.r_lo;
+        q.r_hi = f.T2.r_hi;
+        q.rows_per_tile = f.T2.rows_per_tile;
+        q.tiles = f.T2.tiles;
+        q.gpart = gpart2;
+        q.csum = csum2;
+        q.scale = nullptr;
+        q.phase_only = 0;  // its rows all need their gradient
+        e = graf::run_backward(q, nullptr, nullptr, nullptr, st);
+        p.tiles2 = f.T2.tiles;
+        p.gpart2 = gpart2;
+        p.csum2 = csum2;
+    }
+    if (e == cudaSuccess)
+        e = graf::run_grad_reduce(p, dL, reinterpret_cast<float2*>(grad_s), grad_phi, st);
+    return cuda_status(e);
 }
 
 }  // extern "C"

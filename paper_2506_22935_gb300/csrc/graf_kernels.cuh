@@ -32,6 +32,14 @@ struct AfParams {
     double* usum;          // backward (grad_s): per waveform {sum_k w_b(k) (C[k] + eps), E} [B][2]
     int phase_only;        // backward: only dL/dphi is wanted (row k = 0 contributes nothing)
     int acc_copies;        // backward: gradient accumulators per CTA (divides the slot count)
+    // fused loss + gradient
+    int defer_hi;          // rows r_lo..defer_hi get loss partials only (their gradient is
+                           // computed by af_backward_kernel after the loss is known); -1: none
+    float* scale;          // per-CTA gradient scale [B][tiles], written by the loss finalisation
+    // gradient reduction: a second set of partials (deferred rows), unscaled
+    int tiles2;
+    const float2* gpart2;  // [B][tiles2][N]
+    const float* csum2;    // [B][tiles2]
 };
 
 // Base weight w_b(k) of transformed row k >= 0 (see the backward kernel): the
@@ -86,22 +94,22 @@ int acc_copies_for(int M, int N);                  // backward accumulators, 0 =
 template <int M> cudaError_t run_forward_m(const AfParams& p, cudaStream_t st);
 template <int M> cudaError_t run_loss_m(const AfParams& p, cudaStream_t st);
 template <int M> cudaError_t run_backward_m(const AfParams& p, cudaStream_t st);
+template <int M> cudaError_t run_fused_m(const AfParams& p, cudaStream_t st);
+cudaError_t run_fused(const AfParams& p, cudaStream_t st);
+cudaError_t run_finalize(const AfParams& p, cudaStream_t st);
+cudaError_t run_grad_reduce(const AfParams& p, const float* dL, float2* grad_s, float* grad_phi,
+                            cudaStream_t st);
 cudaError_t run_forward(const AfParams& p, cudaStream_t st);
 cudaError_t run_loss(const AfParams& p, cudaStream_t st);
 cudaError_t run_backward(const AfParams& p, const float* dL, float2* grad_s, float* grad_phi,
                          cudaStream_t st);
 
-// Rows k >= 0 whose transform serves the window: row k gives delay k and,
-// by |X[-k,m]| = |X[k,-m]|, delay -k.
-inline Tiling make_tiling(int B, int M, int k_lo, int k_hi) {
+// Tiles of transformed rows [r_lo, r_hi] for B waveforms: rows per CTA a
+// multiple of the slot count, at least 4 CTAs per SM where the batch allows.
+inline Tiling make_tiling_rows(int B, int M, int r_lo, int r_hi) {
     Tiling T;
-    if (k_lo >= 0) {
-        T.r_lo = k_lo; T.r_hi = k_hi;
-    } else if (k_hi <= 0) {
-        T.r_lo = -k_hi; T.r_hi = -k_lo;
-    } else {
-        T.r_lo = 0; T.r_hi = (-k_lo > k_hi) ? -k_lo : k_hi;
-    }
+    T.r_lo = r_lo;
+    T.r_hi = r_hi;
     T.nrows = T.r_hi - T.r_lo + 1;
     T.slots = kThreads / tpr_of(M);
     int rps = 8;
@@ -113,6 +121,21 @@ inline Tiling make_tiling(int B, int M, int k_lo, int k_hi) {
     T.rows_per_tile = T.slots * rps;
     T.tiles = (T.nrows + T.rows_per_tile - 1) / T.rows_per_tile;
     return T;
+}
+
+// Rows k >= 0 whose transform serves the window: row k gives delay k and,
+// by |X[-k,m]| = |X[k,-m]|, delay -k.
+inline Tiling make_tiling(int B, int M, int k_lo, int k_hi) {
+    if (k_lo >= 0) return make_tiling_rows(B, M, k_lo, k_hi);
+    if (k_hi <= 0) return make_tiling_rows(B, M, -k_hi, -k_lo);
+    return make_tiling_rows(B, M, 0, (-k_lo > k_hi) ? -k_lo : k_hi);
+}
+
+// ex2.approx (PTX): 2^x with relative error below 2^-22, +0 at -inf.
+__device__ __forceinline__ float ex2a(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
 // Load s[0..N) of waveform b into shared memory (phases -> exp(j phi)) and

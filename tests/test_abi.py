@@ -72,10 +72,11 @@ def test_workspace_scales_with_batch(lib):
     w = W.full(1024, 2048)
     b1 = g.graf_af_backward_workspace_bytes(1, 1024, 2048, w.c())
     b256 = g.graf_af_backward_workspace_bytes(256, 1024, 2048, w.c())
-    # per-CTA gradient partials B * tiles * N complex64 (1 <= tiles <= rows / 8)
-    # plus per-CTA and per-waveform scalars
-    assert 1024 * 8 <= b1 <= 128 * 1024 * 8 + 4096
-    assert 256 * 1024 * 8 <= b256 <= 256 * 128 * 1024 * 8 + 256 * 128 * 4 + 4096
+    # per-CTA gradient partials B * tiles * N complex64 (1 <= tiles <= rows / 8),
+    # at most twice (rows deferred to the recomputing backward), plus per-CTA
+    # and per-waveform scalars
+    assert 1024 * 8 <= b1 <= 2 * 128 * 1024 * 8 + 65536
+    assert 256 * 1024 * 8 <= b256 <= 2 * 256 * 128 * 1024 * 8 + 256 * 128 * 64
 
 
 FAKE = 0x1000  # never dereferenced: every call below fails its host checks
