@@ -4,8 +4,8 @@ Workload: 256 random polyphase codes (phases i.i.d. uniform on [0, 2 pi),
 seeded), N = 1024, M = 2048, all 2047 delays and 2048 Doppler bins, loss
 PSL_soft (log-sum-exp, beta = 50) + ISL over the AF minus the zero-delay
 mainlobe, forward and Wirtinger backward with respect to the phases, FP32.
-One step = graf_af_loss + graf_af_backward over the batch; metric = AF cells
-per second, cells = B (2N-1) M per step.
+One step = graf_af_loss_backward over the batch (fused loss + gradient);
+metric = AF cells per second, cells = B (2N-1) M per step.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -35,9 +35,7 @@ METRIC = "AF fwd+bwd Gcells/s at N=1024 M=2048"
 UNIT = "Gcells/s"
 WORKLOAD = ("256 random polyphase codes, N=1024, M=2048, all 2047 delays x 2048 Doppler bins, "
             "PSL(log-sum-exp beta=50)+ISL, forward + Wirtinger backward w.r.t. phases")
-CELLS = B * (2 * N - 1) * M
-FLOP_PER_ROW = 5.0 * M * math.log2(M)          # nominal radix-2 count of one M-point FFT
-ALG_FLOP_BWD = B * (2 * N - 1) * FLOP_PER_ROW  # adjoint DFT of every delay row
+FLOP_PER_ROW = 5.0 * M * math.log2(M)  # nominal radix-2 count of one M-point FFT
 SMS, FP32_LANES = 152, 128
 
 
@@ -203,69 +201,61 @@ def run_graf(args):
     torch.cuda.set_device(dev)
     g.load()
 
-    phi_h = inputs.random_phases(SEED + 1000 * rank, B, N)
+    Bb = args.batch
+    cells = Bb * (2 * N - 1) * M
+    phi_h = inputs.random_phases(SEED + 1000 * rank, Bb, N)
     x = torch.from_numpy(phi_h).to(dev)
     w, loss = g.Window.full(N, M), g.Loss(1.0, 1.0, BETA, EPS)
     wc, lc = w.c(), loss.c()
-    nb = g.graf_af_backward_workspace_bytes(B, N, M, wc)
+    nb = g.graf_af_backward_workspace_bytes(Bb, N, M, wc)
     ws = torch.empty(nb, dtype=torch.uint8, device=dev)
-    out8 = torch.empty((B, 8), dtype=torch.float32, device=dev)
-    grad = torch.empty((B, N), dtype=torch.float32, device=dev)
+    out8 = torch.empty((Bb, 8), dtype=torch.float32, device=dev)
+    grad = torch.empty((Bb, N), dtype=torch.float32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 126 MB L2
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
 
-    def loss_call(xp, o8p):
-        st = g.graf_af_loss(xp, g.GRAF_IN_PHASE, B, N, M, wc, lc, o8p, ws.data_ptr(), nb, sp)
+    def step_call(xp, o8p, gp):
+        st = g.graf_af_loss_backward(xp, g.GRAF_IN_PHASE, Bb, N, M, wc, lc, o8p, None, None, gp, ws.data_ptr(),
+                                     nb, sp)
         assert st == 0, g.graf_status_string(st)
 
-    def bwd_call(xp, o8p, gp):
-        st = g.graf_af_backward(xp, g.GRAF_IN_PHASE, B, N, M, wc, lc, o8p, None, None, gp, ws.data_ptr(),
-                                nb, sp)
-        assert st == 0, g.graf_status_string(st)
-
-    launches_per_step = 4  # loss rows, loss finalize, backward rows, gradient reduce
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    launches_per_step = 3  # fused rows, loss finalisation, gradient reduction
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
     with ClockSampler(dev.index) as clk:
         for _ in range(args.warmup):
-            loss_call(x.data_ptr(), out8.data_ptr())
-            bwd_call(x.data_ptr(), out8.data_ptr(), grad.data_ptr())
+            step_call(x.data_ptr(), out8.data_ptr(), grad.data_ptr())
         torch.cuda.synchronize(dev)
         if dist:
             dist.barrier()
         torch.cuda.synchronize(dev)
         for i in range(args.steps):
             flush.zero_()
-            e0, e1, e2 = ev[i]
+            e0, e1 = ev[i]
             e0.record(stream)
-            loss_call(x.data_ptr(), out8.data_ptr())
+            step_call(x.data_ptr(), out8.data_ptr(), grad.data_ptr())
             e1.record(stream)
-            bwd_call(x.data_ptr(), out8.data_ptr(), grad.data_ptr())
-            e2.record(stream)
         torch.cuda.synchronize(dev)
         if dist:
             dist.barrier()
         torch.cuda.synchronize(dev)
-    step_ms = sum(e0.elapsed_time(e2) for e0, _, e2 in ev)
-    bwd_ms = sum(e1.elapsed_time(e2) for _, e1, e2 in ev) / args.steps
-    loss_ms = sum(e0.elapsed_time(e1) for e0, e1, _ in ev) / args.steps
+    step_ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
     t = torch.tensor([step_ms], dtype=torch.float64, device=dev)
     if dist:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     step_ms = t.item()
     ms_per_step = step_ms / args.steps
-    value = world * CELLS * args.steps / (step_ms / 1e3) / 1e9
+    value = world * cells * args.steps / (step_ms / 1e3) / 1e9
     assert torch.isfinite(out8).all() and torch.isfinite(grad).all()
 
     # end to end: pinned host phases in, loss scalars and gradient out, per step
     xh = torch.from_numpy(phi_h).pin_memory()
-    o8h = torch.empty((B, 8), dtype=torch.float32).pin_memory()
-    gh = torch.empty((B, N), dtype=torch.float32).pin_memory()
+    o8h = torch.empty((Bb, 8), dtype=torch.float32).pin_memory()
+    gh = torch.empty((Bb, N), dtype=torch.float32).pin_memory()
     xd = torch.empty_like(x)
     for _ in range(2):
         xd.copy_(xh, non_blocking=True)
-        loss_call(xd.data_ptr(), out8.data_ptr())
-        bwd_call(xd.data_ptr(), out8.data_ptr(), grad.data_ptr())
+        step_call(xd.data_ptr(), out8.data_ptr(), grad.data_ptr())
         o8h.copy_(out8, non_blocking=True)
         gh.copy_(grad, non_blocking=True)
     torch.cuda.synchronize(dev)
@@ -275,8 +265,7 @@ def run_graf(args):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         xd.copy_(xh, non_blocking=True)
-        loss_call(xd.data_ptr(), out8.data_ptr())
-        bwd_call(xd.data_ptr(), out8.data_ptr(), grad.data_ptr())
+        step_call(xd.data_ptr(), out8.data_ptr(), grad.data_ptr())
         o8h.copy_(out8, non_blocking=True)
         gh.copy_(grad, non_blocking=True)
         b.record(stream)
@@ -285,7 +274,7 @@ def run_graf(args):
     t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
     if dist:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = world * CELLS * args.steps / (t.item() / 1e3) / 1e9
+    e2e_value = world * cells * args.steps / (t.item() / 1e3) / 1e9
 
     if rank != 0:
         if dist:
@@ -295,17 +284,20 @@ def run_graf(args):
     peaks, src = _measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak_tflops = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12
-    achieved = ALG_FLOP_BWD / (bwd_ms / 1e3) / 1e12
-    executed_bwd = B * N * 2 * FLOP_PER_ROW
+    # algorithmic work of one call: the forward DFT and its adjoint for every
+    # one of the 2N-1 delay rows; executed: both transforms for the N rows
+    # k >= 0 (rows -k are mirrors), minus the adjoint of row 0
+    alg = Bb * 2 * (2 * N - 1) * FLOP_PER_ROW
+    executed = Bb * (2 * N - 1) * FLOP_PER_ROW
+    achieved = alg / (ms_per_step / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": _traffic_record(),
-                "kernel": "af_backward_kernel<2048> (+ gradient reduce)",
+                "kernel": "af_fused_kernel<2048> (+ loss finalisation and gradient reduction in the same timing)",
                 "peak_source": f"FP32 FMA peak = {SMS} SMs x {FP32_LANES} lanes x 2 x {sm_max:.0f} MHz "
                                f"(sm_max_mhz from MEASURED_PEAKS.json, {src})",
-                "algorithmic_flop_per_launch": ALG_FLOP_BWD,
-                "executed_flop_per_launch": executed_bwd,
-                "executed_frac": executed_bwd / (bwd_ms / 1e3) / 1e12 / peak_tflops,
-                "loss_kernel_ms": loss_ms, "backward_kernel_ms": bwd_ms}
+                "algorithmic_flop_per_launch": alg,
+                "executed_flop_per_launch": executed,
+                "executed_frac": executed / (ms_per_step / 1e3) / 1e12 / peak_tflops}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cols = _oracle_budget_cols(15.0)
@@ -316,11 +308,12 @@ def run_graf(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "B_per_gpu": B, "N": N, "M": M, "beta": BETA, "eps": EPS,
+            "config": {"workload": WORKLOAD if Bb == B else WORKLOAD.replace("256", str(Bb), 1),
+                       "B_per_gpu": Bb, "N": N, "M": M, "beta": BETA, "eps": EPS,
                        "seed": SEED, "l2": "flushed between steps (256 MB write, outside the timed events)"},
             "roofline": roofline, "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B * N * 4,
-                    "d2h_bytes_per_step": B * 8 * 4 + B * N * 4},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": Bb * N * 4,
+                    "d2h_bytes_per_step": Bb * 8 * 4 + Bb * N * 4},
             "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     if dist:
@@ -334,6 +327,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="graf", choices=["graf", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=B,
+                    help="waveforms per GPU (default 256, the benchmark workload; smaller only for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

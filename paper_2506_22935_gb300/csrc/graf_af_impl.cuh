@@ -237,7 +237,9 @@ __global__ void __launch_bounds__(kThreads, 1) af_loss_kernel(AfParams p) {
 //   acc[n-k] += conj(G_R[n]) s[n]  (through R, which carries s*[n-k])
 // in two phases so no two threads of a row update one address at once.
 // Slots that share an accumulator (turns > 1) take turns, CTA-wide.
-template <int M, bool HALF>
+// CONJ: v holds Y = conj(G_R) (the adjoint computed as conj(DFT(conj(G)))):
+// G_R s = cmulc(s, Y) and conj(G_R) s = Y s.
+template <int M, bool HALF, bool CONJ = false>
 __device__ __forceinline__ void scatter_row(const float2* v, float2* acc, const float2* s_sm, int N,
                                             int k, int t, bool active, int slot, int turns,
                                             int my_turn) {
@@ -249,7 +251,8 @@ __device__ __forceinline__ void scatter_row(const float2* v, float2* acc, const 
             const int n = t + P::TPR * decltype(w)::value;
             if ((unsigned)(n - k) < (unsigned)(N - k)) {
                 const float2 a = acc[n];
-                acc[n] = cadd(a, cmul(v[w], s_sm[n - k]));
+                const float2 g = CONJ ? cmulc(s_sm[n - k], v[w]) : cmul(v[w], s_sm[n - k]);
+                acc[n] = cadd(a, g);
             }
         });
     };
@@ -259,7 +262,8 @@ __device__ __forceinline__ void scatter_row(const float2* v, float2* acc, const 
             const int n = t + P::TPR * decltype(w)::value;
             if ((unsigned)(n - k) < (unsigned)(N - k)) {
                 const float2 a = acc[n - k];
-                acc[n - k] = cadd(a, cmulc(s_sm[n], v[w]));
+                const float2 g = CONJ ? cmul(v[w], s_sm[n]) : cmulc(s_sm[n], v[w]);
+                acc[n - k] = cadd(a, g);
             }
         });
     };
@@ -345,53 +349,84 @@ __global__ void __launch_bounds__(kThreads, 1) af_backward_kernel(AfParams p) {
         // row 0 is R[0,n] = |s[n]|^2: it does not depend on the phases
         const bool valid = k < row_end && !(p.phase_only && k == 0);
         build_lag_row<M, HALF>(v, s_sm, p.N, k, t, valid);
-        row_sync<P::TPR>(slot);
-        row_fft<M, false, HALF, false>(v, buf, t, slot);
-        const RowMasks rmk = row_masks(p, cm, k);
-        const bool uniform = rmk.one == full_mask && (rmk.two == 0ull || rmk.two == full_mask);
-        const float wrow = valid ? (rmk.two != 0ull ? 2.0f : (rmk.one != 0ull ? 1.0f : 0.0f)) : 0.0f;
-        const float wb = valid ? (float)base_weight(p, k) : 0.0f;
-        sfor<0, P::VALS>([&](auto w) {
-            const float2 x = v[w];
-            const float a2 = fmaf(fmaf(x.x, x.x, x.y * x.y), invE2, eps_n);
-            const float wt = (uniform || !valid) ? wrow : mweight<decltype(w)::value>(rmk);
-            const float pr = ex2a(fmaf(a2, bl2, -sh));
-            const float cpsl = wt > 0.0f ? wt * cP * (pr - p0) : 0.0f;
-            float c = fmaf(wt - wb, cA, cpsl);
-            // the origin X[0,0] = E: its scatter (2 E c s) and energy term
-            // (-2 E c a2 s) cancel to -2 eps c s / E, added in closed form by
-            // grad_s_kernel; leaving it out here avoids the cancellation
-            if constexpr (decltype(w)::value == 0) {
-                if (k == 0 && t == 0) c = 0.0f;
-            }
-            csum = fmaf(c, a2, csum);
-            v[w] = make_float2(c * x.x, c * x.y);
-        });
-        row_sync<P::TPR>(slot);  // buffer reads of the forward transform are done
-        row_fft<M, true, false, HALF>(v, buf, t, slot);
-        scatter_row<M, HALF>(v, acc, s_sm, p.N, k, t, valid, slot, turns, my_turn);
+        // one transform instance, run twice: recompute X, then the adjoint as
+        // conj(DFT(conj(c X)))
+#pragma unroll 1
+        for (int ph = 0; ph < 2; ++ph) {
+            row_sync<P::TPR>(slot);
+            row_fft<M, false, false, false>(v, buf, t, slot);
+            if (ph == 1) break;
+            const RowMasks rmk = row_masks(p, cm, k);
+            const bool uniform = rmk.one == full_mask && (rmk.two == 0ull || rmk.two == full_mask);
+            const float wrow = valid ? (rmk.two != 0ull ? 2.0f : (rmk.one != 0ull ? 1.0f : 0.0f)) : 0.0f;
+            const float wb = valid ? (float)base_weight(p, k) : 0.0f;
+            sfor<0, P::VALS>([&](auto w) {
+                const float2 x = v[w];
+                const float a2 = fmaf(fmaf(x.x, x.x, x.y * x.y), invE2, eps_n);
+                const float wt = (uniform || !valid) ? wrow : mweight<decltype(w)::value>(rmk);
+                const float pr = ex2a(fmaf(a2, bl2, -sh));
+                const float cpsl = wt > 0.0f ? wt * cP * (pr - p0) : 0.0f;
+                float c = fmaf(wt - wb, cA, cpsl);
+                // the origin X[0,0] = E: its scatter (2 E c s) and energy term
+                // (-2 E c a2 s) cancel to -2 eps c s / E, added in closed form by
+                // grad_s_kernel; leaving it out here avoids the cancellation
+                if constexpr (decltype(w)::value == 0) {
+                    if (k == 0 && t == 0) c = 0.0f;
+                }
+                csum = fmaf(c, a2, csum);
+                v[w] = make_float2(c * x.x, -c * x.y);
+            });
+        }
+        scatter_row<M, HALF, true>(v, acc, s_sm, p.N, k, t, valid, slot, turns, my_turn);
     }
     write_grad_partial<M>(p, acc_all, red, csum, b, tile);
 }
 
 // ---------------------------------------------------------- fused loss + gradient
+// Maximum over the TPR threads of one row slot (slots are contiguous thread
+// ranges: a segment of a warp, one warp, or several warps).
+template <int TPR>
+__device__ __forceinline__ float slot_max(float x, float* scratch, int slot) {
+    if constexpr (TPR <= 32) {
+#pragma unroll
+        for (int o = TPR / 2; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
+        return x;
+    } else {
+        constexpr int WPS = TPR / 32;  // warps per slot
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
+        const int wi = (threadIdx.x % TPR) >> 5;
+        float* sc = scratch + slot * WPS;
+        if ((threadIdx.x & 31) == 0) sc[wi] = x;
+        row_sync<TPR>(slot);
+        float m = sc[0];
+#pragma unroll
+        for (int i = 1; i < WPS; ++i) m = fmaxf(m, sc[i]);
+        row_sync<TPR>(slot);
+        return m;
+    }
+}
+
 // One pass per row: lag product, forward DFT, loss partials and, for rows
 // whose weights are uniform over the row, the gradient remainder of the split
 // adjoint (see af_backward_kernel) -- no recomputation, no stored AF.
 //
 // The PSL term needs p - p0 = (exp(beta a2) - 1) / Z with Z = sum_Omega
-// exp(beta Ahat^2) unknown until every row is done.  The kernel keeps a
-// CTA-uniform log-sum-exp shift mx (the largest weighted a2 seen so far),
-// forms c = w (e - e0) w_psl / E^2 with e = exp(beta (a2 - mx)), e0 =
-// exp(-beta mx), and when mx grows rescales everything accumulated so far
-// by exp(beta (mx_old - mx_new)).  The finalisation then gives each CTA the
-// factor exp(beta (mx_cta - PSL_soft)) that turns its partial into the true
-// remainder.  With w_psl = 0 the remainder is c = (w - w_b) w_isl / E^2,
-// independent of the shift, and every row is fused.
+// exp(beta Ahat^2) unknown until every row is done.  Each row slot keeps a
+// running log-sum-exp shift mx (the largest weighted a2 it has seen), forms
+// c = w (e - e0) w_psl / E^2 with e = exp(beta (a2 - mx)), e0 = exp(-beta mx),
+// and when mx grows rescales what it has accumulated by exp(beta (mx_old -
+// mx_new)).  At the end the slots are brought to the CTA's largest shift, and
+// the loss finalisation gives each CTA the factor exp(beta (mx_cta -
+// PSL_soft)) that turns its partial into the true remainder.  With w_psl = 0
+// the remainder is c = (w - w_b) w_isl / E^2, independent of the shift, and
+// every row is fused.  No barrier spans the CTA inside the row loop, so the
+// slots drift apart and overlap their shared-memory and arithmetic phases.
 //
 // Rows r_lo..defer_hi (those holding mainlobe-box cells, whose weights are
 // not uniform) contribute loss partials only; af_backward_kernel adds their
-// gradient once PSL_soft is known.
+// gradient once PSL_soft is known.  On the PSL path every slot owns its
+// accumulator (acc_copies == slot count).
 template <int M, bool HALF>
 __global__ void __launch_bounds__(kThreads, 1) af_fused_kernel(AfParams p) {
     using P = RowPlan<M>;
@@ -403,7 +438,8 @@ __global__ void __launch_bounds__(kThreads, 1) af_fused_kernel(AfParams p) {
     float2* acc_all = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(p.N) + row_buffer_bytes<M>());
     float* red = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(acc_all) +
                                           (((size_t)p.acc_copies * p.N * sizeof(float2) + 255) & ~(size_t)255));
-    float* red_max = red + 64;  // [2][NW], double-buffered by row iteration
+    // red: [0,8) reductions, [8,16) slot-max scratch (TPR > 32), [64, 64+SLOTS) final slot shifts
+    // (SLOTS <= 32 here unless M <= 64, where the shifts live in registers only), [128, 160) float4s
 
     const int tid = threadIdx.x, slot = tid / P::TPR, t = tid % P::TPR;
     const int b = blockIdx.x / p.tiles, tile = blockIdx.x % p.tiles;
@@ -428,82 +464,100 @@ __global__ void __launch_bounds__(kThreads, 1) af_fused_kernel(AfParams p) {
     const int iters = (p.rows_per_tile + SLOTS - 1) / SLOTS;
 
     float isl = 0.0f, zs = 0.0f, ts = 0.0f, cs = 0.0f;
-    float mx = -CUDART_INF_F;  // CTA-uniform shift (in a2 units)
+    float mx = -CUDART_INF_F;  // slot-uniform shift (in a2 units)
     float2 v[P::VALS];
     for (int it = 0; it < iters; ++it) {
         const int k = row0 + slot + it * SLOTS;
         const bool valid = k < row_end;
         const bool grad_row = valid && k > p.defer_hi && !(p.phase_only && k == 0);
         build_lag_row<M, HALF>(v, s_sm, p.N, k, t, valid);
-        row_sync<P::TPR>(slot);
-        row_fft<M, false, HALF, false>(v, buf, t, slot);
-        const RowMasks rmk = row_masks(p, cm, k);
-        const bool uniform = !valid || (rmk.one == full_mask && (rmk.two == 0ull || rmk.two == full_mask));
-        const float wrow = valid ? (rmk.two != 0ull ? 2.0f : (rmk.one != 0ull ? 1.0f : 0.0f)) : 0.0f;
-        const float wb = valid ? (float)base_weight(p, k) : 0.0f;
-        // pass 1: largest weighted a2 of this thread, then of the CTA
-        float tmx = -CUDART_INF_F;
-        sfor<0, P::VALS>([&](auto w) {
-            const float2 x = v[w];
-            const float a2 = fmaf(fmaf(x.x, x.x, x.y * x.y), invE2, eps_n);
-            const float wt = uniform ? wrow : mweight<decltype(w)::value>(rmk);
-            tmx = fmaxf(tmx, wt > 0.0f ? a2 : -CUDART_INF_F);
-        });
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) tmx = fmaxf(tmx, __shfl_xor_sync(0xffffffffu, tmx, o));
-        float* rm = red_max + (it & 1) * NW;
-        if ((tid & 31) == 0) rm[tid >> 5] = tmx;
-        __syncthreads();
-        float cmx = rm[0];
-#pragma unroll
-        for (int w = 1; w < NW; ++w) cmx = fmaxf(cmx, rm[w]);
-        if (cmx > mx) {  // CTA-uniform
-            const float f = ex2a((mx - cmx) * bl2);  // 0 while mx = -inf
-            zs *= f;
-            ts *= f;
-            if (psl_mode) {
-                cs *= f;
-                if (mx > -CUDART_INF_F) {
-                    for (int i = tid; i < p.acc_copies * p.N; i += kThreads) {
-                        const float2 a = acc_all[i];
-                        acc_all[i] = make_float2(a.x * f, a.y * f);
-                    }
-                    __syncthreads();
-                }
-            }
-            mx = cmx;
-        }
-        // pass 2: loss partials and the gradient remainder c X
-        const float sh = mx * bl2;
-        const float e0 = ex2a(-sh);
-        float risl = 0.0f;
-        sfor<0, P::VALS>([&](auto w) {
-            const float2 x = v[w];
-            const float a2 = fmaf(fmaf(x.x, x.x, x.y * x.y), invE2, eps_n);
-            const float wt = uniform ? wrow : mweight<decltype(w)::value>(rmk);
-            const float e = wt > 0.0f ? ex2a(fmaf(a2, bl2, -sh)) : 0.0f;
-            const float we = wt * e;
-            risl = fmaf(wt, a2, risl);
-            zs += we;
-            ts = fmaf(we, a2, ts);
-            float c = 0.0f;
-            if (grad_row) c = psl_mode ? wt * (e - e0) * cP : (wt - wb) * cI;
-            cs = fmaf(c, a2, cs);
-            v[w] = make_float2(c * x.x, c * x.y);
-        });
-        isl += risl;
-        if constexpr (P::TPR >= 32) {
-            if (grad_row) {  // slot-uniform: the slot is one or more whole warps
-                row_sync<P::TPR>(slot);
-                row_fft<M, true, false, HALF>(v, buf, t, slot);
-            }
-        } else {
+        // one transform instance, run twice: the forward DFT, then the adjoint
+        // as conj(DFT(conj(c X))) -- the epilogue writes conj(c X) and the
+        // scatter reads the conjugated result
+#pragma unroll 1
+        for (int ph = 0; ph < 2; ++ph) {
             row_sync<P::TPR>(slot);
-            row_fft<M, true, false, HALF>(v, buf, t, slot);
+            row_fft<M, false, false, false>(v, buf, t, slot);
+            if (ph == 1) break;
+            const RowMasks rmk = row_masks(p, cm, k);
+            const bool uniform = !valid || (rmk.one == full_mask && (rmk.two == 0ull || rmk.two == full_mask));
+            const float wrow = valid ? (rmk.two != 0ull ? 2.0f : (rmk.one != 0ull ? 1.0f : 0.0f)) : 0.0f;
+            const float wb = valid ? (float)base_weight(p, k) : 0.0f;
+            // pass 1: largest weighted a2 of the row (two independent chains)
+            float tmx[2] = {-CUDART_INF_F, -CUDART_INF_F};
+            sfor<0, P::VALS>([&](auto w) {
+                const float2 x = v[w];
+                const float a2 = fmaf(fmaf(x.x, x.x, x.y * x.y), invE2, eps_n);
+                const float wt = uniform ? wrow : mweight<decltype(w)::value>(rmk);
+                tmx[w & 1] = fmaxf(tmx[w & 1], wt > 0.0f ? a2 : -CUDART_INF_F);
+            });
+            const float rmx = slot_max<P::TPR>(fmaxf(tmx[0], tmx[1]), red + 8, slot);
+            if (rmx > mx) {  // slot-uniform
+                const float f = ex2a((mx - rmx) * bl2);  // 0 while mx = -inf
+                zs *= f;
+                ts *= f;
+                if (psl_mode) {
+                    cs *= f;
+                    if (mx > -CUDART_INF_F) {  // the slot owns its accumulator on this path
+                        for (int n = t; n < p.N; n += P::TPR) {
+                            const float2 a = acc[n];
+                            acc[n] = make_float2(a.x * f, a.y * f);
+                        }
+                    }
+                }
+                mx = rmx;
+            }
+            // pass 2: loss partials and the gradient remainder, v = conj(c X)
+            const float sh = mx * bl2;
+            const float e0 = ex2a(-sh);
+            // row sums in two independent chains each (even / odd registers)
+            float r_isl[2] = {0.0f, 0.0f}, r_z[2] = {0.0f, 0.0f}, r_t[2] = {0.0f, 0.0f}, r_c[2] = {0.0f, 0.0f};
+            sfor<0, P::VALS>([&](auto w) {
+                constexpr int h = decltype(w)::value & 1;
+                const float2 x = v[w];
+                const float a2 = fmaf(fmaf(x.x, x.x, x.y * x.y), invE2, eps_n);
+                const float wt = uniform ? wrow : mweight<decltype(w)::value>(rmk);
+                const float e = wt > 0.0f ? ex2a(fmaf(a2, bl2, -sh)) : 0.0f;
+                const float we = wt * e;
+                r_isl[h] = fmaf(wt, a2, r_isl[h]);
+                r_z[h] += we;
+                r_t[h] = fmaf(we, a2, r_t[h]);
+                float c = 0.0f;
+                if (grad_row) c = psl_mode ? wt * (e - e0) * cP : (wt - wb) * cI;
+                r_c[h] = fmaf(c, a2, r_c[h]);
+                v[w] = make_float2(c * x.x, -c * x.y);
+            });
+            isl += r_isl[0] + r_isl[1];
+            zs += r_z[0] + r_z[1];
+            ts += r_t[0] + r_t[1];
+            cs += r_c[0] + r_c[1];
+            if constexpr (P::TPR >= 32) {
+                if (!grad_row) break;  // slot-uniform: the slot is one or more whole warps
+            }
         }
-        scatter_row<M, HALF>(v, acc, s_sm, p.N, k, t, grad_row, slot, turns, my_turn);
+        scatter_row<M, HALF, true>(v, acc, s_sm, p.N, k, t, grad_row, slot, turns, my_turn);
     }
-    // loss record {ISL, mx, sum e, sum e a2} with the CTA-uniform shift: plain sums
+    // bring every slot to the CTA's largest shift
+    float cmx = mx;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cmx = fmaxf(cmx, __shfl_xor_sync(0xffffffffu, cmx, o));
+    if ((tid & 31) == 0) red[tid >> 5] = cmx;
+    __syncthreads();
+    cmx = red[0];
+#pragma unroll
+    for (int w = 1; w < NW; ++w) cmx = fmaxf(cmx, red[w]);
+    __syncthreads();
+    const float fs = (mx > -CUDART_INF_F) ? ex2a((mx - cmx) * bl2) : 0.0f;
+    zs *= fs;
+    ts *= fs;
+    if (psl_mode) {
+        cs *= fs;
+        for (int n = t; n < p.N; n += P::TPR) {
+            const float2 a = acc[n];
+            acc[n] = make_float2(a.x * fs, a.y * fs);
+        }
+    }
+    // loss record {ISL, mx, sum e, sum e a2}, all relative to the CTA shift
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         isl += __shfl_xor_sync(0xffffffffu, isl, o);
@@ -511,7 +565,7 @@ __global__ void __launch_bounds__(kThreads, 1) af_fused_kernel(AfParams p) {
         ts += __shfl_xor_sync(0xffffffffu, ts, o);
     }
     float4* wred = reinterpret_cast<float4*>(red + 128);
-    if ((tid & 31) == 0) wred[tid >> 5] = make_float4(isl, mx, zs, ts);
+    if ((tid & 31) == 0) wred[tid >> 5] = make_float4(isl, cmx, zs, ts);
     __syncthreads();
     if (tid == 0) {
         float4 a = wred[0];
@@ -553,17 +607,19 @@ template <int M>
 cudaError_t run_backward_m(const AfParams& p, cudaStream_t st) {
     if (p.acc_copies < 1 || (256 / RowPlan<M>::TPR) % p.acc_copies) return cudaErrorInvalidConfiguration;
     const size_t smem = backward_smem<M>(p.N, p.acc_copies);
-    if (2 * p.N <= M) return launch_rows(af_backward_kernel<M, true>, smem, p, st);
     return launch_rows(af_backward_kernel<M, false>, smem, p, st);
 }
 
-// The fused kernel is instantiated without the N <= M/2 pruning: with it the
-// register allocation of the two transforms plus the epilogue spills, without
-// it nothing of note spills, and the pruning saves only ~5% of the butterflies.
+// The kernels that run two transforms per row use one transform instance for
+// both, so that transform prunes neither a half-zero input nor a half-needed
+// output (one inlined transform keeps the register allocation free of
+// spills); with N <= M/2 the fused kernel still skips the zero half in the
+// lag product and in the scatter.
 template <int M>
 cudaError_t run_fused_m(const AfParams& p, cudaStream_t st) {
     if (p.acc_copies < 1 || (256 / RowPlan<M>::TPR) % p.acc_copies) return cudaErrorInvalidConfiguration;
     const size_t smem = backward_smem<M>(p.N, p.acc_copies);
+    if (2 * p.N <= M) return launch_rows(af_fused_kernel<M, true>, smem, p, st);
     return launch_rows(af_fused_kernel<M, false>, smem, p, st);
 }
 

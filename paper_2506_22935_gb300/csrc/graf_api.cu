@@ -220,7 +220,9 @@ graf_status_t graf_af_loss_backward(const void* x, graf_input_t kind, int32_t B,
     const int acc = graf::acc_copies_for(M, N);
     if (acc < 1) return GRAF_ERR_UNSUPPORTED;
     const bool phase_only = kind == GRAF_IN_PHASE && grad_s == nullptr;
-    const FusedPlan f = fused_plan(B, N, M, w, l.w_psl != 0.0f, phase_only);
+    FusedPlan f = fused_plan(B, N, M, w, l.w_psl != 0.0f, phase_only);
+    // on the PSL path each row slot needs its own gradient accumulator
+    if (l.w_psl != 0.0f && acc < graf::kThreads / graf::tpr_of(M)) f.fused = false;
     if (!f.fused) {
         s = graf_af_loss(x, kind, B, N, M, w, l, out8, workspace, workspace_bytes, stream);
         if (s != GRAF_OK) return s;

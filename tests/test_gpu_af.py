@@ -134,7 +134,8 @@ def test_loss_and_gradient_match_oracle(N, M, win, lp, kind):
     out8 = g.af_loss(xt, M, w, loss).cpu().numpy()
     out8b, grad = g.af_loss_backward(xt, M, w, loss)
     out8b, grad = out8b.cpu().numpy(), grad.cpu().numpy()
-    assert np.array_equal(out8, out8b)
+    # the fused call shifts its log-sum-exp differently: equal up to rounding
+    np.testing.assert_allclose(out8b, out8, rtol=2e-6, atol=0)
     for b in range(B):
         gs, gphi, want = orc.grad(sigs[b], M, w.as_tuple(), loss.w_psl, loss.w_isl, loss.beta, loss.eps)
         _check_scalars(out8[b], want)
