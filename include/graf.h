@@ -163,6 +163,38 @@ GRAF_API graf_status_t graf_af_loss_backward(const void* x, graf_input_t kind, i
                                     const float* dL, graf_c32* grad_s, float* grad_phi,
                                     void* workspace, size_t workspace_bytes, void* stream);
 
+/* Adam hyper-parameters (Kingma & Ba).  The paper's experiments optimise
+ * phase codes with Adam at learning rate 0.01 (Sec. 7.1.2); the betas and
+ * eps it leaves unstated are taken as 0.9, 0.999, 1e-8. */
+typedef struct {
+    float lr, beta1, beta2, eps;
+} graf_adam_t;
+
+/* Device bytes of the per-optimiser state graf_adam_step needs (a
+ * completion counter); zero it once before the first step. */
+GRAF_API size_t graf_adam_state_bytes(void);
+
+/*
+ * graf_adam_step - one Adam update of x[count] in place (the gradient-descent
+ * refinement of Sec. 6.2, Eq. 23, with Adam's moment estimates):
+ *   t = *step + 1, m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ *   x -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps),
+ * then *step = t.  x, m, v, grad: device float[count]; m and v start at
+ * zero.  step: device int32 counter (starts at 0); keeping it on the device
+ * lets a captured CUDA graph of many steps replay with no host work.  state:
+ * graf_adam_state_bytes() of zeroed device memory, returned to zero by every
+ * call.  Invalid hyper-parameters or pointers -> GRAF_ERR_INVALID_ARG.
+ */
+GRAF_API graf_status_t graf_adam_step(float* x, float* m, float* v, const float* grad, int64_t count,
+                                      graf_adam_t hp, int32_t* step, void* state, void* stream);
+
+/*
+ * graf_record_loss - history[*step][b] = out8[b][0] for b < B if
+ * *step < history_len (the loss curve of an optimisation, kept on the device).
+ */
+GRAF_API graf_status_t graf_record_loss(const float* out8, int32_t B, float* history, int32_t history_len,
+                                        const int32_t* step, void* stream);
+
 /*
  * graf_af_loss_backward_noalloc - graf_af_loss_backward without a caller
  * workspace, for callers that cannot allocate device memory (a processing

@@ -197,3 +197,32 @@ def fd_grad_s(s, M, window, w_psl=1.0, w_isl=1.0, beta=50.0, eps=1e-12, h=1e-6,
                                eps, h, _ptr(out.view(np.float64)), _threads(nthreads))
     _check(st, "fd_grad_s")
     return out
+
+
+# ------------------------------------------------------------------ optimiser
+def adam_update(x, m, v, g, t, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam step (Kingma & Ba, Algorithm 1), float64, returns (x, m, v):
+    m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2; x -= lr m_hat / (sqrt(v_hat) + eps),
+    m_hat = m / (1 - b1^t), v_hat = v / (1 - b2^t).  t counts from 1."""
+    x, m, v, g = (np.asarray(a, dtype=np.float64) for a in (x, m, v, g))
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    mh = m / (1.0 - beta1 ** t)
+    vh = v / (1.0 - beta2 ** t)
+    return x - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def optimize_phases(phi0, M, window, w_psl, w_isl, beta, eps, steps, lr=1e-2, beta1=0.9, beta2=0.999,
+                    adam_eps=1e-8, nthreads=None):
+    """Gradient refinement of the phases (the paper's Eq. 23 with Adam): per
+    step the loss and dL/dphi of orc_grad, then one Adam update.  Returns
+    (phi after `steps` steps, loss before each step)."""
+    phi = np.asarray(phi0, dtype=np.float64).copy()
+    m = np.zeros_like(phi)
+    v = np.zeros_like(phi)
+    hist = []
+    for t in range(1, steps + 1):
+        _, gphi, out = grad(signal_from_phase(phi), M, window, w_psl, w_isl, beta, eps, nthreads)
+        hist.append(out[0])
+        phi, m, v = adam_update(phi, m, v, gphi, t, lr, beta1, beta2, adam_eps)
+    return phi, np.array(hist)

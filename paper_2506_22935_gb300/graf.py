@@ -47,6 +47,11 @@ class graf_loss_t(ctypes.Structure):
                 ("eps", ctypes.c_float)]
 
 
+class graf_adam_t(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float)]
+
+
 _lib = None
 _lock = threading.Lock()
 _vp = ctypes.c_void_p
@@ -69,6 +74,9 @@ _SIGS = {
                                              graf_loss_t, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "graf_af_loss_backward_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, _i32, _i32, _i32, graf_window_t,
                                                      graf_loss_t, _vp, _vp, _vp, _vp, _vp]),
+    "graf_adam_state_bytes": (_sz, []),
+    "graf_adam_step": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int64, graf_adam_t, _vp, _vp, _vp]),
+    "graf_record_loss": (ctypes.c_int, [_vp, _i32, _vp, _i32, _vp, _vp]),
 }
 
 EXPORTED = tuple(_SIGS)
@@ -134,6 +142,18 @@ def graf_af_loss_backward_noalloc(x, kind, B, N, M, w, l, out8, dL, grad_s, grad
     argument, nothing allocated): for callers that cannot allocate device
     memory.  Calls that may overlap on the GPU must be serialised."""
     return load().graf_af_loss_backward_noalloc(x, kind, B, N, M, w, l, out8, dL, grad_s, grad_phi, stream)
+
+
+def graf_adam_state_bytes() -> int:
+    return load().graf_adam_state_bytes()
+
+
+def graf_adam_step(x, m, v, grad, count, hp, step, state, stream) -> int:
+    return load().graf_adam_step(x, m, v, grad, count, hp, step, state, stream)
+
+
+def graf_record_loss(out8, B, history, history_len, step, stream) -> int:
+    return load().graf_record_loss(out8, B, history, history_len, step, stream)
 
 
 # ---------------------------------------------------------------- helpers
