@@ -196,6 +196,66 @@ GRAF_API graf_status_t graf_record_loss(const float* out8, int32_t B, float* his
                                         const int32_t* step, void* stream);
 
 /*
+ * Batches of unequal waveforms (the batch processing of Sec. 4.3, s in
+ * C^{B x N}, made ragged): waveform b has its own length N_b, Doppler length
+ * M_b, window and loss.  A plan groups the waveforms by M, splits each
+ * waveform's delay rows into tiles, and orders the (waveform, tile) work
+ * items longest first; each M then runs as one persistent launch whose CTAs
+ * claim items from an atomic counter.  Plans own device memory (created and
+ * freed here, never in the compute calls).  Phase input (GRAF_IN_PHASE) and
+ * the phase gradient only.
+ *   N_host   host int32[B], 1 <= N_b
+ *   M_host   host int32[B] (power of two, N_b <= M_b <= GRAF_M_MAX) or NULL
+ *            for the next power of two >= 2 N_b
+ *   w_host   host graf_window_t[B], or NULL for every delay and Doppler bin
+ *            minus the zero-delay mainlobe box |m| < M_b / N_b
+ *   l_host   host graf_loss_t[B] if losses_per_waveform, else [1] for all
+ * Packed layout: waveform b occupies elements [off_b, off_b + N_b) of the
+ * input phases and of the gradient, off_b = N_0 + ... + N_{b-1}.
+ */
+typedef struct graf_batch_plan_s* graf_batch_plan_t;
+
+GRAF_API graf_status_t graf_batch_plan_create(int32_t B, const int32_t* N_host, const int32_t* M_host,
+                                              const graf_window_t* w_host, const graf_loss_t* l_host,
+                                              int32_t losses_per_waveform, graf_input_t kind,
+                                              graf_batch_plan_t* plan);
+
+GRAF_API graf_status_t graf_batch_plan_destroy(graf_batch_plan_t plan);
+
+/* Device workspace for graf_batch_loss_backward (changes after autotuning). */
+GRAF_API size_t graf_batch_workspace_bytes(graf_batch_plan_t plan);
+
+/* Per M bucket (largest M first, up to `capacity`): M, rows per tile, work
+ * items, and 1 if the bucket runs the fused loss + gradient kernel (0: the
+ * loss kernel, then the recomputing backward kernel). */
+GRAF_API graf_status_t graf_batch_plan_info(graf_batch_plan_t plan, int32_t* n_buckets, int32_t* M_out,
+                                            int32_t* rows_per_tile_out, int32_t* items_out,
+                                            int32_t* fused_out, int32_t capacity);
+
+/*
+ * graf_batch_loss_backward - loss scalars (out8 [B][GRAF_LOSS_OUT], as
+ * graf_af_loss) and grad_phi (packed, dL_b * dL/dphi) for every waveform of
+ * the plan.  dL: device float[B] or NULL for ones.  Enqueues on `stream`,
+ * allocates nothing.
+ */
+GRAF_API graf_status_t graf_batch_loss_backward(graf_batch_plan_t plan, const float* phi, float* out8,
+                                                const float* dL, float* grad_phi, void* workspace,
+                                                size_t workspace_bytes, void* stream);
+
+/*
+ * graf_batch_autotune - for every M of the plan, time the row kernel with
+ * tiles of 1, 2, 4, 8 and 16 rows per slot on these inputs and keep the
+ * fastest (the load balance of the persistent launch against the per-tile
+ * overhead); choices are read from and written to `cache_path` ("M rows"
+ * per line) when it is not NULL.  Synchronises `stream`.  Re-query
+ * graf_batch_workspace_bytes afterwards.  Candidates needing more workspace
+ * than given are skipped.
+ */
+GRAF_API graf_status_t graf_batch_autotune(graf_batch_plan_t plan, const float* phi, float* out8,
+                                           float* grad_phi, void* workspace, size_t workspace_bytes,
+                                           void* stream, const char* cache_path);
+
+/*
  * graf_af_loss_backward_noalloc - graf_af_loss_backward without a caller
  * workspace, for callers that cannot allocate device memory (a processing
  * loop whose memory map is fixed at start-up, a host framework whose pool

@@ -7,7 +7,7 @@
 namespace graf {
 
 // |Omega| = |window| - |window intersect mainlobe box|, exact in int64.
-__device__ __forceinline__ long long omega_count(const AfParams& p) {
+__device__ __forceinline__ long long omega_count(const Wave& p) {
     const long long nk = p.k_hi - p.k_lo + 1, nm = p.m_hi - p.m_lo + 1;
     long long bk = 0, bm = 0;
     if (p.k_ml >= 0 && p.m_ml >= 0) {
@@ -24,10 +24,11 @@ __global__ void loss_finalize_kernel(AfParams p, float* out8) {
     const int b = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     const int lane = threadIdx.x & 31;
     if (b >= p.B) return;
-    const double beta = p.beta;
+    const Wave wv = wave_of(p, b);
+    const double beta = wv.beta;
     double isl = 0.0, mx = -CUDART_INF, z = 0.0, T = 0.0;
-    for (int i = lane; i < p.tiles; i += 32) {
-        const float4 r = p.rec[(size_t)b * p.tiles + i];
+    for (int i = lane; i < wv.tiles; i += 32) {
+        const float4 r = p.rec[wv.rec_off + i];
         isl += r.x;
         if (r.y > -CUDART_INF_F) {
             const double m2 = r.y;
@@ -64,12 +65,12 @@ __global__ void loss_finalize_kernel(AfParams p, float* out8) {
     double psl_soft = 0.0;
     if (lane == 0) {
         float* o = out8 + (size_t)b * 8;
-        const double cnt = (double)omega_count(p);
+        const double cnt = (double)omega_count(wv);
         if (mx == -CUDART_INF || z <= 0.0) {
             o[0] = 0.0f; o[1] = 0.0f; o[2] = 0.0f; o[3] = 0.0f; o[6] = 0.0f;
         } else {
             psl_soft = mx + log(z) / beta;
-            o[0] = (float)(p.w_psl * psl_soft + p.w_isl * isl);
+            o[0] = (float)(wv.w_psl * psl_soft + wv.w_isl * isl);
             o[1] = (float)psl_soft;
             o[2] = (float)isl;
             o[3] = (float)mx;
@@ -83,37 +84,38 @@ __global__ void loss_finalize_kernel(AfParams p, float* out8) {
     // PSL_soft)) on the PSL path, 1 on the ISL-only path
     if (p.scale) {
         psl_soft = __shfl_sync(0xffffffffu, psl_soft, 0);
-        for (int i = lane; i < p.tiles; i += 32) {
-            const float m = p.rec[(size_t)b * p.tiles + i].y;
+        for (int i = lane; i < wv.tiles; i += 32) {
+            const float m = p.rec[wv.rec_off + i].y;
             float f = 1.0f;
-            if (p.w_psl != 0.0f) f = m > -CUDART_INF_F ? (float)exp(beta * ((double)m - psl_soft)) : 0.0f;
-            p.scale[(size_t)b * p.tiles + i] = f;
+            if (wv.w_psl != 0.0f && !wv.unscaled)
+                f = m > -CUDART_INF_F ? (float)exp(beta * ((double)m - psl_soft)) : 0.0f;
+            p.scale[wv.rec_off + i] = f;
         }
     }
 }
 
-__device__ __forceinline__ float2 signal_at(const AfParams& p, int b, int n) {
-    if (p.kind == 1) {
+__device__ __forceinline__ float2 signal_at(const Wave& wv, int n) {
+    if (wv.kind == 1) {
         float sn, cs;
-        sincosf(static_cast<const float*>(p.x)[(size_t)b * p.N + n], &sn, &cs);
+        sincosf(static_cast<const float*>(wv.x)[n], &sn, &cs);
         return make_float2(cs, sn);
     }
-    return static_cast<const float2*>(p.x)[(size_t)b * p.N + n];
+    return static_cast<const float2*>(wv.x)[n];
 }
 
 // dL/ds* of the FFT part: scaled sum of the per-CTA partials of the first
 // set plus the unscaled second set (deferred rows), in a fixed order; the
 // same for the per-CTA sums of c a2.
-__device__ __forceinline__ float2 sum_partials(const AfParams& p, int b, int n, double* cs) {
-    const float2* g1 = p.gpart + (size_t)b * p.tiles * p.N + n;
+__device__ __forceinline__ float2 sum_partials(const AfParams& p, const Wave& wv, int b, int n, double* cs) {
+    const float2* g1 = p.gpart + wv.gpart_off + n;
     float2 g = make_float2(0.0f, 0.0f);
     double c = 0.0;
-    for (int i = 0; i < p.tiles; ++i) {
-        const float f = p.scale ? p.scale[(size_t)b * p.tiles + i] : 1.0f;
-        const float2 a = g1[(size_t)i * p.N];
+    for (int i = 0; i < wv.tiles; ++i) {
+        const float f = p.scale ? p.scale[wv.rec_off + i] : 1.0f;
+        const float2 a = g1[(size_t)i * wv.N];
         g.x = fmaf(f, a.x, g.x);
         g.y = fmaf(f, a.y, g.y);
-        if (cs) c += (double)f * p.csum[(size_t)b * p.tiles + i];
+        if (cs) c += (double)f * p.csum[wv.rec_off + i];
     }
     if (p.gpart2) {
         const float2* g2 = p.gpart2 + (size_t)b * p.tiles2 * p.N + n;
@@ -132,11 +134,12 @@ __global__ void grad_phi_kernel(AfParams p, const float* dL, float* grad_phi) {
     const int nblk = (p.N + blockDim.x - 1) / blockDim.x;
     const int b = blockIdx.x / nblk;
     const int n = (blockIdx.x % nblk) * blockDim.x + threadIdx.x;
-    if (n >= p.N) return;
-    const float2 g = sum_partials(p, b, n, nullptr);
-    const float2 s = signal_at(p, b, n);
+    const Wave wv = wave_of(p, b);
+    if (n >= wv.N) return;
+    const float2 g = sum_partials(p, wv, b, n, nullptr);
+    const float2 s = signal_at(wv, n);
     const float scale = 2.0f * (dL ? dL[b] : 1.0f);
-    grad_phi[(size_t)b * p.N + n] = scale * (g.y * s.x - g.x * s.y);
+    grad_phi[wv.out_off + n] = scale * (g.y * s.x - g.x * s.y);
 }
 
 // Per waveform, in FP64: U = sum_k w_b(k) (C[k] + eps) over the transformed
@@ -146,22 +149,23 @@ __global__ void uniform_sum_kernel(AfParams p) {
     extern __shared__ double a_sm[];
     __shared__ double red[32];
     const int b = blockIdx.x;
-    for (int n = threadIdx.x; n < p.N; n += blockDim.x) {
-        const float2 s = signal_at(p, b, n);
+    const Wave wv = wave_of(p, b);
+    for (int n = threadIdx.x; n < wv.N; n += blockDim.x) {
+        const float2 s = signal_at(wv, n);
         a_sm[n] = (double)s.x * s.x + (double)s.y * s.y;
     }
     __syncthreads();
     double acc = 0.0;
-    for (int k = p.r_lo + threadIdx.x; k <= p.r_hi; k += blockDim.x) {
-        const int wb = base_weight(p, k);
+    for (int k = wv.r_lo + threadIdx.x; k <= wv.r_hi; k += blockDim.x) {
+        const int wb = base_weight(wv, k);
         if (wb == 0) continue;
         double c = 0.0;
-        for (int n = k; n < p.N; ++n) c += a_sm[n] * a_sm[n - k];
-        acc += wb * (c + (double)p.eps);
+        for (int n = k; n < wv.N; ++n) c += a_sm[n] * a_sm[n - k];
+        acc += wb * (c + (double)wv.eps);
     }
     // E in FP64 from the same |s|^2, so the closed form cancels exactly
     double e = 0.0;
-    for (int n = threadIdx.x; n < p.N; n += blockDim.x) e += a_sm[n];
+    for (int n = threadIdx.x; n < wv.N; n += blockDim.x) e += a_sm[n];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -194,45 +198,45 @@ __global__ void grad_s_kernel(AfParams p, const float* dL, float2* grad_s, float
     const int nblk = (p.N + blockDim.x - 1) / blockDim.x;
     const int b = blockIdx.x / nblk;
     const int n0 = (blockIdx.x % nblk) * blockDim.x;
-    for (int n = threadIdx.x; n < p.N; n += blockDim.x) {
-        const float2 s = signal_at(p, b, n);
+    const Wave wv = wave_of(p, b);
+    for (int n = threadIdx.x; n < wv.N; n += blockDim.x) {
+        const float2 s = signal_at(wv, n);
         a_sm[n] = (double)s.x * s.x + (double)s.y * s.y;
     }
     __syncthreads();
     const int n = n0 + threadIdx.x;
-    if (n >= p.N) return;
+    if (n >= wv.N) return;
     double cs = 0.0;
-    const float2 g = sum_partials(p, b, n, &cs);
-    const float2 s = signal_at(p, b, n);
+    const float2 g = sum_partials(p, wv, b, n, &cs);
+    const float2 s = signal_at(wv, n);
     const float* sv = p.saved8 + (size_t)b * 8;
     const double E = p.usum[2 * b + 1];
-    const float bl2 = p.beta * 1.4426950408889634f;
+    const float bl2 = wv.beta * 1.4426950408889634f;
     const float p0 = ex2a(-(sv[1] * bl2));
-    const double Ap = (double)fmaf(p.w_psl, p0, p.w_isl);
+    const double Ap = (double)fmaf(wv.w_psl, p0, wv.w_isl);
     double corr = 0.0;
-    for (int k = p.r_lo; k <= p.r_hi; ++k) {
-        const int wb = base_weight(p, k);
+    for (int k = wv.r_lo; k <= wv.r_hi; ++k) {
+        const int wb = base_weight(wv, k);
         if (wb == 0) continue;
         double t = 0.0;
         if (n >= k) t += a_sm[n - k];
-        if (n + k < p.N) t += a_sm[n + k];
+        if (n + k < wv.N) t += a_sm[n + k];
         corr += wb * t;
     }
-    const double gu = Ap * (double)p.M * (corr / (E * E) - 2.0 * p.usum[2 * b] / (E * E * E));
+    const double gu = Ap * (double)wv.M * (corr / (E * E) - 2.0 * p.usum[2 * b] / (E * E * E));
     // origin cell, left out of the FFT part: its exact total is -2 eps c00 s / E
     double c00 = 0.0;
-    if (p.k_lo <= 0 && p.k_hi >= 0 && p.m_lo <= 0 && p.m_hi >= 0) {
-        const int w00 = (p.k_ml >= 0 && p.m_ml >= 0) ? 0 : 1;
-        const double a00 = 1.0 + (double)p.eps / (E * E);
-        const double pr = exp((double)p.beta * (a00 - (double)sv[1]));
-        c00 = ((w00 - base_weight(p, 0)) * Ap + (w00 > 0 ? w00 * (double)p.w_psl * (pr - (double)p0) : 0.0)) /
+    if (wv.k_lo <= 0 && wv.k_hi >= 0 && wv.m_lo <= 0 && wv.m_hi >= 0) {
+        const int w00 = (wv.k_ml >= 0 && wv.m_ml >= 0) ? 0 : 1;
+        const double a00 = 1.0 + (double)wv.eps / (E * E);
+        const double pr = exp((double)wv.beta * (a00 - (double)sv[1]));
+        c00 = ((w00 - base_weight(wv, 0)) * Ap + (w00 > 0 ? w00 * (double)wv.w_psl * (pr - (double)p0) : 0.0)) /
               (E * E);
     }
-    const double coef = -2.0 * E * cs + gu - 2.0 * (double)p.eps * c00 / E;  // real multiplier of s[n]
+    const double coef = -2.0 * E * cs + gu - 2.0 * (double)wv.eps * c00 / E;  // real multiplier of s[n]
     const double scale = 2.0 * (dL ? (double)dL[b] : 1.0);
-    grad_s[(size_t)b * p.N + n] = make_float2((float)(scale * (g.x + coef * s.x)),
-                                              (float)(scale * (g.y + coef * s.y)));
-    if (grad_phi) grad_phi[(size_t)b * p.N + n] = (float)(scale * ((double)g.y * s.x - (double)g.x * s.y));
+    grad_s[wv.out_off + n] = make_float2((float)(scale * (g.x + coef * s.x)), (float)(scale * (g.y + coef * s.y)));
+    if (grad_phi) grad_phi[wv.out_off + n] = (float)(scale * ((double)g.y * s.x - (double)g.x * s.y));
 }
 
 #define GRAF_DISPATCH_M(FN, M, ...)                      \
@@ -341,6 +345,9 @@ cudaError_t run_grad_reduce(const AfParams& p, const float* dL, float2* grad_s, 
     grad_s_kernel<<<(unsigned)grid, 256, sm, st>>>(p, dL, grad_s, grad_phi);
     return cudaGetLastError();
 }
+
+cudaError_t run_backward_rows(const AfParams& p, cudaStream_t st) { GRAF_DISPATCH_M(run_backward_m, p.M, p, st) }
+cudaError_t run_loss_rows(const AfParams& p, cudaStream_t st) { GRAF_DISPATCH_M(run_loss_m, p.M, p, st) }
 
 cudaError_t run_backward(const AfParams& p, const float* dL, float2* grad_s, float* grad_phi,
                          cudaStream_t st) {

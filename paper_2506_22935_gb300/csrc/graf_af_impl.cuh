@@ -38,6 +38,29 @@ __device__ __forceinline__ void build_lag_row(float2* v, const float2* s_sm, int
     }
 }
 
+// Work-item loop of a row kernel.  Uniform batch: CTA i runs item
+// (i / tiles, i % tiles) once.  Batch plan: persistent CTAs claim items from
+// the plan's atomic counter until none is left (items are ordered longest
+// first, so this is a longest-processing-time schedule).
+template <class F>
+__device__ __forceinline__ void for_each_item(const AfParams& p, F&& body) {
+    if (!p.items) {
+        body((int)(blockIdx.x / p.tiles), (int)(blockIdx.x % p.tiles));
+        return;
+    }
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(p.counter, 1u);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= p.n_items) break;
+        const int2 bt = p.items[it];
+        body(bt.x, bt.y);
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------- forward (store)
 // Ahat = sqrt(|X|^2 + eps) / E (Eq. 12, Eq. 17) for every window cell of
 // rows k and -k.  Stores are coalesced along m (consecutive threads hold
@@ -52,10 +75,11 @@ __global__ void __launch_bounds__(kThreads, 1) af_forward_kernel(AfParams p) {
 
     const int tid = threadIdx.x, slot = tid / P::TPR, t = tid % P::TPR;
     const int b = blockIdx.x / p.tiles, tile = blockIdx.x % p.tiles;
-    const float E = load_signal(p, b, s_sm, red);
+    const Wave wv = wave_of(p, b);
+    const float E = load_signal(wv, s_sm, red);
     const float invE = 1.0f / E;
     float2* buf = bufs + (size_t)slot * (P::SPLIT ? P::SMEM_ROW / 2 : P::SMEM_ROW);
-    const ColMasks cm = col_masks<M>(p, t);
+    const ColMasks cm = col_masks<M>(wv, t);
 
     const int ncols = p.m_hi - p.m_lo + 1;
     const size_t rows_out = (size_t)(p.k_hi - p.k_lo + 1);
@@ -72,7 +96,7 @@ __global__ void __launch_bounds__(kThreads, 1) af_forward_kernel(AfParams p) {
         row_sync<P::TPR>(slot);
         row_fft<M, false, HALF, false>(v, buf, t, slot);
         if (valid) {
-            const RowMasks rmk = row_masks(p, cm, k);
+            const RowMasks rmk = row_masks(wv, cm, k);
             const bool in_pos = rmk.pos != 0ull, in_neg = rmk.neg != 0ull;
             // row k at rp[m], row -k at rn[m'] (m' = -m, and -M/2 maps to itself)
             float* rp = out_b + (in_pos ? (size_t)(k - p.k_lo) * ncols : 0) - p.m_lo + t;
@@ -126,39 +150,43 @@ __device__ __forceinline__ void lse_merge(float& isl, float& mx, float& sum, flo
 }
 
 template <int M, bool HALF>
-__global__ void __launch_bounds__(kThreads, 1) af_loss_kernel(AfParams p) {
+__device__ __forceinline__ void loss_item(const AfParams& p, int b, int tile, unsigned char* smem) {
     using P = RowPlan<M>;
-    extern __shared__ __align__(256) unsigned char smem[];
+    // the waveform's parameters live in shared memory (CTA-uniform), so they
+    // are re-read after barriers instead of occupying registers
+    __shared__ Wave s_wave;
+    if (threadIdx.x == 0) s_wave = wave_of(p, b);
+    __syncthreads();
+    const Wave& wv = s_wave;
     float2* s_sm = reinterpret_cast<float2*>(smem);
     float2* bufs = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(p.N));
     float* red = reinterpret_cast<float*>(smem + smem_signal_bytes<M>(p.N) + row_buffer_bytes<M>());
 
     const int tid = threadIdx.x, slot = tid / P::TPR, t = tid % P::TPR;
-    const int b = blockIdx.x / p.tiles, tile = blockIdx.x % p.tiles;
-    const float E = load_signal(p, b, s_sm, red);
+    const float E = load_signal(wv, s_sm, red);
     if (tile == 0 && tid == 0) p.out8[(size_t)b * 8 + 4] = E;
     const float invE2 = 1.0f / (E * E);
-    const float eps_n = p.eps * invE2;
-    const float bl2 = p.beta * 1.4426950408889634f;  // beta * log2(e)
+    const float eps_n = wv.eps * invE2;
+    const float bl2 = wv.beta * 1.4426950408889634f;  // beta * log2(e)
     float2* buf = bufs + (size_t)slot * (P::SPLIT ? P::SMEM_ROW / 2 : P::SMEM_ROW);
-    const ColMasks cm = col_masks<M>(p, t);
+    const ColMasks cm = col_masks<M>(wv, t);
     constexpr unsigned long long full_mask = P::VALS == 64 ? ~0ull : ((1ull << P::VALS) - 1ull);
 
-    const int row0 = p.r_lo + tile * p.rows_per_tile;
-    const int row_end = min(row0 + p.rows_per_tile, p.r_hi + 1);
+    const int row0 = wv.r_lo + tile * wv.rows_per_tile;
+    const int row_end = min(row0 + wv.rows_per_tile, wv.r_hi + 1);
     constexpr int SLOTS = kThreads / P::TPR;
-    const int iters = (p.rows_per_tile + SLOTS - 1) / SLOTS;
+    const int iters = (wv.rows_per_tile + SLOTS - 1) / SLOTS;
 
     float isl = 0.0f, mx = -CUDART_INF_F, sum = 0.0f, T = 0.0f;
     float2 v[P::VALS];
     for (int it = 0; it < iters; ++it) {
         const int k = row0 + slot + it * SLOTS;
         const bool valid = k < row_end;
-        build_lag_row<M, HALF>(v, s_sm, p.N, k, t, valid);
+        build_lag_row<M, HALF>(v, s_sm, wv.N, k, t, valid);
         row_sync<P::TPR>(slot);
         row_fft<M, false, HALF, false>(v, buf, t, slot);
         if (!valid) continue;
-        const RowMasks rmk = row_masks(p, cm, k);
+        const RowMasks rmk = row_masks(wv, cm, k);
         if ((rmk.one | rmk.two) == 0ull) continue;
         // a row whose weights are all equal (every Doppler bin in the window,
         // no mainlobe cell) skips the per-cell mask tests
@@ -203,8 +231,14 @@ __global__ void __launch_bounds__(kThreads, 1) af_loss_kernel(AfParams p) {
             const float4 c = wred[w];
             lse_merge(a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w, bl2);
         }
-        p.rec[(size_t)b * p.tiles + tile] = a;
+        p.rec[wv.rec_off + tile] = a;
     }
+}
+
+template <int M, bool HALF>
+__global__ void __launch_bounds__(kThreads, 1) af_loss_kernel(AfParams p) {
+    extern __shared__ __align__(256) unsigned char smem[];
+    for_each_item(p, [&](int b, int tile) { loss_item<M, HALF>(p, b, tile, smem); });
 }
 
 // ---------------------------------------------------------- backward
@@ -287,8 +321,8 @@ __device__ __forceinline__ void scatter_row(const float2* v, float2* acc, const 
 // Per-CTA partial sums of the gradient accumulators and one scalar, in a
 // fixed order (warp xor tree, then warps in order).
 template <int M>
-__device__ __forceinline__ void write_grad_partial(const AfParams& p, const float2* acc_all, float* red,
-                                                   float cs, int b, int tile) {
+__device__ __forceinline__ void write_grad_partial(const AfParams& p, const Wave& wv, const float2* acc_all,
+                                                   float* red, float cs, int tile) {
     const int tid = threadIdx.x;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
@@ -297,21 +331,26 @@ __device__ __forceinline__ void write_grad_partial(const AfParams& p, const floa
     if (tid == 0) {
         float s = red[0];
         for (int w = 1; w < kThreads / 32; ++w) s += red[w];
-        p.csum[(size_t)b * p.tiles + tile] = s;
+        p.csum[wv.rec_off + tile] = s;
     }
-    float2* out = p.gpart + ((size_t)b * p.tiles + tile) * p.N;
-    for (int n = tid; n < p.N; n += kThreads) {
+    float2* out = p.gpart + wv.gpart_off + (long long)tile * wv.N;
+    for (int n = tid; n < wv.N; n += kThreads) {
         float2 a = acc_all[n];
-        for (int s = 1; s < p.acc_copies; ++s) a = cadd(a, acc_all[(size_t)s * p.N + n]);
+        for (int s = 1; s < p.acc_copies; ++s) a = cadd(a, acc_all[(size_t)s * wv.N + n]);
         out[n] = a;
     }
 }
 
 template <int M, bool HALF>
-__global__ void __launch_bounds__(kThreads, 1) af_backward_kernel(AfParams p) {
+__device__ __forceinline__ void backward_item(const AfParams& p, int b, int tile, unsigned char* smem) {
     using P = RowPlan<M>;
     constexpr int SLOTS = kThreads / P::TPR;
-    extern __shared__ __align__(256) unsigned char smem[];
+    // the waveform's parameters live in shared memory (CTA-uniform), so they
+    // are re-read after barriers instead of occupying registers
+    __shared__ Wave s_wave;
+    if (threadIdx.x == 0) s_wave = wave_of(p, b);
+    __syncthreads();
+    const Wave& wv = s_wave;
     float2* s_sm = reinterpret_cast<float2*>(smem);
     float2* bufs = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(p.N));
     float2* acc_all = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(p.N) + row_buffer_bytes<M>());
@@ -319,36 +358,35 @@ __global__ void __launch_bounds__(kThreads, 1) af_backward_kernel(AfParams p) {
                                           (((size_t)p.acc_copies * p.N * sizeof(float2) + 255) & ~(size_t)255));
 
     const int tid = threadIdx.x, slot = tid / P::TPR, t = tid % P::TPR;
-    const int b = blockIdx.x / p.tiles, tile = blockIdx.x % p.tiles;
-    for (int i = tid; i < p.acc_copies * p.N; i += kThreads) acc_all[i] = make_float2(0.0f, 0.0f);
-    const float E = load_signal(p, b, s_sm, red);  // includes __syncthreads
+    for (int i = tid; i < p.acc_copies * wv.N; i += kThreads) acc_all[i] = make_float2(0.0f, 0.0f);
+    const float E = load_signal(wv, s_sm, red);  // includes __syncthreads
     const float invE2 = 1.0f / (E * E);
-    const float eps_n = p.eps * invE2;
-    const float bl2 = p.beta * 1.4426950408889634f;
+    const float eps_n = wv.eps * invE2;
+    const float bl2 = wv.beta * 1.4426950408889634f;
     const float psl_soft = p.saved8[(size_t)b * 8 + 1];
     const float sh = psl_soft * bl2;
     const float p0 = ex2a(-sh);
-    const float cA = fmaf(p.w_psl, p0, p.w_isl) * invE2;  // A' / E^2
-    const float cP = p.w_psl * invE2;
+    const float cA = fmaf(wv.w_psl, p0, wv.w_isl) * invE2;  // A' / E^2
+    const float cP = wv.w_psl * invE2;
     float csum = 0.0f;
     float2* buf = bufs + (size_t)slot * (P::SPLIT ? P::SMEM_ROW / 2 : P::SMEM_ROW);
-    const ColMasks cm = col_masks<M>(p, t);
+    const ColMasks cm = col_masks<M>(wv, t);
     constexpr unsigned long long full_mask = P::VALS == 64 ? ~0ull : ((1ull << P::VALS) - 1ull);
     // slots sharing an accumulator (when shared memory is short) take turns
     const int turns = SLOTS / p.acc_copies;
     const int my_turn = slot / p.acc_copies;
-    float2* acc = acc_all + (size_t)(slot % p.acc_copies) * p.N;
+    float2* acc = acc_all + (size_t)(slot % p.acc_copies) * wv.N;
 
-    const int row0 = p.r_lo + tile * p.rows_per_tile;
-    const int row_end = min(row0 + p.rows_per_tile, p.r_hi + 1);
-    const int iters = (p.rows_per_tile + SLOTS - 1) / SLOTS;
+    const int row0 = wv.r_lo + tile * wv.rows_per_tile;
+    const int row_end = min(row0 + wv.rows_per_tile, wv.r_hi + 1);
+    const int iters = (wv.rows_per_tile + SLOTS - 1) / SLOTS;
 
     float2 v[P::VALS];
     for (int it = 0; it < iters; ++it) {
         const int k = row0 + slot + it * SLOTS;
         // row 0 is R[0,n] = |s[n]|^2: it does not depend on the phases
         const bool valid = k < row_end && !(p.phase_only && k == 0);
-        build_lag_row<M, HALF>(v, s_sm, p.N, k, t, valid);
+        build_lag_row<M, HALF>(v, s_sm, wv.N, k, t, valid);
         // one transform instance, run twice: recompute X, then the adjoint as
         // conj(DFT(conj(c X)))
 #pragma unroll 1
@@ -356,10 +394,10 @@ __global__ void __launch_bounds__(kThreads, 1) af_backward_kernel(AfParams p) {
             row_sync<P::TPR>(slot);
             row_fft<M, false, false, false>(v, buf, t, slot);
             if (ph == 1) break;
-            const RowMasks rmk = row_masks(p, cm, k);
+            const RowMasks rmk = row_masks(wv, cm, k);
             const bool uniform = rmk.one == full_mask && (rmk.two == 0ull || rmk.two == full_mask);
             const float wrow = valid ? (rmk.two != 0ull ? 2.0f : (rmk.one != 0ull ? 1.0f : 0.0f)) : 0.0f;
-            const float wb = valid ? (float)base_weight(p, k) : 0.0f;
+            const float wb = valid ? (float)base_weight(wv, k) : 0.0f;
             sfor<0, P::VALS>([&](auto w) {
                 const float2 x = v[w];
                 const float a2 = fmaf(fmaf(x.x, x.x, x.y * x.y), invE2, eps_n);
@@ -377,9 +415,15 @@ __global__ void __launch_bounds__(kThreads, 1) af_backward_kernel(AfParams p) {
                 v[w] = make_float2(c * x.x, -c * x.y);
             });
         }
-        scatter_row<M, HALF, true>(v, acc, s_sm, p.N, k, t, valid, slot, turns, my_turn);
+        scatter_row<M, HALF, true>(v, acc, s_sm, wv.N, k, t, valid, slot, turns, my_turn);
     }
-    write_grad_partial<M>(p, acc_all, red, csum, b, tile);
+    write_grad_partial<M>(p, wv, acc_all, red, csum, tile);
+}
+
+template <int M, bool HALF>
+__global__ void __launch_bounds__(kThreads, 1) af_backward_kernel(AfParams p) {
+    extern __shared__ __align__(256) unsigned char smem[];
+    for_each_item(p, [&](int b, int tile) { backward_item<M, HALF>(p, b, tile, smem); });
 }
 
 // ---------------------------------------------------------- fused loss + gradient
@@ -428,11 +472,16 @@ __device__ __forceinline__ float slot_max(float x, float* scratch, int slot) {
 // gradient once PSL_soft is known.  On the PSL path every slot owns its
 // accumulator (acc_copies == slot count).
 template <int M, bool HALF>
-__global__ void __launch_bounds__(kThreads, 1) af_fused_kernel(AfParams p) {
+__device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, unsigned char* smem) {
     using P = RowPlan<M>;
     constexpr int SLOTS = kThreads / P::TPR;
     constexpr int NW = kThreads / 32;
-    extern __shared__ __align__(256) unsigned char smem[];
+    // the waveform's parameters live in shared memory (CTA-uniform), so they
+    // are re-read after barriers instead of occupying registers
+    __shared__ Wave s_wave;
+    if (threadIdx.x == 0) s_wave = wave_of(p, b);
+    __syncthreads();
+    const Wave& wv = s_wave;
     float2* s_sm = reinterpret_cast<float2*>(smem);
     float2* bufs = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(p.N));
     float2* acc_all = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(p.N) + row_buffer_bytes<M>());
@@ -442,26 +491,25 @@ __global__ void __launch_bounds__(kThreads, 1) af_fused_kernel(AfParams p) {
     // (SLOTS <= 32 here unless M <= 64, where the shifts live in registers only), [128, 160) float4s
 
     const int tid = threadIdx.x, slot = tid / P::TPR, t = tid % P::TPR;
-    const int b = blockIdx.x / p.tiles, tile = blockIdx.x % p.tiles;
-    for (int i = tid; i < p.acc_copies * p.N; i += kThreads) acc_all[i] = make_float2(0.0f, 0.0f);
-    const float E = load_signal(p, b, s_sm, red);  // includes __syncthreads
+    for (int i = tid; i < p.acc_copies * wv.N; i += kThreads) acc_all[i] = make_float2(0.0f, 0.0f);
+    const float E = load_signal(wv, s_sm, red);  // includes __syncthreads
     if (tile == 0 && tid == 0) p.out8[(size_t)b * 8 + 4] = E;
     const float invE2 = 1.0f / (E * E);
-    const float eps_n = p.eps * invE2;
-    const float bl2 = p.beta * 1.4426950408889634f;  // beta * log2(e)
-    const bool psl_mode = p.w_psl != 0.0f;
-    const float cP = p.w_psl * invE2;
-    const float cI = p.w_isl * invE2;
+    const float eps_n = wv.eps * invE2;
+    const float bl2 = wv.beta * 1.4426950408889634f;  // beta * log2(e)
+    const bool psl_mode = wv.w_psl != 0.0f;
+    const float cP = wv.w_psl * invE2;
+    const float cI = wv.w_isl * invE2;
     float2* buf = bufs + (size_t)slot * (P::SPLIT ? P::SMEM_ROW / 2 : P::SMEM_ROW);
-    const ColMasks cm = col_masks<M>(p, t);
+    const ColMasks cm = col_masks<M>(wv, t);
     constexpr unsigned long long full_mask = P::VALS == 64 ? ~0ull : ((1ull << P::VALS) - 1ull);
     const int turns = SLOTS / p.acc_copies;
     const int my_turn = slot / p.acc_copies;
-    float2* acc = acc_all + (size_t)(slot % p.acc_copies) * p.N;
+    float2* acc = acc_all + (size_t)(slot % p.acc_copies) * wv.N;
 
-    const int row0 = p.r_lo + tile * p.rows_per_tile;
-    const int row_end = min(row0 + p.rows_per_tile, p.r_hi + 1);
-    const int iters = (p.rows_per_tile + SLOTS - 1) / SLOTS;
+    const int row0 = wv.r_lo + tile * wv.rows_per_tile;
+    const int row_end = min(row0 + wv.rows_per_tile, wv.r_hi + 1);
+    const int iters = (wv.rows_per_tile + SLOTS - 1) / SLOTS;
 
     float isl = 0.0f, zs = 0.0f, ts = 0.0f, cs = 0.0f;
     float mx = -CUDART_INF_F;  // slot-uniform shift (in a2 units)
@@ -469,8 +517,8 @@ __global__ void __launch_bounds__(kThreads, 1) af_fused_kernel(AfParams p) {
     for (int it = 0; it < iters; ++it) {
         const int k = row0 + slot + it * SLOTS;
         const bool valid = k < row_end;
-        const bool grad_row = valid && k > p.defer_hi && !(p.phase_only && k == 0);
-        build_lag_row<M, HALF>(v, s_sm, p.N, k, t, valid);
+        const bool grad_row = valid && k > wv.defer_hi && !(p.phase_only && k == 0);
+        build_lag_row<M, HALF>(v, s_sm, wv.N, k, t, valid);
         // one transform instance, run twice: the forward DFT, then the adjoint
         // as conj(DFT(conj(c X))) -- the epilogue writes conj(c X) and the
         // scatter reads the conjugated result
@@ -479,10 +527,10 @@ __global__ void __launch_bounds__(kThreads, 1) af_fused_kernel(AfParams p) {
             row_sync<P::TPR>(slot);
             row_fft<M, false, false, false>(v, buf, t, slot);
             if (ph == 1) break;
-            const RowMasks rmk = row_masks(p, cm, k);
+            const RowMasks rmk = row_masks(wv, cm, k);
             const bool uniform = !valid || (rmk.one == full_mask && (rmk.two == 0ull || rmk.two == full_mask));
             const float wrow = valid ? (rmk.two != 0ull ? 2.0f : (rmk.one != 0ull ? 1.0f : 0.0f)) : 0.0f;
-            const float wb = valid ? (float)base_weight(p, k) : 0.0f;
+            const float wb = valid ? (float)base_weight(wv, k) : 0.0f;
             // pass 1: largest weighted a2 of the row (two independent chains)
             float tmx[2] = {-CUDART_INF_F, -CUDART_INF_F};
             sfor<0, P::VALS>([&](auto w) {
@@ -499,7 +547,7 @@ __global__ void __launch_bounds__(kThreads, 1) af_fused_kernel(AfParams p) {
                 if (psl_mode) {
                     cs *= f;
                     if (mx > -CUDART_INF_F) {  // the slot owns its accumulator on this path
-                        for (int n = t; n < p.N; n += P::TPR) {
+                        for (int n = t; n < wv.N; n += P::TPR) {
                             const float2 a = acc[n];
                             acc[n] = make_float2(a.x * f, a.y * f);
                         }
@@ -535,7 +583,7 @@ __global__ void __launch_bounds__(kThreads, 1) af_fused_kernel(AfParams p) {
                 if (!grad_row) break;  // slot-uniform: the slot is one or more whole warps
             }
         }
-        scatter_row<M, HALF, true>(v, acc, s_sm, p.N, k, t, grad_row, slot, turns, my_turn);
+        scatter_row<M, HALF, true>(v, acc, s_sm, wv.N, k, t, grad_row, slot, turns, my_turn);
     }
     // bring every slot to the CTA's largest shift
     float cmx = mx;
@@ -552,7 +600,7 @@ __global__ void __launch_bounds__(kThreads, 1) af_fused_kernel(AfParams p) {
     ts *= fs;
     if (psl_mode) {
         cs *= fs;
-        for (int n = t; n < p.N; n += P::TPR) {
+        for (int n = t; n < wv.N; n += P::TPR) {
             const float2 a = acc[n];
             acc[n] = make_float2(a.x * fs, a.y * fs);
         }
@@ -574,9 +622,15 @@ __global__ void __launch_bounds__(kThreads, 1) af_fused_kernel(AfParams p) {
             a.z += wred[w].z;
             a.w += wred[w].w;
         }
-        p.rec[(size_t)b * p.tiles + tile] = a;
+        p.rec[wv.rec_off + tile] = a;
     }
-    write_grad_partial<M>(p, acc_all, red, cs, b, tile);
+    write_grad_partial<M>(p, wv, acc_all, red, cs, tile);
+}
+
+template <int M, bool HALF>
+__global__ void __launch_bounds__(kThreads, 1) af_fused_kernel(AfParams p) {
+    extern __shared__ __align__(256) unsigned char smem[];
+    for_each_item(p, [&](int b, int tile) { fused_item<M, HALF>(p, b, tile, smem); });
 }
 
 // ---------------------------------------------------------- host launchers
@@ -585,7 +639,13 @@ static cudaError_t launch_rows(K kernel, size_t smem, const AfParams& p, cudaStr
     if (smem > kMaxSmem) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const long long grid = (long long)p.B * p.tiles;
+    long long grid = (long long)p.B * p.tiles;
+    if (p.items) {  // persistent: one CTA per SM (the row kernels fill an SM each)
+        int dev = 0, sms = kSmsTarget;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        grid = p.n_items < sms ? p.n_items : sms;
+        if (grid < 1) return cudaSuccess;
+    }
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     kernel<<<(unsigned)grid, kThreads, smem, st>>>(p);
     return cudaGetLastError();

@@ -13,42 +13,107 @@ namespace graf {
 constexpr int kThreads = 256;     // threads per CTA of the row kernels
 constexpr int kSmsTarget = 152;   // GB300 SM count, used to size tiles
 
-// Everything a row kernel needs, passed by value.
+// Per-waveform parameters of a batch of unequal waveforms (device table, one
+// entry per waveform).  Offsets are in elements of the arrays they index.
+struct WaveDesc {
+    long long x_off;      // first element of waveform b in the packed input
+    long long out_off;    // first element of its gradient in the packed output
+    long long gpart_off;  // first float2 of its per-CTA gradient partials (tiles x N)
+    int rec_off;          // index of its first per-CTA record / scale / sum
+    int N, M;
+    int k_lo, k_hi, m_lo, m_hi, k_ml, m_ml;
+    int r_lo, r_hi, rows_per_tile, tiles, defer_hi;
+    int unscaled;         // 1: its gradient partials are final (loss, then recomputing backward)
+    float eps, beta, w_psl, w_isl;
+};
+
+// Everything a row kernel needs, passed by value.  Two modes: a uniform
+// batch (waves == nullptr: B waveforms of length N sharing window and loss,
+// CTA i handles waveform i / tiles, tile i % tiles) or a batch plan (waves
+// and items set: persistent CTAs claim work items (waveform, tile) from an
+// atomic counter in the order the plan gives, longest first).
 struct AfParams {
-    const void* x;   // [B][N] complex64 or float phases
+    const void* x;   // uniform: [B][N]; plan: packed, waveform b at waves[b].x_off
     int kind;        // 0 complex, 1 phase
-    int B, N, M;
+    int B, N, M;     // plan: N = longest waveform, M = this launch's row length
     int k_lo, k_hi, m_lo, m_hi, k_ml, m_ml;
     int r_lo, r_hi;        // k >= 0 rows to transform (negative rows are mirrored)
     int rows_per_tile, tiles;
     int full_m;            // window covers every Doppler bin
     float eps, beta, w_psl, w_isl;
     float* af_out;         // forward: [B][k_hi-k_lo+1][m_hi-m_lo+1]
-    float4* rec;           // loss: per-CTA records [B][tiles] {isl, max, sum, T}
+    float4* rec;           // loss: per-CTA records {isl, max, sum, T}
     float* out8;           // loss: [B][8] scalars
     const float* saved8;   // backward: [B][8]
-    float2* gpart;         // backward: per-CTA partial dL/ds* [B][tiles][N]
-    float* csum;           // backward: per-CTA sum of c a2 [B][tiles]
+    float2* gpart;         // backward: per-CTA partial dL/ds*
+    float* csum;           // backward: per-CTA sum of c a2
     double* usum;          // backward (grad_s): per waveform {sum_k w_b(k) (C[k] + eps), E} [B][2]
     int phase_only;        // backward: only dL/dphi is wanted (row k = 0 contributes nothing)
     int acc_copies;        // backward: gradient accumulators per CTA (divides the slot count)
     // fused loss + gradient
     int defer_hi;          // rows r_lo..defer_hi get loss partials only (their gradient is
                            // computed by af_backward_kernel after the loss is known); -1: none
-    float* scale;          // per-CTA gradient scale [B][tiles], written by the loss finalisation
-    // gradient reduction: a second set of partials (deferred rows), unscaled
+    float* scale;          // per-CTA gradient scale, written by the loss finalisation
+    // gradient reduction: a second set of partials (deferred rows), unscaled (uniform mode)
     int tiles2;
     const float2* gpart2;  // [B][tiles2][N]
     const float* csum2;    // [B][tiles2]
+    // batch plan
+    const WaveDesc* waves;
+    const int2* items;     // (waveform, tile) of this launch's work items, longest first
+    int n_items;
+    unsigned int* counter; // zeroed before the launch
 };
+
+// The view of one waveform a kernel works with, in either mode.
+struct Wave {
+    const void* x;  // this waveform's input
+    long long out_off, gpart_off;
+    int rec_off;
+    int kind, N, M;
+    int k_lo, k_hi, m_lo, m_hi, k_ml, m_ml;
+    int r_lo, r_hi, rows_per_tile, tiles, full_m, defer_hi, unscaled;
+    float eps, beta, w_psl, w_isl;
+};
+
+__host__ __device__ __forceinline__ Wave wave_of(const AfParams& p, int b) {
+    Wave w;
+    w.kind = p.kind;
+    if (p.waves) {
+        const WaveDesc& d = p.waves[b];
+        w.x = static_cast<const char*>(p.x) + d.x_off * (p.kind == 1 ? 4 : 8);
+        w.out_off = d.out_off;
+        w.gpart_off = d.gpart_off;
+        w.rec_off = d.rec_off;
+        w.N = d.N; w.M = d.M;
+        w.k_lo = d.k_lo; w.k_hi = d.k_hi; w.m_lo = d.m_lo; w.m_hi = d.m_hi; w.k_ml = d.k_ml; w.m_ml = d.m_ml;
+        w.r_lo = d.r_lo; w.r_hi = d.r_hi; w.rows_per_tile = d.rows_per_tile; w.tiles = d.tiles;
+        w.defer_hi = d.defer_hi;
+        w.unscaled = d.unscaled;
+        w.eps = d.eps; w.beta = d.beta; w.w_psl = d.w_psl; w.w_isl = d.w_isl;
+    } else {
+        w.x = static_cast<const char*>(p.x) + (long long)b * p.N * (p.kind == 1 ? 4 : 8);
+        w.out_off = (long long)b * p.N;
+        w.gpart_off = (long long)b * p.tiles * p.N;
+        w.rec_off = b * p.tiles;
+        w.N = p.N; w.M = p.M;
+        w.k_lo = p.k_lo; w.k_hi = p.k_hi; w.m_lo = p.m_lo; w.m_hi = p.m_hi; w.k_ml = p.k_ml; w.m_ml = p.m_ml;
+        w.r_lo = p.r_lo; w.r_hi = p.r_hi; w.rows_per_tile = p.rows_per_tile; w.tiles = p.tiles;
+        w.defer_hi = p.defer_hi;
+        w.unscaled = 0;
+        w.eps = p.eps; w.beta = p.beta; w.w_psl = p.w_psl; w.w_isl = p.w_isl;
+    }
+    w.full_m = (w.m_lo == -(w.M / 2) && w.m_hi == w.M / 2 - 1) ? 1 : 0;
+    return w;
+}
 
 // Base weight w_b(k) of transformed row k >= 0 (see the backward kernel): the
 // weight every Doppler bin of rows k and -k carries when the window spans all
 // bins, unless the mainlobe box takes half the row or more; otherwise 0.
-__host__ __device__ inline int base_weight(const AfParams& p, int k) {
-    if (!p.full_m) return 0;
-    if (k <= p.k_ml && 2 * p.m_ml + 1 > p.M / 2) return 0;
-    return ((k >= p.k_lo && k <= p.k_hi) ? 1 : 0) + ((k > 0 && -k >= p.k_lo && -k <= p.k_hi) ? 1 : 0);
+__host__ __device__ __forceinline__ int base_weight(const Wave& w, int k) {
+    if (!w.full_m) return 0;
+    if (k <= w.k_ml && 2 * w.m_ml + 1 > w.M / 2) return 0;
+    return ((k >= w.k_lo && k <= w.k_hi) ? 1 : 0) + ((k > 0 && -k >= w.k_lo && -k <= w.k_hi) ? 1 : 0);
 }
 
 // Row range and tiling shared by the host code (workspace sizes) and launches.
@@ -90,6 +155,8 @@ int backward_acc_copies(int N) {
 }
 
 size_t row_kernel_smem(int M, int N, int which);  // which: 0 forward/loss, 2 backward
+cudaError_t run_loss_rows(const AfParams& p, cudaStream_t st);      // loss row kernel only
+cudaError_t run_backward_rows(const AfParams& p, cudaStream_t st);  // backward row kernel only
 int acc_copies_for(int M, int N);                  // backward accumulators, 0 = unsupported
 template <int M> cudaError_t run_forward_m(const AfParams& p, cudaStream_t st);
 template <int M> cudaError_t run_loss_m(const AfParams& p, cudaStream_t st);
@@ -138,22 +205,22 @@ __device__ __forceinline__ float ex2a(float x) {
     return y;
 }
 
-// Load s[0..N) of waveform b into shared memory (phases -> exp(j phi)) and
+// Load s[0..N) of one waveform into shared memory (phases -> exp(j phi)) and
 // return E = sum |s|^2, reduced in a fixed order (identical in every CTA).
-__device__ __forceinline__ float load_signal(const AfParams& p, int b, float2* s_sm, float* red) {
+__device__ __forceinline__ float load_signal(const Wave& wv, float2* s_sm, float* red) {
     const int tid = threadIdx.x;
     float e = 0.0f;
-    if (p.kind == 1) {
-        const float* ph = static_cast<const float*>(p.x) + (size_t)b * p.N;
-        for (int n = tid; n < p.N; n += kThreads) {
+    if (wv.kind == 1) {
+        const float* ph = static_cast<const float*>(wv.x);
+        for (int n = tid; n < wv.N; n += kThreads) {
             float sn, cs;
             sincosf(__ldg(ph + n), &sn, &cs);
             s_sm[n] = make_float2(cs, sn);
             e = fmaf(cs, cs, fmaf(sn, sn, e));
         }
     } else {
-        const float2* xs = static_cast<const float2*>(p.x) + (size_t)b * p.N;
-        for (int n = tid; n < p.N; n += kThreads) {
+        const float2* xs = static_cast<const float2*>(wv.x);
+        for (int n = tid; n < wv.N; n += kThreads) {
             float2 v = __ldg(xs + n);
             s_sm[n] = v;
             e = fmaf(v.x, v.x, fmaf(v.y, v.y, e));
@@ -189,7 +256,7 @@ struct ColMasks {
 };
 
 template <int M>
-__device__ __forceinline__ ColMasks col_masks(const AfParams& p, int t) {
+__device__ __forceinline__ ColMasks col_masks(const Wave& p, int t) {
     using P = RowPlan<M>;
     ColMasks c{0ull, 0ull, 0ull};
     for (int w = 0; w < P::VALS; ++w) {
@@ -211,7 +278,7 @@ struct RowMasks {
     unsigned long long pos, neg, one, two;
 };
 
-__device__ __forceinline__ RowMasks row_masks(const AfParams& p, const ColMasks& c, int k) {
+__device__ __forceinline__ RowMasks row_masks(const Wave& p, const ColMasks& c, int k) {
     const bool in_pos = (k >= p.k_lo) && (k <= p.k_hi);
     const bool in_neg = (k > 0) && (-k >= p.k_lo) && (-k <= p.k_hi);
     const bool ml_row = k <= p.k_ml;  // k >= 0, so |-k| = k too

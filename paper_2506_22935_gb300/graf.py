@@ -74,6 +74,12 @@ _SIGS = {
                                              graf_loss_t, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "graf_af_loss_backward_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, _i32, _i32, _i32, graf_window_t,
                                                      graf_loss_t, _vp, _vp, _vp, _vp, _vp]),
+    "graf_batch_plan_create": (ctypes.c_int, [_i32, _vp, _vp, _vp, _vp, _i32, ctypes.c_int, _vp]),
+    "graf_batch_plan_destroy": (ctypes.c_int, [_vp]),
+    "graf_batch_workspace_bytes": (_sz, [_vp]),
+    "graf_batch_plan_info": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _i32]),
+    "graf_batch_loss_backward": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "graf_batch_autotune": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _sz, _vp, ctypes.c_char_p]),
     "graf_adam_state_bytes": (_sz, []),
     "graf_adam_step": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int64, graf_adam_t, _vp, _vp, _vp]),
     "graf_record_loss": (ctypes.c_int, [_vp, _i32, _vp, _i32, _vp, _vp]),
@@ -142,6 +148,30 @@ def graf_af_loss_backward_noalloc(x, kind, B, N, M, w, l, out8, dL, grad_s, grad
     argument, nothing allocated): for callers that cannot allocate device
     memory.  Calls that may overlap on the GPU must be serialised."""
     return load().graf_af_loss_backward_noalloc(x, kind, B, N, M, w, l, out8, dL, grad_s, grad_phi, stream)
+
+
+def graf_batch_plan_create(B, N_host, M_host, w_host, l_host, losses_per_waveform, kind, plan_out) -> int:
+    return load().graf_batch_plan_create(B, N_host, M_host, w_host, l_host, losses_per_waveform, kind, plan_out)
+
+
+def graf_batch_plan_destroy(plan) -> int:
+    return load().graf_batch_plan_destroy(plan)
+
+
+def graf_batch_workspace_bytes(plan) -> int:
+    return load().graf_batch_workspace_bytes(plan)
+
+
+def graf_batch_plan_info(plan, n_buckets, M_out, rpt_out, items_out, fused_out, capacity) -> int:
+    return load().graf_batch_plan_info(plan, n_buckets, M_out, rpt_out, items_out, fused_out, capacity)
+
+
+def graf_batch_loss_backward(plan, phi, out8, dL, grad_phi, workspace, workspace_bytes, stream) -> int:
+    return load().graf_batch_loss_backward(plan, phi, out8, dL, grad_phi, workspace, workspace_bytes, stream)
+
+
+def graf_batch_autotune(plan, phi, out8, grad_phi, workspace, workspace_bytes, stream, cache_path) -> int:
+    return load().graf_batch_autotune(plan, phi, out8, grad_phi, workspace, workspace_bytes, stream, cache_path)
 
 
 def graf_adam_state_bytes() -> int:
@@ -309,6 +339,88 @@ def af_loss_backward(x, M: int, window: Window | None = None, loss: Loss = Loss(
                                  None if dl is None else dl.data_ptr(), gs, gp, ws.data_ptr(), ws.numel(),
                                  _stream(x.device)), "graf_af_loss_backward")
     return out8, grad
+
+
+class BatchPlan:
+    """A ragged batch plan (graf_batch_plan_create) with torch-allocated
+    workspace: waveform b has length N[b], Doppler length M[b] (default the
+    next power of two >= 2 N[b]), window windows[b] (default: all bins minus
+    the zero-delay mainlobe) and loss losses[b] (or one loss for all)."""
+
+    def __init__(self, N, M=None, windows=None, losses=None, device=None):
+        torch = _torch()
+        import numpy as np
+        self.N = np.asarray(N, dtype=np.int32)
+        self.B = len(self.N)
+        Nc = np.ascontiguousarray(self.N)
+        Mc = None if M is None else np.ascontiguousarray(np.asarray(M, dtype=np.int32))
+        wc = None
+        if windows is not None:
+            wc = (graf_window_t * self.B)(*[w.c() for w in windows])
+        if losses is None:
+            losses = [Loss()]
+        per = 1 if len(losses) == self.B and self.B > 1 else 0
+        lc = (graf_loss_t * len(losses))(*[l.c() for l in losses])
+        h = ctypes.c_void_p()
+        st = graf_batch_plan_create(self.B, Nc.ctypes.data, None if Mc is None else Mc.ctypes.data,
+                                    None if wc is None else ctypes.addressof(wc), ctypes.addressof(lc), per,
+                                    GRAF_IN_PHASE, ctypes.byref(h))
+        _check(st, "graf_batch_plan_create")
+        self.handle = h
+        self.offsets = np.concatenate([[0], np.cumsum(self.N.astype(np.int64))])
+        self.device = device or torch.device("cuda", torch.cuda.current_device())
+        self._ws = None
+
+    def workspace(self):
+        torch = _torch()
+        nb = graf_batch_workspace_bytes(self.handle)
+        if self._ws is None or self._ws.numel() < nb:
+            self._ws = torch.empty(max(nb, 256), dtype=torch.uint8, device=self.device)
+        return self._ws
+
+    def info(self):
+        n = ctypes.c_int32()
+        cap = 32
+        arrs = [(ctypes.c_int32 * cap)() for _ in range(4)]
+        _check(graf_batch_plan_info(self.handle, ctypes.byref(n), *[ctypes.addressof(a) for a in arrs], cap),
+               "graf_batch_plan_info")
+        return [dict(M=arrs[0][i], rows_per_tile=arrs[1][i], items=arrs[2][i], fused=bool(arrs[3][i]))
+                for i in range(n.value)]
+
+    def loss_backward(self, phi_packed, dL=None, out8=None, grad=None):
+        torch = _torch()
+        out8 = out8 if out8 is not None else torch.empty((self.B, 8), dtype=torch.float32, device=self.device)
+        grad = grad if grad is not None else torch.empty_like(phi_packed)
+        ws = self.workspace()
+        st = graf_batch_loss_backward(self.handle, phi_packed.data_ptr(), out8.data_ptr(),
+                                      None if dL is None else dL.data_ptr(), grad.data_ptr(), ws.data_ptr(),
+                                      ws.numel(), torch.cuda.current_stream(self.device).cuda_stream)
+        _check(st, "graf_batch_loss_backward")
+        return out8, grad
+
+    def autotune(self, phi_packed, cache_path=None):
+        torch = _torch()
+        out8 = torch.empty((self.B, 8), dtype=torch.float32, device=self.device)
+        grad = torch.empty_like(phi_packed)
+        # room for the smallest tiles tried
+        ws = torch.empty(max(4 * graf_batch_workspace_bytes(self.handle), 1 << 20), dtype=torch.uint8,
+                         device=self.device)
+        st = graf_batch_autotune(self.handle, phi_packed.data_ptr(), out8.data_ptr(), grad.data_ptr(),
+                                 ws.data_ptr(), ws.numel(), torch.cuda.current_stream(self.device).cuda_stream,
+                                 None if cache_path is None else str(cache_path).encode())
+        _check(st, "graf_batch_autotune")
+        self._ws = None
+
+    def close(self):
+        if getattr(self, "handle", None):
+            graf_batch_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _make_autograd():
