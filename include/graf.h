@@ -256,6 +256,46 @@ GRAF_API graf_status_t graf_batch_autotune(graf_batch_plan_t plan, const float* 
                                            void* stream, const char* cache_path);
 
 /*
+ * Learned proposal network (the NN -> waveform -> GRAF -> loss pipeline of
+ * Sec. 6.1): an MLP spec[8] -> 512 -> 512 -> 1024 phases, GELU on the hidden
+ * layers, BF16 weights on the tensor cores with FP32 accumulation, FP32
+ * master weights.  Parameter layout (fp32 master and bf16 copy alike, the
+ * bf16 biases unused): W1 [16][512] (rows 8..15 multiply the zero padding
+ * of the 8 inputs to the 16-wide MMA k-step) | b1 [512] | W2 [512][512] |
+ * b2 [512] | W3 [512][1024] | b3 [1024].  All pointers are device memory.
+ */
+#define GRAF_MLP_IN 8
+#define GRAF_MLP_IN_PAD 16
+#define GRAF_MLP_HID 512
+#define GRAF_MLP_OUT 1024
+
+/* Number of parameters (floats in the master copy, bf16 in the copy). */
+GRAF_API size_t graf_mlp_param_count(void);
+/* Bytes of the per-call activation buffer for `rows` specs. */
+GRAF_API size_t graf_mlp_activation_bytes(int32_t rows);
+/* params_bf16 = bf16(master), round to nearest even. */
+GRAF_API graf_status_t graf_mlp_cast_params(const float* master, void* params_bf16, void* stream);
+/* phases [rows][1024] fp32 = MLP(spec [rows][8] fp32); keeps what the
+ * backward needs in `activations`. */
+GRAF_API graf_status_t graf_mlp_forward(const float* spec, int32_t rows, const float* master,
+                                        const void* params_bf16, float* phases, void* activations,
+                                        void* stream);
+/* Label loss per row, invariant to a global phase and to conjugation (the
+ * symmetries that leave a Doppler-symmetric masked ISL unchanged):
+ * L_b = min_{s=+-1} (1 - |mean_n exp(j(phases_n - s target_n))|) -> loss[b]
+ * (may be NULL); scale * dL_b/dphases becomes the output gradient. */
+GRAF_API graf_status_t graf_mlp_label_loss(const float* phases, const float* target, int32_t rows,
+                                           float scale, float* loss, void* activations, void* stream);
+/* Use dphases [rows][1024] (e.g. dL/dphi of an AF loss of the proposed
+ * codes) as the output gradient instead. */
+GRAF_API graf_status_t graf_mlp_set_output_grad(const float* dphases, int32_t rows, void* activations,
+                                                void* stream);
+/* grad (fp32, parameter layout) = gradient of the summed output-gradient
+ * objective w.r.t. the parameters, for the last forward's activations. */
+GRAF_API graf_status_t graf_mlp_backward(int32_t rows, const float* master, const void* params_bf16,
+                                         void* activations, float* grad, void* stream);
+
+/*
  * graf_af_loss_backward_noalloc - graf_af_loss_backward without a caller
  * workspace, for callers that cannot allocate device memory (a processing
  * loop whose memory map is fixed at start-up, a host framework whose pool

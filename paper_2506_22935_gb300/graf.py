@@ -29,6 +29,8 @@ GRAF_IN_PHASE = 1
 GRAF_LOSS_OUT = 8
 GRAF_M_MIN = 8
 GRAF_M_MAX = 16384
+GRAF_MLP_IN = 8
+GRAF_MLP_OUT = 1024
 
 
 class GrafError(RuntimeError):
@@ -80,6 +82,13 @@ _SIGS = {
     "graf_batch_plan_info": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _i32]),
     "graf_batch_loss_backward": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "graf_batch_autotune": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _sz, _vp, ctypes.c_char_p]),
+    "graf_mlp_param_count": (_sz, []),
+    "graf_mlp_activation_bytes": (_sz, [_i32]),
+    "graf_mlp_cast_params": (ctypes.c_int, [_vp, _vp, _vp]),
+    "graf_mlp_forward": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp, _vp]),
+    "graf_mlp_label_loss": (ctypes.c_int, [_vp, _vp, _i32, ctypes.c_float, _vp, _vp, _vp]),
+    "graf_mlp_set_output_grad": (ctypes.c_int, [_vp, _i32, _vp, _vp]),
+    "graf_mlp_backward": (ctypes.c_int, [_i32, _vp, _vp, _vp, _vp, _vp]),
     "graf_adam_state_bytes": (_sz, []),
     "graf_adam_step": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int64, graf_adam_t, _vp, _vp, _vp]),
     "graf_record_loss": (ctypes.c_int, [_vp, _i32, _vp, _i32, _vp, _vp]),
@@ -172,6 +181,34 @@ def graf_batch_loss_backward(plan, phi, out8, dL, grad_phi, workspace, workspace
 
 def graf_batch_autotune(plan, phi, out8, grad_phi, workspace, workspace_bytes, stream, cache_path) -> int:
     return load().graf_batch_autotune(plan, phi, out8, grad_phi, workspace, workspace_bytes, stream, cache_path)
+
+
+def graf_mlp_param_count() -> int:
+    return load().graf_mlp_param_count()
+
+
+def graf_mlp_activation_bytes(rows) -> int:
+    return load().graf_mlp_activation_bytes(rows)
+
+
+def graf_mlp_cast_params(master, params_bf16, stream) -> int:
+    return load().graf_mlp_cast_params(master, params_bf16, stream)
+
+
+def graf_mlp_forward(spec, rows, master, params_bf16, phases, activations, stream) -> int:
+    return load().graf_mlp_forward(spec, rows, master, params_bf16, phases, activations, stream)
+
+
+def graf_mlp_label_loss(phases, target, rows, scale, loss, activations, stream) -> int:
+    return load().graf_mlp_label_loss(phases, target, rows, scale, loss, activations, stream)
+
+
+def graf_mlp_set_output_grad(dphases, rows, activations, stream) -> int:
+    return load().graf_mlp_set_output_grad(dphases, rows, activations, stream)
+
+
+def graf_mlp_backward(rows, master, params_bf16, activations, grad, stream) -> int:
+    return load().graf_mlp_backward(rows, master, params_bf16, activations, grad, stream)
 
 
 def graf_adam_state_bytes() -> int:

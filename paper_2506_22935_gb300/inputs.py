@@ -69,3 +69,60 @@ def barker13() -> np.ndarray:
     textbook binary sequence whose aperiodic autocorrelation sidelobes are at
     most 1 in magnitude."""
     return np.array([1, 1, 1, 1, 1, -1, -1, 1, 1, -1, 1, -1, 1], dtype=np.float64)
+
+
+def normal(seed: int, count: int, offset: int = 0) -> np.ndarray:
+    """Standard normal draws (Box-Muller on pairs of uniforms)."""
+    m = (count + 1) // 2
+    u1 = uniform(seed, m, 2 * offset)
+    u2 = uniform(seed, m, 2 * offset + m)
+    r = np.sqrt(-2.0 * np.log(1.0 - u1))
+    z = np.concatenate([r * np.cos(2 * math.pi * u2), r * np.sin(2 * math.pi * u2)])
+    return z[:count]
+
+
+def design_specs(seed: int, count: int) -> dict:
+    """Design specs of the learned proposal: delay-mask half-width K log-uniform
+    on [16, 512], Doppler-mask half-width Mw log-uniform on [8, 256] (both
+    rounded), PSL and ISL weights uniform on [0, 1] (ISL weight at least 0.1),
+    and four standard-normal noise dimensions."""
+    u = uniform(seed, 4 * count).reshape(count, 4)
+    K = np.rint(np.exp(math.log(16) + u[:, 0] * (math.log(512) - math.log(16)))).astype(np.int32)
+    Mw = np.rint(np.exp(math.log(8) + u[:, 1] * (math.log(256) - math.log(8)))).astype(np.int32)
+    w_psl = u[:, 2]
+    w_isl = 0.1 + 0.9 * u[:, 3]
+    noise = normal(seed + 1, 4 * count).reshape(count, 4)
+    return dict(K=K, Mw=Mw, w_psl=w_psl, w_isl=w_isl, noise=noise)
+
+
+def spec_features(specs: dict) -> np.ndarray:
+    """float32 [count, 8]: log-widths mapped to [-1, 1], the two weights, the
+    noise dimensions."""
+    k = (np.log(specs["K"]) - math.log(16)) / (math.log(512) - math.log(16)) * 2.0 - 1.0
+    m = (np.log(specs["Mw"]) - math.log(8)) / (math.log(256) - math.log(8)) * 2.0 - 1.0
+    f = np.concatenate([k[:, None], m[:, None], specs["w_psl"][:, None], specs["w_isl"][:, None],
+                        specs["noise"]], axis=1)
+    return f.astype(np.float32)
+
+
+def mlp_init_params(seed: int) -> np.ndarray:
+    """float64 flat parameters of the 8(16)->512->512->1024 MLP: weights
+    uniform(-a, a) with a = sqrt(6 / (fan_in + fan_out)) (Glorot), zero rows
+    for the input padding, zero biases.  Layout W1 [16][512] | b1 | W2
+    [512][512] | b2 | W3 [512][1024] | b3."""
+    shapes = [("W", 16, 512, 8), ("b", 512), ("W", 512, 512, 512), ("b", 512), ("W", 512, 1024, 512),
+              ("b", 1024)]
+    parts, off = [], 0
+    for s in shapes:
+        if s[0] == "W":
+            _, rows, cols, fan_in = s
+            n = rows * cols
+            a = math.sqrt(6.0 / (fan_in + cols))
+            w = ((uniform(seed, n, off) * 2.0 - 1.0) * a).reshape(rows, cols)
+            w[fan_in:, :] = 0.0
+            parts.append(w.ravel())
+        else:
+            n = s[1]
+            parts.append(np.zeros(n))
+        off += n
+    return np.concatenate(parts)

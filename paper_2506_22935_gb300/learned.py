@@ -1,0 +1,175 @@
+"""Learned proposal of initial phase codes (the paper's Sec. 6.1 pipeline: a
+network maps design parameters to a waveform, the GRAF layer scores it).
+
+``ProposalMLP`` is an MLP spec[8] -> 512 -> 512 -> 1024 phases whose forward,
+backward and optimiser run in the library's kernels (BF16 tensor-core GEMMs,
+FP32 accumulation and master weights, Adam from ``graf_adam_step``).  Design
+specs (delay and Doppler mask half-widths, PSL/ISL weights, noise) come from
+``inputs.design_specs``; training labels are codes optimised on the GPU by
+``PhaseOptimizer`` over each spec's own mask and loss (a ragged batch plan);
+``time_to_target`` compares how many optimiser steps the proposal and a random
+initialisation need to reach a masked-ISL target.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+from . import graf as g
+from . import inputs
+from .optim import Adam, PhaseOptimizer
+
+N_CODE, M_CODE = 1024, 2048
+
+
+class ProposalMLP:
+    def __init__(self, seed: int = 0, device=None, lr: float = 1e-3):
+        g.load()
+        self.device = device or torch.device("cuda", torch.cuda.current_device())
+        n = g.graf_mlp_param_count()
+        self.master = torch.from_numpy(inputs.mlp_init_params(seed).astype(np.float32)).to(self.device)
+        assert self.master.numel() == n
+        self.bf16 = torch.empty(n, dtype=torch.bfloat16, device=self.device)
+        self.grad = torch.zeros(n, dtype=torch.float32, device=self.device)
+        self.m = torch.zeros(n, dtype=torch.float32, device=self.device)
+        self.v = torch.zeros(n, dtype=torch.float32, device=self.device)
+        self.step = torch.zeros(1, dtype=torch.int32, device=self.device)
+        self.state = torch.zeros(g.graf_adam_state_bytes(), dtype=torch.uint8, device=self.device)
+        self.hp = Adam(lr=lr).c()
+        self._acts = None
+        self._rows = 0
+        self._cast()
+
+    def _stream(self):
+        return torch.cuda.current_stream(self.device).cuda_stream
+
+    def _cast(self):
+        st = g.graf_mlp_cast_params(self.master.data_ptr(), self.bf16.data_ptr(), self._stream())
+        if st != 0:
+            raise g.GrafError(st, "graf_mlp_cast_params")
+
+    def _activations(self, rows):
+        if self._acts is None or self._rows < rows:
+            self._acts = torch.empty(g.graf_mlp_activation_bytes(rows), dtype=torch.uint8, device=self.device)
+            self._rows = rows
+        return self._acts
+
+    def forward(self, feats: torch.Tensor) -> torch.Tensor:
+        """phases [rows, 1024] for spec features [rows, 8] (float32, CUDA)."""
+        feats = feats.contiguous()
+        rows = feats.shape[0]
+        out = torch.empty((rows, g.GRAF_MLP_OUT), dtype=torch.float32, device=self.device)
+        st = g.graf_mlp_forward(feats.data_ptr(), rows, self.master.data_ptr(), self.bf16.data_ptr(),
+                                out.data_ptr(), self._activations(rows).data_ptr(), self._stream())
+        if st != 0:
+            raise g.GrafError(st, "graf_mlp_forward")
+        return out
+
+    def train_step(self, feats: torch.Tensor, targets: torch.Tensor, loss_out: torch.Tensor | None = None):
+        """One Adam step on the mean phase label loss of a minibatch."""
+        rows = feats.shape[0]
+        phases = self.forward(feats)
+        st = g.graf_mlp_label_loss(phases.data_ptr(), targets.contiguous().data_ptr(), rows, 1.0 / rows,
+                                   None if loss_out is None else loss_out.data_ptr(), self._acts.data_ptr(),
+                                   self._stream())
+        if st != 0:
+            raise g.GrafError(st, "graf_mlp_label_loss")
+        st = g.graf_mlp_backward(rows, self.master.data_ptr(), self.bf16.data_ptr(), self._acts.data_ptr(),
+                                 self.grad.data_ptr(), self._stream())
+        if st != 0:
+            raise g.GrafError(st, "graf_mlp_backward")
+        st = g.graf_adam_step(self.master.data_ptr(), self.m.data_ptr(), self.v.data_ptr(), self.grad.data_ptr(),
+                              self.master.numel(), self.hp, self.step.data_ptr(), self.state.data_ptr(),
+                              self._stream())
+        if st != 0:
+            raise g.GrafError(st, "graf_adam_step")
+        self._cast()
+        return phases
+
+
+def spec_windows_losses(specs, isl_only=False, beta=50.0):
+    windows, losses = [], []
+    for i in range(len(specs["K"])):
+        windows.append(g.Window.masked(int(specs["K"][i]), int(specs["Mw"][i])))
+        w_psl = 0.0 if isl_only else float(specs["w_psl"][i])
+        w_isl = 1.0 if isl_only else float(specs["w_isl"][i])
+        losses.append(g.Loss(w_psl, w_isl, beta, 1e-12))
+    return windows, losses
+
+
+def lfm_init(count: int) -> np.ndarray:
+    """The deterministic starting code of the label optimiser: the discrete
+    chirp pi n^2 / N for every spec."""
+    return np.tile(inputs.lfm_phases(N_CODE), (count, 1))
+
+
+def optimise_codes(specs, phi0: np.ndarray, steps: int, isl_only=False, device=None, graph=True, chunk=1024):
+    """Adam (lr 1e-2) on each spec's own masked loss from phi0 [count, N].
+    Returns (codes [count, N], loss history [steps, count]) as numpy."""
+    device = device or torch.device("cuda", torch.cuda.current_device())
+    count = phi0.shape[0]
+    codes = np.empty_like(phi0, dtype=np.float32)
+    hist = np.empty((steps, count), dtype=np.float32)
+    for c0 in range(0, count, chunk):
+        c1 = min(count, c0 + chunk)
+        sub = {k: v[c0:c1] for k, v in specs.items()}
+        windows, losses = spec_windows_losses(sub, isl_only)
+        plan = g.BatchPlan([N_CODE] * (c1 - c0), M=[M_CODE] * (c1 - c0), windows=windows, losses=losses,
+                           device=device)
+        phi = torch.from_numpy(np.ascontiguousarray(phi0[c0:c1], dtype=np.float32)).to(device)
+        opt = PhaseOptimizer(phi.view(-1), plan=plan, history_len=steps)
+        opt.run(steps, graph=graph)
+        torch.cuda.synchronize(device)
+        codes[c0:c1] = phi.cpu().numpy()
+        hist[:, c0:c1] = opt.history.cpu().numpy()
+        plan.close()
+    return codes, hist
+
+
+def steps_to_target(hist: np.ndarray, target: np.ndarray) -> np.ndarray:
+    """First step index (1-based, steps taken) whose loss is <= target, per
+    column; hist.shape[0] + 1 where it never gets there."""
+    ok = hist <= target[None, :]
+    first = np.where(ok.any(axis=0), ok.argmax(axis=0), hist.shape[0])
+    return first + 1
+
+
+def time_to_target(mlp: ProposalMLP, specs, steps=500, seeds=4, seed_base=7000, device=None):
+    """Per spec: target T = median over `seeds` random initialisations of the
+    masked ISL after `steps` Adam steps; then the steps (and GPU time) the
+    optimiser needs to reach T from the MLP proposal and from one more random
+    initialisation.  Returns a dict of numpy arrays and timings."""
+    device = device or torch.device("cuda", torch.cuda.current_device())
+    count = len(specs["K"])
+    finals = []
+    for s in range(seeds):
+        phi0 = inputs.random_phases(seed_base + s, count, N_CODE)
+        _, h = optimise_codes(specs, phi0, steps, isl_only=True, device=device)
+        finals.append(h[-1])
+    target = np.median(np.stack(finals), axis=0)
+    feats = torch.from_numpy(inputs.spec_features(specs)).to(device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    prop = mlp.forward(feats)
+    e1.record()
+    torch.cuda.synchronize(device)
+    mlp_ms = e0.elapsed_time(e1)
+    prop = np.mod(prop.cpu().numpy(), 2 * math.pi).astype(np.float32)
+    e0.record()
+    _, h_learned = optimise_codes(specs, prop, steps, isl_only=True, device=device)
+    e1.record()
+    torch.cuda.synchronize(device)
+    learned_ms = e0.elapsed_time(e1)
+    phi_r = inputs.random_phases(seed_base + seeds, count, N_CODE)
+    e0.record()
+    _, h_random = optimise_codes(specs, phi_r, steps, isl_only=True, device=device)
+    e1.record()
+    torch.cuda.synchronize(device)
+    random_ms = e0.elapsed_time(e1)
+    s_l = steps_to_target(h_learned, target)
+    s_r = steps_to_target(h_random, target)
+    return dict(target=target, steps_learned=s_l, steps_random=s_r, isl0_learned=h_learned[0],
+                isl0_random=h_random[0], mlp_ms=mlp_ms, run_ms_learned=learned_ms, run_ms_random=random_ms,
+                steps=steps)

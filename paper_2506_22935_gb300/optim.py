@@ -29,36 +29,50 @@ class Adam:
 
 class PhaseOptimizer:
     """Adam on phases phi [B, N] (float32, CUDA, updated in place) for the loss
-    ``loss`` over ``window`` with Doppler length M."""
+    ``loss`` over ``window`` with Doppler length M; or, with ``plan`` (a
+    graf.BatchPlan), on the packed phases of a ragged batch whose windows and
+    losses the plan holds (phi then [sum N] or [B, N] for equal lengths)."""
 
-    def __init__(self, phi: torch.Tensor, M: int, window: g.Window, loss: g.Loss, adam: Adam = Adam(),
-                 history_len: int = 1000):
-        if phi.dtype != torch.float32 or not phi.is_cuda or phi.dim() != 2 or not phi.is_contiguous():
-            raise ValueError("phi must be a contiguous CUDA float32 tensor [B, N]")
+    def __init__(self, phi: torch.Tensor, M: int = 0, window: g.Window | None = None, loss: g.Loss | None = None,
+                 adam: Adam = Adam(), history_len: int = 1000, plan: "g.BatchPlan | None" = None):
+        if phi.dtype != torch.float32 or not phi.is_cuda or not phi.is_contiguous():
+            raise ValueError("phi must be a contiguous CUDA float32 tensor")
         g.load()
-        self.phi, self.M, self.window, self.loss, self.adam = phi, M, window, loss, adam
-        self.B, self.N = phi.shape
+        self.phi, self.M, self.window, self.loss, self.adam, self.plan = phi, M, window, loss, adam, plan
         dev = phi.device
+        if plan is None:
+            if phi.dim() != 2:
+                raise ValueError("phi must be [B, N]")
+            self.B, self.N = phi.shape
+            self.nb = g.graf_af_backward_workspace_bytes(self.B, self.N, M, window.c())
+            if self.nb == 0:
+                raise g.GrafError(1, "graf_af_backward_workspace_bytes")
+            self.ws = torch.empty(self.nb, dtype=torch.uint8, device=dev)
+            self._wc, self._lc = window.c(), loss.c()
+        else:
+            self.B, self.N = plan.B, int(plan.offsets[-1])
+            self.ws = plan.workspace()
+            self.nb = self.ws.numel()
         self.m = torch.zeros_like(phi)
         self.v = torch.zeros_like(phi)
         self.grad = torch.zeros_like(phi)
         self.out8 = torch.zeros((self.B, 8), dtype=torch.float32, device=dev)
-        self.nb = g.graf_af_backward_workspace_bytes(self.B, self.N, M, window.c())
-        if self.nb == 0:
-            raise g.GrafError(1, "graf_af_backward_workspace_bytes")
-        self.ws = torch.empty(self.nb, dtype=torch.uint8, device=dev)
         self.step_counter = torch.zeros(1, dtype=torch.int32, device=dev)
         self.state = torch.zeros(g.graf_adam_state_bytes(), dtype=torch.uint8, device=dev)
         self.history = torch.full((history_len, self.B), float("nan"), dtype=torch.float32, device=dev)
-        self._wc, self._lc, self._hp = window.c(), loss.c(), adam.c()
+        self._hp = adam.c()
         self._graphs = {}
 
     def enqueue_step(self) -> None:
         """Enqueue one optimisation step on torch's current stream."""
         st = torch.cuda.current_stream(self.phi.device).cuda_stream
-        r = g.graf_af_loss_backward(self.phi.data_ptr(), g.GRAF_IN_PHASE, self.B, self.N, self.M, self._wc,
-                                    self._lc, self.out8.data_ptr(), None, None, self.grad.data_ptr(),
-                                    self.ws.data_ptr(), self.nb, st)
+        if self.plan is None:
+            r = g.graf_af_loss_backward(self.phi.data_ptr(), g.GRAF_IN_PHASE, self.B, self.N, self.M, self._wc,
+                                        self._lc, self.out8.data_ptr(), None, None, self.grad.data_ptr(),
+                                        self.ws.data_ptr(), self.nb, st)
+        else:
+            r = g.graf_batch_loss_backward(self.plan.handle, self.phi.data_ptr(), self.out8.data_ptr(), None,
+                                           self.grad.data_ptr(), self.ws.data_ptr(), self.nb, st)
         if r != 0:
             raise g.GrafError(r, "graf_af_loss_backward")
         r = g.graf_record_loss(self.out8.data_ptr(), self.B, self.history.data_ptr(), self.history.shape[0],
@@ -66,7 +80,7 @@ class PhaseOptimizer:
         if r != 0:
             raise g.GrafError(r, "graf_record_loss")
         r = g.graf_adam_step(self.phi.data_ptr(), self.m.data_ptr(), self.v.data_ptr(), self.grad.data_ptr(),
-                             self.B * self.N, self._hp, self.step_counter.data_ptr(), self.state.data_ptr(), st)
+                             self.phi.numel(), self._hp, self.step_counter.data_ptr(), self.state.data_ptr(), st)
         if r != 0:
             raise g.GrafError(r, "graf_adam_step")
 
