@@ -320,6 +320,76 @@ def run_graf(args):
         dist.destroy_process_group()
 
 
+def run_learned(args):
+    """Time to a masked-ISL target from the learned proposal vs from a random
+    initialisation (the second half of the headline metric).  The proposal is
+    trained end to end through the GRAF layer (spec -> MLP -> phases -> masked
+    loss -> backprop, Sec. 6.1), optionally after a warm start on optimised
+    codes with the phase label loss."""
+    import numpy as np
+    import torch
+
+    from paper_2506_22935_gb300 import graf as g
+    from paper_2506_22935_gb300 import inputs, learned
+
+    g.load()
+    dev = torch.device("cuda", 0)
+    train = inputs.design_specs(SEED + 10, args.train_specs)
+    test = inputs.design_specs(SEED + 11, args.test_specs)
+    net = learned.ProposalMLP(seed=SEED, lr=args.mlp_lr)
+    secs, label_curve, graf_curve = {}, [], []
+    if args.label_epochs > 0:
+        t0 = time.perf_counter()
+        codes, _ = learned.optimise_codes(train, learned.lfm_init(args.train_specs), args.label_steps, device=dev)
+        secs["labels"] = time.perf_counter() - t0
+        feats = torch.from_numpy(inputs.spec_features(train)).to(dev)
+        tgt = torch.from_numpy(codes).to(dev)
+        loss = torch.empty(args.batch_mlp, device=dev)
+        rng = np.random.default_rng(0)
+        t1 = time.perf_counter()
+        for _ in range(args.label_epochs):
+            order = torch.from_numpy(rng.permutation(args.train_specs)).to(dev)
+            for i in range(0, args.train_specs - args.batch_mlp + 1, args.batch_mlp):
+                idx = order[i:i + args.batch_mlp]
+                net.train_step(feats[idx], tgt[idx], loss_out=loss)
+            label_curve.append(float(loss.mean()))
+        torch.cuda.synchronize(dev)
+        secs["label_train"] = time.perf_counter() - t1
+    if args.graf_epochs > 0:
+        t2 = time.perf_counter()
+        trainer = learned.GrafTrainer(net, train, group=args.batch_mlp, isl_only=args.train_isl_only)
+        for _ in range(args.graf_epochs):
+            graf_curve.append(trainer.epoch())
+        torch.cuda.synchronize(dev)
+        trainer.close()
+        secs["graf_train"] = time.perf_counter() - t2
+    r = learned.time_to_target(net, test, steps=args.eval_steps, device=dev)
+    sl, sr = r["steps_learned"], r["steps_random"]
+    ratio = np.median(r["time_learned_ms"] / r["time_random_ms"])
+    every = lambda c: [round(x, 4) for x in c[:: max(1, len(c) // 10)]]
+    line = {"metric": "time to masked-ISL target, learned vs plain", "value": float(ratio),
+            "unit": "median over held-out specs of GPU time to target, learned proposal / random init",
+            "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "dtype": "bf16 mlp, f32 af",
+            "config": {"workload": f"{args.train_specs} training specs, {args.test_specs} held-out, N=1024, M=2048",
+                       "label_epochs": args.label_epochs, "label_steps": args.label_steps,
+                       "graf_epochs": args.graf_epochs, "train_isl_only": args.train_isl_only,
+                       "eval_steps": args.eval_steps},
+            "learned_wins_fraction": float(np.mean(r["time_learned_ms"] < r["time_random_ms"])),
+            "learned_reached_fraction": float(np.mean(sl <= args.eval_steps)),
+            "random_reached_fraction": float(np.mean(sr <= args.eval_steps)),
+            "median_steps_learned": float(np.median(sl)), "median_steps_random": float(np.median(sr)),
+            "median_isl0_learned": float(np.median(r["isl0_learned"])),
+            "median_isl0_random": float(np.median(r["isl0_random"])),
+            "median_final_learned": float(np.median(r["final_learned"])),
+            "median_final_random": float(np.median(r["final_random"])),
+            "median_target": float(np.median(r["target"])),
+            "mlp_inference_ms": r["mlp_ms"],
+            "gpu_ms_per_step_batch": r["run_ms_random"] / args.eval_steps,
+            "label_loss_curve": every(label_curve), "graf_loss_curve": every(graf_curve),
+            "seconds": secs}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -329,11 +399,23 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=B,
                     help="waveforms per GPU (default 256, the benchmark workload; smaller only for profiling)")
+    ap.add_argument("--workload", default="af", choices=["af", "learned"])
+    ap.add_argument("--train-specs", type=int, default=20000)
+    ap.add_argument("--test-specs", type=int, default=512)
+    ap.add_argument("--label-steps", type=int, default=300)
+    ap.add_argument("--label-epochs", type=int, default=0)
+    ap.add_argument("--graf-epochs", type=int, default=400)
+    ap.add_argument("--train-isl-only", type=int, default=1)
+    ap.add_argument("--batch-mlp", type=int, default=256)
+    ap.add_argument("--mlp-lr", type=float, default=1e-3)
+    ap.add_argument("--eval-steps", type=int, default=500)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "learned":
+        run_learned(args)
     else:
         run_graf(args)
 

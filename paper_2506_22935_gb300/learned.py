@@ -88,6 +88,70 @@ class ProposalMLP:
         self._cast()
         return phases
 
+    def train_graf_step(self, feats: torch.Tensor, plan: "g.BatchPlan", ws: torch.Tensor, out8: torch.Tensor,
+                        dphi: torch.Tensor):
+        """One Adam step of the Sec. 6.1 pipeline: spec -> MLP -> phases ->
+        GRAF loss of each spec's own window and weights (``plan``, one
+        waveform of length 1024 per spec row) -> dL/dphi -> MLP backward.
+        ``out8`` [rows, 8] receives the per-spec loss records."""
+        rows = feats.shape[0]
+        stream = self._stream()
+        phases = self.forward(feats)
+        st = g.graf_batch_loss_backward(plan.handle, phases.data_ptr(), out8.data_ptr(), None, dphi.data_ptr(),
+                                        ws.data_ptr(), ws.numel(), stream)
+        if st != 0:
+            raise g.GrafError(st, "graf_batch_loss_backward")
+        st = g.graf_mlp_set_output_grad(dphi.data_ptr(), rows, self._acts.data_ptr(), stream)
+        if st != 0:
+            raise g.GrafError(st, "graf_mlp_set_output_grad")
+        st = g.graf_mlp_backward(rows, self.master.data_ptr(), self.bf16.data_ptr(), self._acts.data_ptr(),
+                                 self.grad.data_ptr(), stream)
+        if st != 0:
+            raise g.GrafError(st, "graf_mlp_backward")
+        st = g.graf_adam_step(self.master.data_ptr(), self.m.data_ptr(), self.v.data_ptr(), self.grad.data_ptr(),
+                              self.master.numel(), self.hp, self.step.data_ptr(), self.state.data_ptr(), stream)
+        if st != 0:
+            raise g.GrafError(st, "graf_adam_step")
+        self._cast()
+        return phases
+
+
+class GrafTrainer:
+    """End-to-end training of a ProposalMLP through the GRAF layer on a fixed
+    set of training specs, split once into groups of ``group`` specs, each
+    with its own batch plan (window and loss per spec); an epoch visits the
+    groups in a fresh random order.  One workspace serves every plan."""
+
+    def __init__(self, mlp: ProposalMLP, specs, group: int = 256, isl_only: bool = True, seed: int = 0):
+        self.mlp, self.group = mlp, group
+        dev = mlp.device
+        count = len(specs["K"])
+        self.feats = torch.from_numpy(inputs.spec_features(specs)).to(dev)
+        self.plans = []
+        nb = 256
+        for c0 in range(0, count - group + 1, group):
+            sub = {k: v[c0:c0 + group] for k, v in specs.items()}
+            windows, losses = spec_windows_losses(sub, isl_only)
+            plan = g.BatchPlan([N_CODE] * group, M=[M_CODE] * group, windows=windows, losses=losses, device=dev)
+            nb = max(nb, g.graf_batch_workspace_bytes(plan.handle))
+            self.plans.append((c0, plan))
+        self.ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+        self.out8 = torch.empty((group, 8), dtype=torch.float32, device=dev)
+        self.dphi = torch.empty((group, N_CODE), dtype=torch.float32, device=dev)
+        self.rng = np.random.default_rng(seed)
+
+    def epoch(self) -> float:
+        """One pass over the groups; returns the mean loss of the last group."""
+        for i in self.rng.permutation(len(self.plans)):
+            c0, plan = self.plans[i]
+            self.mlp.train_graf_step(self.feats[c0:c0 + self.group], plan, self.ws, self.out8, self.dphi)
+        return float(self.out8[:, 0].mean())
+
+    def close(self):
+        for _, plan in self.plans:
+            plan.close()
+        self.plans = []
+
 
 def spec_windows_losses(specs, isl_only=False, beta=50.0):
     windows, losses = [], []
@@ -170,6 +234,13 @@ def time_to_target(mlp: ProposalMLP, specs, steps=500, seeds=4, seed_base=7000, 
     random_ms = e0.elapsed_time(e1)
     s_l = steps_to_target(h_learned, target)
     s_r = steps_to_target(h_random, target)
+    # GPU time per spec: its share of the batch's inference plus the steps it
+    # needs at the batch's measured time per step and spec
+    t_step_l = learned_ms / (steps * count)
+    t_step_r = random_ms / (steps * count)
+    time_l = mlp_ms / count + s_l * t_step_l
+    time_r = s_r * t_step_r
     return dict(target=target, steps_learned=s_l, steps_random=s_r, isl0_learned=h_learned[0],
-                isl0_random=h_random[0], mlp_ms=mlp_ms, run_ms_learned=learned_ms, run_ms_random=random_ms,
-                steps=steps)
+                isl0_random=h_random[0], final_learned=h_learned[-1], final_random=h_random[-1],
+                time_learned_ms=time_l, time_random_ms=time_r, mlp_ms=mlp_ms, run_ms_learned=learned_ms,
+                run_ms_random=random_ms, steps=steps)
