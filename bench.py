@@ -131,12 +131,13 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples_under_load": len(sm)}
 
 
-def _oracle_cols(cols, nthreads=None):
+def _oracle_cols(cols, nthreads=None, want_grad=False):
     """FP64 oracle loss + gradient (forward + backward) of ONE waveform of the
-    workload over all 2047 delays and `cols` Doppler bins centred on m = 0
-    (cols = M is the whole AF).  Every cell costs the same O(N - |k|) in the
-    forward and O(1) per (k, n) in the adjoint, so a Doppler slice is a
-    representative sample.  Returns (cells, seconds, cores)."""
+    workload (waveform 0 of rank 0's batch) over all 2047 delays and `cols`
+    Doppler bins centred on m = 0 (cols = M is the whole AF).  Every cell
+    costs the same O(N - |k|) in the forward and O(1) per (k, n) in the
+    adjoint, so a Doppler slice is a representative sample.  Returns (cells,
+    seconds, cores) and, with want_grad, the phase gradient as well."""
     import numpy as np
 
     import oracle
@@ -147,8 +148,10 @@ def _oracle_cols(cols, nthreads=None):
     win = (-(N - 1), N - 1, m_lo, m_lo + cols - 1, 0, max(M // N - 1, 0))
     cores = nthreads or os.cpu_count() or 1
     t0 = time.perf_counter()
-    oracle.grad(s, M, win, 1.0, 1.0, BETA, EPS, nthreads=cores)
+    _, gp, _ = oracle.grad(s, M, win, 1.0, 1.0, BETA, EPS, nthreads=cores)
     dt = time.perf_counter() - t0
+    if want_grad:
+        return (2 * N - 1) * cols, dt, cores, gp
     return (2 * N - 1) * cols, dt, cores
 
 
@@ -281,6 +284,24 @@ def run_graf(args):
             dist.destroy_process_group()
         return
 
+    cmp, cufft_g0 = None, None
+    if world == 1 and not args.no_cufft:
+        # the same step through cuFFT + eager torch ops (timed comparison only)
+        nl = torch.full((Bb,), N, dtype=torch.int64, device=dev)
+        fn = lambda: cufft_loss_grad(x, nl, M, max(M // N - 1, 0), BETA, EPS, chunk=32)
+        ms_c, (lc_, gc_) = time_cufft(fn, 3, 1, stream)
+        step_call(x.data_ptr(), out8.data_ptr(), grad.data_ptr())
+        torch.cuda.synchronize(dev)
+        cufft_g0 = gc_[0].double().cpu().numpy()
+        cmp = {"value": cells / (ms_c / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms_c,
+               "speedup_of_graf": ms_c / ms_per_step,
+               "loss_max_rel_diff": float(((lc_ - out8[:, 0]).abs() / out8[:, 0].abs()).max()),
+               "grad_rel_l2_diff": float((gc_ - grad).norm() / grad.norm()),
+               "what": "torch.fft (cuFFT) row DFTs + eager torch lag products, magnitudes, "
+                       "log-sum-exp and autograd backward, rows k >= 0 with mirror weights, 32 codes per chunk"}
+        del lc_, gc_
+        torch.cuda.empty_cache()
+
     peaks, src = _measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak_tflops = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12
@@ -300,11 +321,18 @@ def run_graf(args):
                 "executed_frac": executed / (ms_per_step / 1e3) / 1e12 / peak_tflops}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
+        import numpy as np
         cols = _oracle_budget_cols(15.0)
-        cells, dt, cores = _oracle_cols(cols)
+        cells, dt, cores, g_orc = _oracle_cols(cols, want_grad=True)
         cpu = {"value": cells / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"all 2047 delays x {cols} of {M} Doppler bins of 1 of {B} waveforms (N={N}), "
                          f"FP64 loss + gradient, {dt:.1f} s on {cores} threads"}
+        if cols == M:
+            # the whole AF of waveform 0: both GPU gradients against FP64
+            rel = lambda a: float(np.linalg.norm(a - g_orc) / np.linalg.norm(g_orc))
+            cpu["grad_rel_l2_graf_vs_oracle_wave0"] = rel(grad[0].double().cpu().numpy())
+            if cufft_g0 is not None:
+                cmp["grad_rel_l2_vs_oracle_wave0"] = rel(cufft_g0)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -314,10 +342,271 @@ def run_graf(args):
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": Bb * N * 4,
                     "d2h_bytes_per_step": Bb * 8 * 4 + Bb * N * 4},
-            "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary()}
+            "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary(),
+            "cufft_pipeline": cmp}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def cufft_loss_grad(phi, N_len, M_len, box_m, beta, eps, chunk=64):
+    """The comparison pipeline: the same loss and gradient with the row DFTs
+    done by cuFFT (torch.fft) and the rest in eager torch ops with autograd.
+    phi [B, Nmax] fp32 (columns >= N_len[b] ignored), N_len [B] int64 tensor,
+    one M for all.  Rows k >= 0 only, weight 2 for k > 0 (the mirror rows),
+    Omega = every cell minus {k = 0, |m| <= box_m} (box_m an int or a [B]
+    tensor).  Returns (L [B], dL/dphi)."""
+    import torch
+    dev = phi.device
+    Bn, Nmax = phi.shape
+    k = torch.arange(Nmax, device=dev)
+    n = torch.arange(M_len, device=dev)
+    mb = torch.minimum(n, M_len - n)
+    box = torch.as_tensor(box_m, device=dev).expand(Bn)
+    losses, grads = [], []
+    for c0 in range(0, Bn, chunk):
+        p = phi[c0:c0 + chunk].detach().clone().requires_grad_(True)
+        nl = N_len[c0:c0 + chunk]
+        live = (torch.arange(Nmax, device=dev)[None, :] < nl[:, None])
+        s = torch.polar(live.float(), p)
+        s_pad = torch.nn.functional.pad(s, (0, M_len - Nmax))
+        # row k of the lagged signal s[n - k] as a window of s with Nmax - 1
+        # leading zeros (window Nmax - 1 - k), rows put back in k order
+        s_ext = torch.nn.functional.pad(s_pad, (Nmax - 1, 0))
+        lag = s_ext.unfold(-1, M_len, 1).flip(1)
+        R = s_pad[:, None, :] * torch.conj(lag)
+        X = torch.fft.fft(R, dim=-1)
+        E = (s.real ** 2 + s.imag ** 2).sum(dim=1)
+        A2 = (X.real ** 2 + X.imag ** 2 + eps) / (E ** 2)[:, None, None]
+        w = torch.where(k[None, :, None] == 0, 1.0, 2.0) * (k[None, :, None] < nl[:, None, None])
+        w = w * ~((k[None, :, None] == 0) & (mb[None, None, :] <= box[c0:c0 + chunk, None, None]))
+        isl = (w * A2).sum(dim=(1, 2))
+        psl = torch.logsumexp(beta * A2 + torch.log(w), dim=(1, 2)) / beta
+        L = psl + isl
+        (gp,) = torch.autograd.grad(L.sum(), p)
+        losses.append(L.detach())
+        grads.append(gp)
+    return torch.cat(losses), torch.cat(grads)
+
+
+def time_cufft(fn, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, out
+
+
+def _timed_events(fn, steps, warmup, stream, flush=None):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    total = 0.0
+    for _ in range(steps):
+        if flush is not None:
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    return total / steps
+
+
+def run_optim(args):
+    """Masked-ISL phase optimisation: 64 random codes, N = 4096, M = 8192,
+    window |k| <= 512, |m| <= 256 minus the origin, ISL loss, 500 Adam steps
+    (lr 1e-2) captured in one CUDA graph and replayed."""
+    import numpy as np
+    import torch
+
+    from paper_2506_22935_gb300 import graf as g
+    from paper_2506_22935_gb300 import inputs
+    from paper_2506_22935_gb300.optim import Adam, PhaseOptimizer
+
+    g.load()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    B3, N3, M3, K3, W3, STEPS = 64, 4096, 8192, 512, 256, 500
+    phi0 = torch.from_numpy(inputs.random_phases(2506229350 + 3, B3, N3)).to(dev)
+    phi = phi0.clone()
+    opt = PhaseOptimizer(phi, M3, g.Window.masked(K3, W3), g.Loss(0.0, 1.0, BETA, EPS), Adam(lr=1e-2),
+                         history_len=STEPS)
+    opt.capture(STEPS)
+    runs = max(1, args.optim_runs)
+
+    def graph_run():
+        opt.reset(phi0)
+        opt.run(STEPS, graph=True)
+
+    with ClockSampler(0) as clk:
+        ms_graph = _timed_events(graph_run, runs, 1, stream)
+    hist = opt.history.cpu().numpy()
+    ms_eager = _timed_events(lambda: (opt.reset(phi0), opt.run(STEPS, graph=False)), 1, 1, stream)
+    rows = 2 * K3 + 1
+    alg_step = B3 * 2 * rows * 5.0 * M3 * math.log2(M3)
+    peaks, src = _measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    achieved = alg_step * STEPS / (ms_graph / 1e3) / 1e12
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        s = oracle.signal_from_phase(phi0[0].cpu().numpy().astype(np.float64))
+        win = (-K3, K3, -W3, W3, 0, 0)
+        cores = os.cpu_count() or 1
+        t0 = time.perf_counter()
+        oracle.grad(s, M3, win, 0.0, 1.0, BETA, EPS, nthreads=cores)
+        dt = time.perf_counter() - t0
+        cpu = {"value": dt * B3 * STEPS * 1e3, "unit": "ms per run (extrapolated)", "cores": cores,
+               "kind": "oracle", "sample": f"one FP64 loss + gradient of 1 of {B3} codes ({dt:.1f} s), "
+                                           f"x {B3} codes x {STEPS} steps, Adam update not counted"}
+    line = {"metric": "masked-ISL Adam run, 500 steps in one CUDA graph", "value": ms_graph,
+            "unit": "ms per run", "higher_is_better": False, "n_gpus": 1, "steps": runs, "warmup": 1,
+            "ms_per_step": ms_graph / STEPS, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{B3} random codes, N={N3}, M={M3}, |k|<={K3}, |m|<={W3} minus origin, "
+                                   f"ISL, Adam lr 1e-2, {STEPS} steps", "seed": 2506229350 + 3,
+                       "l2": "working set (phases, moments, gradient partials) stays resident across steps"},
+            "eager_ms_per_run": ms_eager,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "algorithmic_flop_per_step": alg_step,
+                         "peak_source": f"FP32 FMA peak at {sm_max:.0f} MHz ({src})"},
+            "isl_median_start": float(np.median(hist[0])), "isl_median_end": float(np.median(hist[-1])),
+            "cpu_baseline": cpu, "gpu_launches": 4 * STEPS * runs, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
+def run_ragged(args):
+    """1000 codes of uneven length N_i log-uniform on [128, 8192], M_i = the
+    next power of two >= 2 N_i, PSL(beta = 50) + ISL over every delay and
+    Doppler bin minus the zero-delay mainlobe, fused loss + gradient."""
+    import numpy as np
+    import torch
+
+    from paper_2506_22935_gb300 import graf as g
+    from paper_2506_22935_gb300 import inputs
+
+    g.load()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    t_start = time.perf_counter()
+    say = lambda what: print(f"[ragged {time.perf_counter() - t_start:7.1f} s] {what}", file=sys.stderr, flush=True)
+    seed = 2506229350 + 4
+    Ns = inputs.uneven_lengths(seed, 1000).astype(np.int64)
+    Ms = np.array([1 << int(math.ceil(math.log2(2 * n))) for n in Ns], dtype=np.int64)
+    phi_h = inputs.random_phases(seed + 1, 1, int(Ns.sum()))[0]
+    x = torch.from_numpy(phi_h).to(dev)
+    cells = float(((2 * Ns - 1) * Ms).sum())
+    alg = float((2 * (2 * Ns - 1) * 5.0 * Ms * np.log2(Ms)).sum())
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    loss = g.Loss(1.0, 1.0, BETA, EPS)
+    plan = g.BatchPlan(Ns.astype(np.int32), losses=[loss], device=dev)
+    out8 = torch.empty((1000, 8), dtype=torch.float32, device=dev)
+    grad = torch.empty_like(x)
+    steps = max(3, min(args.steps, 50))
+
+    def plan_step():
+        plan.loss_backward(x, out8=out8, grad=grad)
+
+    say("plan created")
+    ms_default = _timed_events(plan_step, steps, 3, stream, flush)
+    say(f"untuned plan {ms_default:.2f} ms/step")
+    cache = os.path.join(tempfile.gettempdir(), "graf_autotune_ragged.txt")
+    plan.autotune(x, cache_path=cache)
+    with ClockSampler(0) as clk:
+        ms_tuned = _timed_events(plan_step, steps, 3, stream, flush)
+    info = plan.info()
+    torch.cuda.synchronize()
+    say(f"tuned plan {ms_tuned:.2f} ms/step")
+    ref8, refg = out8.clone(), grad.clone()
+
+    # per-M buckets, each padded to its longest code: one graf_af_loss_backward per bucket
+    offs = np.concatenate([[0], np.cumsum(Ns)])
+    buckets = []
+    for Mb in sorted(set(Ms.tolist())):
+        ids = np.nonzero(Ms == Mb)[0]
+        nmax = int(Ns[ids].max())
+        xs = np.zeros((len(ids), nmax), dtype=np.complex64)
+        for j, b in enumerate(ids):
+            xs[j, :Ns[b]] = np.exp(1j * phi_h[offs[b]:offs[b + 1]].astype(np.float64))
+        xd = torch.from_numpy(xs.view(np.float32).reshape(len(ids), 2 * nmax)).to(dev)
+        w = g.Window.full(nmax, Mb)
+        nb = g.graf_af_backward_workspace_bytes(len(ids), nmax, Mb, w.c())
+        buckets.append((Mb, ids, nmax, xd, w, torch.empty(nb, dtype=torch.uint8, device=dev),
+                        torch.empty((len(ids), 8), dtype=torch.float32, device=dev),
+                        torch.empty((len(ids), 2 * nmax), dtype=torch.float32, device=dev)))
+
+    def padded_step():
+        for Mb, ids, nmax, xd, w, ws, o8, gs in buckets:
+            st = g.graf_af_loss_backward(xd.data_ptr(), g.GRAF_IN_COMPLEX, len(ids), nmax, Mb, w.c(), loss.c(),
+                                         o8.data_ptr(), None, gs.data_ptr(), None, ws.data_ptr(), ws.numel(),
+                                         stream.cuda_stream)
+            assert st == 0, g.graf_status_string(st)
+
+    say("padded buckets set up")
+    ms_padded = _timed_events(padded_step, steps, 3, stream, flush)
+    say(f"padded launches {ms_padded:.2f} ms/step")
+    del buckets
+    torch.cuda.empty_cache()
+
+    cmp = None
+    if not args.no_cufft:
+        parts = []
+        sample = np.arange(0, 1000, args.cufft_stride)
+        for Mb in sorted(set(Ms[sample].tolist())):
+            ids = sample[Ms[sample] == Mb]
+            nmax = int(Ns[ids].max())
+            ph = np.zeros((len(ids), nmax), dtype=np.float32)
+            for j, b in enumerate(ids):
+                ph[j, :Ns[b]] = phi_h[offs[b]:offs[b + 1]]
+            chunk = max(1, (1 << 30) // (nmax * Mb * 8))
+            parts.append((torch.from_numpy(ph).to(dev), torch.from_numpy(Ns[ids]).to(dev), Mb,
+                          torch.from_numpy(np.maximum(Mb // Ns[ids] - 1, 0)).to(dev), chunk, ids))
+
+        def cufft_step():
+            return [cufft_loss_grad(ph, nl, Mb, box, BETA, EPS, chunk=ch) for ph, nl, Mb, box, ch, _ in parts]
+
+        ms_c, res = time_cufft(cufft_step, 1, 0, stream)
+        say(f"cuFFT pipeline {ms_c:.1f} ms/step")
+        lc_ = torch.empty(1000, device=dev)
+        for (ph, nl, Mb, box, ch, ids), (l_, _) in zip(parts, res):
+            lc_[torch.from_numpy(ids).to(dev)] = l_
+        s_cells = float(((2 * Ns[sample] - 1) * Ms[sample]).sum())
+        sl = torch.from_numpy(sample).to(dev)
+        cmp = {"value": s_cells / (ms_c / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms_c,
+               "sample": f"every {args.cufft_stride}th code ({len(sample)} codes, {s_cells:.3g} cells), one pass",
+               "loss_max_rel_diff": float(((lc_[sl] - ref8[sl, 0]).abs() / ref8[sl, 0].abs()).max()),
+               "what": "per-M buckets padded to the longest code, torch.fft (cuFFT) + eager torch ops + autograd"}
+        del res, parts
+        torch.cuda.empty_cache()
+    plan.close()
+    peaks, src = _measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    achieved = alg / (ms_tuned / 1e3) / 1e12
+    line = {"metric": "ragged-batch AF fwd+bwd Gcells/s", "value": cells / (ms_tuned / 1e3) / 1e9,
+            "unit": UNIT, "higher_is_better": True, "n_gpus": 1, "steps": steps, "warmup": 3,
+            "ms_per_step": ms_tuned, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "1000 random codes, N_i log-uniform on [128, 8192], M_i = nextpow2(2 N_i), "
+                                   "all delays and Doppler bins minus the zero-delay mainlobe, PSL(beta=50)+ISL, "
+                                   "loss + gradient w.r.t. phases", "seed": seed, "cells_per_step": cells,
+                       "l2": "flushed between steps (256 MB write, outside the timed events)"},
+            "untuned_plan_ms": ms_default, "padded_per_M_launches_ms": ms_padded,
+            "plan": info,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None, "algorithmic_flop_per_step": alg,
+                         "peak_source": f"FP32 FMA peak at {sm_max:.0f} MHz ({src})"},
+            "cufft_pipeline": cmp, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
 
 
 def run_learned(args):
@@ -397,9 +686,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="graf", choices=["graf", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison pipeline")
     ap.add_argument("--batch", type=int, default=B,
                     help="waveforms per GPU (default 256, the benchmark workload; smaller only for profiling)")
-    ap.add_argument("--workload", default="af", choices=["af", "learned"])
+    ap.add_argument("--workload", default="af", choices=["af", "learned", "optim", "ragged"])
+    ap.add_argument("--optim-runs", type=int, default=3)
+    ap.add_argument("--cufft-stride", type=int, default=50,
+                    help="ragged workload: the cuFFT comparison runs on every n-th code")
     ap.add_argument("--train-specs", type=int, default=20000)
     ap.add_argument("--test-specs", type=int, default=512)
     ap.add_argument("--label-steps", type=int, default=300)
@@ -416,6 +709,10 @@ def main():
         run_reference(args)
     elif args.workload == "learned":
         run_learned(args)
+    elif args.workload == "optim":
+        run_optim(args)
+    elif args.workload == "ragged":
+        run_ragged(args)
     else:
         run_graf(args)
 
