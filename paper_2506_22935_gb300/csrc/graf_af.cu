@@ -26,12 +26,14 @@ __global__ void loss_finalize_kernel(AfParams p, float* out8) {
     if (b >= p.B) return;
     const Wave wv = wave_of(p, b);
     const double beta = wv.beta;
-    double isl = 0.0, mx = -CUDART_INF, z = 0.0, T = 0.0;
+    const bool fixed = wv.lse_fix > 0.0f;
+    double isl = 0.0, mx = -CUDART_INF, z = 0.0, T = 0.0, hard = -CUDART_INF;
     for (int i = lane; i < wv.tiles; i += 32) {
         const float4 r = p.rec[wv.rec_off + i];
         isl += r.x;
+        hard = fmax(hard, (double)r.y);
         if (r.y > -CUDART_INF_F) {
-            const double m2 = r.y;
+            const double m2 = fixed ? (double)wv.lse_fix : (double)r.y;
             if (m2 > mx) {
                 const double f = exp(beta * (mx - m2));
                 z = z * f + r.z;
@@ -50,6 +52,7 @@ __global__ void loss_finalize_kernel(AfParams p, float* out8) {
         const double m2 = __shfl_xor_sync(0xffffffffu, mx, o);
         const double z2 = __shfl_xor_sync(0xffffffffu, z, o);
         const double t2 = __shfl_xor_sync(0xffffffffu, T, o);
+        hard = fmax(hard, __shfl_xor_sync(0xffffffffu, hard, o));
         isl += i2;
         if (m2 > mx) {
             const double f = exp(beta * (mx - m2));
@@ -73,7 +76,7 @@ __global__ void loss_finalize_kernel(AfParams p, float* out8) {
             o[0] = (float)(wv.w_psl * psl_soft + wv.w_isl * isl);
             o[1] = (float)psl_soft;
             o[2] = (float)isl;
-            o[3] = (float)mx;
+            o[3] = (float)hard;
             o[6] = (float)(T / z);
         }
         o[5] = (float)cnt;
@@ -85,7 +88,7 @@ __global__ void loss_finalize_kernel(AfParams p, float* out8) {
     if (p.scale) {
         psl_soft = __shfl_sync(0xffffffffu, psl_soft, 0);
         for (int i = lane; i < wv.tiles; i += 32) {
-            const float m = p.rec[wv.rec_off + i].y;
+            const float m = fixed ? wv.lse_fix : p.rec[wv.rec_off + i].y;
             float f = 1.0f;
             if (wv.w_psl != 0.0f && !wv.unscaled)
                 f = m > -CUDART_INF_F ? (float)exp(beta * ((double)m - psl_soft)) : 0.0f;

@@ -231,6 +231,11 @@ __device__ __forceinline__ void loss_item(const AfParams& p, int b, int tile, un
             const float4 c = wred[w];
             lse_merge(a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w, bl2);
         }
+        if (wv.lse_fix > 0.0f && a.y > -CUDART_INF_F) {  // sums relative to the fixed shift
+            const float f = ex2a((a.y - wv.lse_fix) * bl2);
+            a.z *= f;
+            a.w *= f;
+        }
         p.rec[wv.rec_off + tile] = a;
     }
 }
@@ -512,7 +517,9 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
     const int iters = (wv.rows_per_tile + SLOTS - 1) / SLOTS;
 
     float isl = 0.0f, zs = 0.0f, ts = 0.0f, cs = 0.0f;
-    float mx = -CUDART_INF_F;  // slot-uniform shift (in a2 units)
+    const bool fixed = wv.lse_fix > 0.0f;      // fixed shift: no running maximum
+    float mx = fixed ? wv.lse_fix : -CUDART_INF_F;  // slot-uniform shift (in a2 units)
+    float hm[2] = {-CUDART_INF_F, -CUDART_INF_F};  // largest weighted a2 (fixed shift)
     float2 v[P::VALS];
     for (int it = 0; it < iters; ++it) {
         const int k = row0 + slot + it * SLOTS;
@@ -531,15 +538,18 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
             const bool uniform = !valid || (rmk.one == full_mask && (rmk.two == 0ull || rmk.two == full_mask));
             const float wrow = valid ? (rmk.two != 0ull ? 2.0f : (rmk.one != 0ull ? 1.0f : 0.0f)) : 0.0f;
             const float wb = valid ? (float)base_weight(wv, k) : 0.0f;
-            // pass 1: largest weighted a2 of the row (two independent chains)
+            // pass 1 (running shift only): largest weighted a2 of the row
+            // (two independent chains)
             float tmx[2] = {-CUDART_INF_F, -CUDART_INF_F};
-            sfor<0, P::VALS>([&](auto w) {
-                const float2 x = v[w];
-                const float a2 = fmaf(fmaf(x.x, x.x, x.y * x.y), invE2, eps_n);
-                const float wt = uniform ? wrow : mweight<decltype(w)::value>(rmk);
-                tmx[w & 1] = fmaxf(tmx[w & 1], wt > 0.0f ? a2 : -CUDART_INF_F);
-            });
-            const float rmx = slot_max<P::TPR>(fmaxf(tmx[0], tmx[1]), red + 8, slot);
+            if (!fixed) {
+                sfor<0, P::VALS>([&](auto w) {
+                    const float2 x = v[w];
+                    const float a2 = fmaf(fmaf(x.x, x.x, x.y * x.y), invE2, eps_n);
+                    const float wt = uniform ? wrow : mweight<decltype(w)::value>(rmk);
+                    tmx[w & 1] = fmaxf(tmx[w & 1], wt > 0.0f ? a2 : -CUDART_INF_F);
+                });
+            }
+            const float rmx = fixed ? mx : slot_max<P::TPR>(fmaxf(tmx[0], tmx[1]), red + 8, slot);
             if (rmx > mx) {  // slot-uniform
                 const float f = ex2a((mx - rmx) * bl2);  // 0 while mx = -inf
                 zs *= f;
@@ -566,6 +576,7 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
                 const float a2 = fmaf(fmaf(x.x, x.x, x.y * x.y), invE2, eps_n);
                 const float wt = uniform ? wrow : mweight<decltype(w)::value>(rmk);
                 const float e = wt > 0.0f ? ex2a(fmaf(a2, bl2, -sh)) : 0.0f;
+                hm[h] = fmaxf(hm[h], wt > 0.0f ? a2 : -CUDART_INF_F);
                 const float we = wt * e;
                 r_isl[h] = fmaf(wt, a2, r_isl[h]);
                 r_z[h] += we;
@@ -585,8 +596,9 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
         }
         scatter_row<M, HALF, true>(v, acc, s_sm, wv.N, k, t, grad_row, slot, turns, my_turn);
     }
-    // bring every slot to the CTA's largest shift
-    float cmx = mx;
+    // bring every slot to the CTA's largest shift (fixed shift: the CTA's
+    // largest weighted a2, the record's hard maximum)
+    float cmx = fixed ? fmaxf(hm[0], hm[1]) : mx;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) cmx = fmaxf(cmx, __shfl_xor_sync(0xffffffffu, cmx, o));
     if ((tid & 31) == 0) red[tid >> 5] = cmx;
@@ -595,10 +607,10 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
 #pragma unroll
     for (int w = 1; w < NW; ++w) cmx = fmaxf(cmx, red[w]);
     __syncthreads();
-    const float fs = (mx > -CUDART_INF_F) ? ex2a((mx - cmx) * bl2) : 0.0f;
+    const float fs = fixed ? 1.0f : (mx > -CUDART_INF_F) ? ex2a((mx - cmx) * bl2) : 0.0f;
     zs *= fs;
     ts *= fs;
-    if (psl_mode) {
+    if (psl_mode && !fixed) {
         cs *= fs;
         for (int n = t; n < wv.N; n += P::TPR) {
             const float2 a = acc[n];

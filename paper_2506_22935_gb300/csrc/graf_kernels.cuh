@@ -74,6 +74,13 @@ struct Wave {
     int k_lo, k_hi, m_lo, m_hi, k_ml, m_ml;
     int r_lo, r_hi, rows_per_tile, tiles, full_m, defer_hi, unscaled;
     float eps, beta, w_psl, w_isl;
+    // Fixed log-sum-exp shift (in units of Ahat^2), 0 = none.  For phase
+    // input E = N and every cell has a2 = |X|^2/E^2 + eps/E^2 <= 1 + eps/N^2
+    // (|X[k,m]| <= E by Cauchy-Schwarz), so with m = (1 + eps/N^2)/2 the terms
+    // exp(beta (a2 - m)) stay within 2^(+-88) whenever beta log2(e) m <= 88:
+    // no running maximum is needed.  Per-CTA loss records hold their sums
+    // relative to this shift when it is set, else relative to their maximum.
+    float lse_fix;
 };
 
 __host__ __device__ __forceinline__ Wave wave_of(const AfParams& p, int b) {
@@ -104,6 +111,11 @@ __host__ __device__ __forceinline__ Wave wave_of(const AfParams& p, int b) {
         w.eps = p.eps; w.beta = p.beta; w.w_psl = p.w_psl; w.w_isl = p.w_isl;
     }
     w.full_m = (w.m_lo == -(w.M / 2) && w.m_hi == w.M / 2 - 1) ? 1 : 0;
+    w.lse_fix = 0.0f;
+    if (w.kind == 1) {
+        const float m = 0.5f * (1.0f + w.eps / ((float)w.N * (float)w.N));
+        if (w.beta * 1.4426950408889634f * m <= 88.0f) w.lse_fix = m;
+    }
     return w;
 }
 
