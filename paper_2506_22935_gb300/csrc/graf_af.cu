@@ -107,9 +107,10 @@ __device__ __forceinline__ float2 signal_at(const Wave& wv, int n) {
 }
 
 // dL/ds* of the FFT part: scaled sum of the per-CTA partials of the first
-// set plus the unscaled second set (deferred rows), in a fixed order; the
-// same for the per-CTA sums of c a2.
-__device__ __forceinline__ float2 sum_partials(const AfParams& p, const Wave& wv, int b, int n, double* cs) {
+// set (g1) and the unscaled second set (deferred rows, g2), each in a fixed
+// order; the same for the per-CTA sums of c a2.
+__device__ __forceinline__ void sum_partials(const AfParams& p, const Wave& wv, int b, int n, float2& g1s,
+                                             float2& g2s, double* cs) {
     const float2* g1 = p.gpart + wv.gpart_off + n;
     float2 g = make_float2(0.0f, 0.0f);
     double c = 0.0;
@@ -120,6 +121,8 @@ __device__ __forceinline__ float2 sum_partials(const AfParams& p, const Wave& wv
         g.y = fmaf(f, a.y, g.y);
         if (cs) c += (double)f * p.csum[wv.rec_off + i];
     }
+    g1s = g;
+    g = make_float2(0.0f, 0.0f);
     if (p.gpart2) {
         const float2* g2 = p.gpart2 + (size_t)b * p.tiles2 * p.N + n;
         for (int i = 0; i < p.tiles2; ++i) {
@@ -127,22 +130,28 @@ __device__ __forceinline__ float2 sum_partials(const AfParams& p, const Wave& wv
             if (cs) c += p.csum2[(size_t)b * p.tiles2 + i];
         }
     }
+    g2s = g;
     if (cs) *cs = c;
-    return g;
 }
 
 // grad_phi = 2 Im(dL/ds* conj(s)): the row-uniform part and the energy terms
-// are s[n] times real numbers and contribute nothing to it.
+// are s[n] times real numbers and contribute nothing to it.  In phase-only
+// mode the first set already holds Im(dL/ds* conj(s)) (real accumulators);
+// the second set (deferred rows) is always complex.
 __global__ void grad_phi_kernel(AfParams p, const float* dL, float* grad_phi) {
     const int nblk = (p.N + blockDim.x - 1) / blockDim.x;
     const int b = blockIdx.x / nblk;
     const int n = (blockIdx.x % nblk) * blockDim.x + threadIdx.x;
     const Wave wv = wave_of(p, b);
     if (n >= wv.N) return;
-    const float2 g = sum_partials(p, wv, b, n, nullptr);
+    float2 g1, g2;
+    sum_partials(p, wv, b, n, g1, g2, nullptr);
     const float2 s = signal_at(wv, n);
     const float scale = 2.0f * (dL ? dL[b] : 1.0f);
-    grad_phi[wv.out_off + n] = scale * (g.y * s.x - g.x * s.y);
+    float im;
+    if (p.phase_only) im = g1.x + (g2.y * s.x - g2.x * s.y);
+    else im = (g1.y + g2.y) * s.x - (g1.x + g2.x) * s.y;
+    grad_phi[wv.out_off + n] = scale * im;
 }
 
 // Per waveform, in FP64: U = sum_k w_b(k) (C[k] + eps) over the transformed
@@ -210,7 +219,9 @@ __global__ void grad_s_kernel(AfParams p, const float* dL, float2* grad_s, float
     const int n = n0 + threadIdx.x;
     if (n >= wv.N) return;
     double cs = 0.0;
-    const float2 g = sum_partials(p, wv, b, n, &cs);
+    float2 g1, g2;
+    sum_partials(p, wv, b, n, g1, g2, &cs);
+    const float2 g = cadd(g1, g2);
     const float2 s = signal_at(wv, n);
     const float* sv = p.saved8 + (size_t)b * 8;
     const double E = p.usum[2 * b + 1];

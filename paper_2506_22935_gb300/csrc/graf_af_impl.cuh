@@ -323,8 +323,63 @@ __device__ __forceinline__ void scatter_row(const float2* v, float2* acc, const 
     }
 }
 
+// Phase-only gradient with a real accumulator.  grad_phi[p] = 2 Im(g[p]
+// s*[p]) and the two Wirtinger terms of row k give
+//   Im(G_R[k,n] s[n-k] s*[n]) = q[k,n]          at p = n,
+//   Im(conj(G_R[k,n]) s[n] s*[n-k]) = -q[k,n]   at p = n - k,
+// with q = Im(G_R conj(R)), R[k,n] = s[n] conj(s[n-k]) (Eq. 8): one real
+// number per cell, added at n and subtracted at n - k.  v holds conj(G_R)
+// (CONJ form), so q = -Im(v R).  Row 0 cancels exactly (n = n - k).
+template <int M, bool HALF>
+__device__ __forceinline__ void scatter_row_real(const float2* v, float* acc, const float2* s_sm, int N,
+                                                 int k, int t, bool active, int slot, int turns,
+                                                 int my_turn) {
+    using P = RowPlan<M>;
+    constexpr int WN = HALF ? P::VALS / 2 : P::VALS;
+    float q[WN];
+    sfor<0, WN>([&](auto w) {
+        const int n = t + P::TPR * decltype(w)::value;
+        q[w] = 0.0f;
+        if (active && (unsigned)(n - k) < (unsigned)(N - k)) {
+            const float2 r = cmulc(s_sm[n], s_sm[n - k]);
+            q[w] = -fmaf(v[w].x, r.y, v[w].y * r.x);
+        }
+    });
+    auto scatter_a = [&]() {
+        if (!active) return;
+        sfor<0, WN>([&](auto w) {
+            const int n = t + P::TPR * decltype(w)::value;
+            if ((unsigned)(n - k) < (unsigned)(N - k)) acc[n] += q[w];
+        });
+    };
+    auto scatter_b = [&]() {
+        if (!active) return;
+        sfor<0, WN>([&](auto w) {
+            const int n = t + P::TPR * decltype(w)::value;
+            if ((unsigned)(n - k) < (unsigned)(N - k)) acc[n - k] -= q[w];
+        });
+    };
+    if (turns == 1) {
+        scatter_a();
+        row_sync<P::TPR>(slot);
+        scatter_b();
+        row_sync<P::TPR>(slot);
+    } else {
+        for (int tt = 0; tt < turns; ++tt) {
+            if (tt == my_turn) scatter_a();
+            __syncthreads();
+        }
+        for (int tt = 0; tt < turns; ++tt) {
+            if (tt == my_turn) scatter_b();
+            __syncthreads();
+        }
+    }
+}
+
 // Per-CTA partial sums of the gradient accumulators and one scalar, in a
-// fixed order (warp xor tree, then warps in order).
+// fixed order (warp xor tree, then warps in order).  Phase-only mode: the
+// accumulators are real (copy i at floats [i N, (i+1) N)) and a partial is
+// stored as (sum, 0).
 template <int M>
 __device__ __forceinline__ void write_grad_partial(const AfParams& p, const Wave& wv, const float2* acc_all,
                                                    float* red, float cs, int tile) {
@@ -339,6 +394,15 @@ __device__ __forceinline__ void write_grad_partial(const AfParams& p, const Wave
         p.csum[wv.rec_off + tile] = s;
     }
     float2* out = p.gpart + wv.gpart_off + (long long)tile * wv.N;
+    if (p.phase_only) {
+        const float* acc_r = reinterpret_cast<const float*>(acc_all);
+        for (int n = tid; n < wv.N; n += kThreads) {
+            float a = acc_r[n];
+            for (int s = 1; s < p.acc_copies; ++s) a += acc_r[(size_t)s * wv.N + n];
+            out[n] = make_float2(a, 0.0f);
+        }
+        return;
+    }
     for (int n = tid; n < wv.N; n += kThreads) {
         float2 a = acc_all[n];
         for (int s = 1; s < p.acc_copies; ++s) a = cadd(a, acc_all[(size_t)s * wv.N + n]);
@@ -381,6 +445,7 @@ __device__ __forceinline__ void backward_item(const AfParams& p, int b, int tile
     const int turns = SLOTS / p.acc_copies;
     const int my_turn = slot / p.acc_copies;
     float2* acc = acc_all + (size_t)(slot % p.acc_copies) * wv.N;
+    float* acc_r = reinterpret_cast<float*>(acc_all) + (size_t)(slot % p.acc_copies) * wv.N;
 
     const int row0 = wv.r_lo + tile * wv.rows_per_tile;
     const int row_end = min(row0 + wv.rows_per_tile, wv.r_hi + 1);
@@ -420,7 +485,10 @@ __device__ __forceinline__ void backward_item(const AfParams& p, int b, int tile
                 v[w] = make_float2(c * x.x, -c * x.y);
             });
         }
-        scatter_row<M, HALF, true>(v, acc, s_sm, wv.N, k, t, valid, slot, turns, my_turn);
+        if (p.phase_only)
+            scatter_row_real<M, HALF>(v, acc_r, s_sm, wv.N, k, t, valid, slot, turns, my_turn);
+        else
+            scatter_row<M, HALF, true>(v, acc, s_sm, wv.N, k, t, valid, slot, turns, my_turn);
     }
     write_grad_partial<M>(p, wv, acc_all, red, csum, tile);
 }
@@ -511,6 +579,7 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
     const int turns = SLOTS / p.acc_copies;
     const int my_turn = slot / p.acc_copies;
     float2* acc = acc_all + (size_t)(slot % p.acc_copies) * wv.N;
+    float* acc_r = reinterpret_cast<float*>(acc_all) + (size_t)(slot % p.acc_copies) * wv.N;
 
     const int row0 = wv.r_lo + tile * wv.rows_per_tile;
     const int row_end = min(row0 + wv.rows_per_tile, wv.r_hi + 1);
@@ -557,9 +626,13 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
                 if (psl_mode) {
                     cs *= f;
                     if (mx > -CUDART_INF_F) {  // the slot owns its accumulator on this path
-                        for (int n = t; n < wv.N; n += P::TPR) {
-                            const float2 a = acc[n];
-                            acc[n] = make_float2(a.x * f, a.y * f);
+                        if (p.phase_only) {
+                            for (int n = t; n < wv.N; n += P::TPR) acc_r[n] *= f;
+                        } else {
+                            for (int n = t; n < wv.N; n += P::TPR) {
+                                const float2 a = acc[n];
+                                acc[n] = make_float2(a.x * f, a.y * f);
+                            }
                         }
                     }
                 }
@@ -594,7 +667,10 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
                 if (!grad_row) break;  // slot-uniform: the slot is one or more whole warps
             }
         }
-        scatter_row<M, HALF, true>(v, acc, s_sm, wv.N, k, t, grad_row, slot, turns, my_turn);
+        if (p.phase_only)
+            scatter_row_real<M, HALF>(v, acc_r, s_sm, wv.N, k, t, grad_row, slot, turns, my_turn);
+        else
+            scatter_row<M, HALF, true>(v, acc, s_sm, wv.N, k, t, grad_row, slot, turns, my_turn);
     }
     // bring every slot to the CTA's largest shift (fixed shift: the CTA's
     // largest weighted a2, the record's hard maximum)
@@ -612,9 +688,13 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
     ts *= fs;
     if (psl_mode && !fixed) {
         cs *= fs;
-        for (int n = t; n < wv.N; n += P::TPR) {
-            const float2 a = acc[n];
-            acc[n] = make_float2(a.x * fs, a.y * fs);
+        if (p.phase_only) {
+            for (int n = t; n < wv.N; n += P::TPR) acc_r[n] *= fs;
+        } else {
+            for (int n = t; n < wv.N; n += P::TPR) {
+                const float2 a = acc[n];
+                acc[n] = make_float2(a.x * fs, a.y * fs);
+            }
         }
     }
     // loss record {ISL, mx, sum e, sum e a2}, all relative to the CTA shift
