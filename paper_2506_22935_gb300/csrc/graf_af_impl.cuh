@@ -641,28 +641,62 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
             // pass 2: loss partials and the gradient remainder, v = conj(c X)
             const float sh = mx * bl2;
             const float e0 = ex2a(-sh);
-            // row sums in two independent chains each (even / odd registers)
-            float r_isl[2] = {0.0f, 0.0f}, r_z[2] = {0.0f, 0.0f}, r_t[2] = {0.0f, 0.0f}, r_c[2] = {0.0f, 0.0f};
-            sfor<0, P::VALS>([&](auto w) {
-                constexpr int h = decltype(w)::value & 1;
-                const float2 x = v[w];
-                const float a2 = fmaf(fmaf(x.x, x.x, x.y * x.y), invE2, eps_n);
-                const float wt = uniform ? wrow : mweight<decltype(w)::value>(rmk);
-                const float e = wt > 0.0f ? ex2a(fmaf(a2, bl2, -sh)) : 0.0f;
-                hm[h] = fmaxf(hm[h], wt > 0.0f ? a2 : -CUDART_INF_F);
-                const float we = wt * e;
-                r_isl[h] = fmaf(wt, a2, r_isl[h]);
-                r_z[h] += we;
-                r_t[h] = fmaf(we, a2, r_t[h]);
-                float c = 0.0f;
-                if (grad_row) c = psl_mode ? wt * (e - e0) * cP : (wt - wb) * cI;
-                r_c[h] = fmaf(c, a2, r_c[h]);
-                v[w] = make_float2(c * x.x, -c * x.y);
-            });
-            isl += r_isl[0] + r_isl[1];
-            zs += r_z[0] + r_z[1];
-            ts += r_t[0] + r_t[1];
-            cs += r_c[0] + r_c[1];
+            if (__all_sync(0xffffffffu, uniform && wrow > 0.0f)) {
+                // every cell of the row carries weight wrow: accumulate
+                // P = sum |X|^2, Z = sum e, Q = sum e |X|^2 and apply the
+                // weight, 1/E^2 and eps once per row.  e = exp(beta (a2 - mx))
+                // from |X|^2 in one FMA; c = Kp (e - e0) + Ki.
+                const float Kp = (grad_row && psl_mode) ? wrow * cP : 0.0f;
+                const float Ki = (grad_row && !psl_mode) ? (wrow - wb) * cI : 0.0f;
+                const float Kc0 = fmaf(-e0, Kp, Ki);
+                const float kexp = invE2 * bl2, kofs = fmaf(eps_n, bl2, -sh);
+                float rP[2] = {0.0f, 0.0f}, rZ[2] = {0.0f, 0.0f}, rQ[2] = {0.0f, 0.0f};
+                float rH[2] = {0.0f, 0.0f};
+                sfor<0, P::VALS>([&](auto w) {
+                    constexpr int h = decltype(w)::value & 1;
+                    const float2 x = v[w];
+                    const float p2 = fmaf(x.x, x.x, x.y * x.y);
+                    const float e = ex2a(fmaf(p2, kexp, kofs));
+                    rH[h] = fmaxf(rH[h], p2);
+                    rP[h] += p2;
+                    rZ[h] += e;
+                    rQ[h] = fmaf(e, p2, rQ[h]);
+                    const float c = fmaf(e, Kp, Kc0);
+                    v[w] = make_float2(c * x.x, -c * x.y);
+                });
+                const float sa2 = fmaf(rP[0] + rP[1], invE2, (float)P::VALS * eps_n);  // sum a2
+                const float Zr = rZ[0] + rZ[1];
+                const float sea2 = fmaf(rQ[0] + rQ[1], invE2, eps_n * Zr);            // sum e a2
+                isl = fmaf(wrow, sa2, isl);
+                zs = fmaf(wrow, Zr, zs);
+                ts = fmaf(wrow, sea2, ts);
+                cs += fmaf(Kp, fmaf(-e0, sa2, sea2), Ki * sa2);
+                hm[0] = fmaxf(hm[0], fmaf(fmaxf(rH[0], rH[1]), invE2, eps_n));
+            } else {
+                // row sums in two independent chains each (even / odd registers)
+                float r_isl[2] = {0.0f, 0.0f}, r_z[2] = {0.0f, 0.0f}, r_t[2] = {0.0f, 0.0f};
+                float r_c[2] = {0.0f, 0.0f};
+                sfor<0, P::VALS>([&](auto w) {
+                    constexpr int h = decltype(w)::value & 1;
+                    const float2 x = v[w];
+                    const float a2 = fmaf(fmaf(x.x, x.x, x.y * x.y), invE2, eps_n);
+                    const float wt = uniform ? wrow : mweight<decltype(w)::value>(rmk);
+                    const float e = wt > 0.0f ? ex2a(fmaf(a2, bl2, -sh)) : 0.0f;
+                    hm[h] = fmaxf(hm[h], wt > 0.0f ? a2 : -CUDART_INF_F);
+                    const float we = wt * e;
+                    r_isl[h] = fmaf(wt, a2, r_isl[h]);
+                    r_z[h] += we;
+                    r_t[h] = fmaf(we, a2, r_t[h]);
+                    float c = 0.0f;
+                    if (grad_row) c = psl_mode ? wt * (e - e0) * cP : (wt - wb) * cI;
+                    r_c[h] = fmaf(c, a2, r_c[h]);
+                    v[w] = make_float2(c * x.x, -c * x.y);
+                });
+                isl += r_isl[0] + r_isl[1];
+                zs += r_z[0] + r_z[1];
+                ts += r_t[0] + r_t[1];
+                cs += r_c[0] + r_c[1];
+            }
             if constexpr (P::TPR >= 32) {
                 if (!grad_row) break;  // slot-uniform: the slot is one or more whole warps
             }
