@@ -566,15 +566,22 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
     const int tid = threadIdx.x, slot = tid / P::TPR, t = tid % P::TPR;
     for (int i = tid; i < p.acc_copies * wv.N; i += kThreads) acc_all[i] = make_float2(0.0f, 0.0f);
     const float E = load_signal(wv, s_sm, red);  // includes __syncthreads
-    if (tile == 0 && tid == 0) p.out8[(size_t)b * 8 + 4] = E;
-    const float invE2 = 1.0f / (E * E);
-    const float eps_n = wv.eps * invE2;
-    const float bl2 = wv.beta * 1.4426950408889634f;  // beta * log2(e)
-    const bool psl_mode = wv.w_psl != 0.0f;
-    const float cP = wv.w_psl * invE2;
-    const float cI = wv.w_isl * invE2;
+    // the item's constants live in shared memory and are re-read after each
+    // transform, so that none of them occupies a register during the FFTs
+    __shared__ float s_k[6];
+    if (tid == 0) {
+        if (tile == 0) p.out8[(size_t)b * 8 + 4] = E;
+        const float invE2 = 1.0f / (E * E);
+        const float bl2 = wv.beta * 1.4426950408889634f;  // beta * log2(e)
+        s_k[0] = invE2;
+        s_k[1] = wv.eps * invE2;   // eps / E^2
+        s_k[2] = bl2;
+        s_k[3] = wv.w_psl * invE2;  // cP
+        s_k[4] = wv.w_isl * invE2;  // cI
+        s_k[5] = invE2 * bl2;       // exponent per unit |X|^2
+    }
+    __syncthreads();
     float2* buf = bufs + (size_t)slot * (P::SPLIT ? P::SMEM_ROW / 2 : P::SMEM_ROW);
-    const ColMasks cm = col_masks<M>(wv, t);
     constexpr unsigned long long full_mask = P::VALS == 64 ? ~0ull : ((1ull << P::VALS) - 1ull);
     const int turns = SLOTS / p.acc_copies;
     const int my_turn = slot / p.acc_copies;
@@ -588,7 +595,7 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
     float isl = 0.0f, zs = 0.0f, ts = 0.0f, cs = 0.0f;
     const bool fixed = wv.lse_fix > 0.0f;      // fixed shift: no running maximum
     float mx = fixed ? wv.lse_fix : -CUDART_INF_F;  // slot-uniform shift (in a2 units)
-    float hm[2] = {-CUDART_INF_F, -CUDART_INF_F};  // largest weighted a2 (fixed shift)
+    float hm = -CUDART_INF_F;  // largest weighted a2 (fixed shift)
     float2 v[P::VALS];
     for (int it = 0; it < iters; ++it) {
         const int k = row0 + slot + it * SLOTS;
@@ -603,60 +610,32 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
             row_sync<P::TPR>(slot);
             row_fft<M, false, false, false>(v, buf, t, slot);
             if (ph == 1) break;
-            const RowMasks rmk = row_masks(wv, cm, k);
-            const bool uniform = !valid || (rmk.one == full_mask && (rmk.two == 0ull || rmk.two == full_mask));
-            const float wrow = valid ? (rmk.two != 0ull ? 2.0f : (rmk.one != 0ull ? 1.0f : 0.0f)) : 0.0f;
+            const float invE2 = s_k[0], eps_n = s_k[1], bl2 = s_k[2], cP = s_k[3], cI = s_k[4];
+            const bool psl_mode = wv.w_psl != 0.0f;
             const float wb = valid ? (float)base_weight(wv, k) : 0.0f;
-            // pass 1 (running shift only): largest weighted a2 of the row
-            // (two independent chains)
-            float tmx[2] = {-CUDART_INF_F, -CUDART_INF_F};
-            if (!fixed) {
-                sfor<0, P::VALS>([&](auto w) {
-                    const float2 x = v[w];
-                    const float a2 = fmaf(fmaf(x.x, x.x, x.y * x.y), invE2, eps_n);
-                    const float wt = uniform ? wrow : mweight<decltype(w)::value>(rmk);
-                    tmx[w & 1] = fmaxf(tmx[w & 1], wt > 0.0f ? a2 : -CUDART_INF_F);
-                });
-            }
-            const float rmx = fixed ? mx : slot_max<P::TPR>(fmaxf(tmx[0], tmx[1]), red + 8, slot);
-            if (rmx > mx) {  // slot-uniform
-                const float f = ex2a((mx - rmx) * bl2);  // 0 while mx = -inf
-                zs *= f;
-                ts *= f;
-                if (psl_mode) {
-                    cs *= f;
-                    if (mx > -CUDART_INF_F) {  // the slot owns its accumulator on this path
-                        if (p.phase_only) {
-                            for (int n = t; n < wv.N; n += P::TPR) acc_r[n] *= f;
-                        } else {
-                            for (int n = t; n < wv.N; n += P::TPR) {
-                                const float2 a = acc[n];
-                                acc[n] = make_float2(a.x * f, a.y * f);
-                            }
-                        }
-                    }
-                }
-                mx = rmx;
-            }
-            // pass 2: loss partials and the gradient remainder, v = conj(c X)
-            const float sh = mx * bl2;
-            const float e0 = ex2a(-sh);
-            if (__all_sync(0xffffffffu, uniform && wrow > 0.0f)) {
-                // every cell of the row carries weight wrow: accumulate
-                // P = sum |X|^2, Z = sum e, Q = sum e |X|^2 and apply the
-                // weight, 1/E^2 and eps once per row.  e = exp(beta (a2 - mx))
-                // from |X|^2 in one FMA; c = Kp (e - e0) + Ki.
+            // A row every cell of which carries the same weight (the window
+            // spans all Doppler bins, delay k and/or -k in it, no mainlobe-box
+            // cell) takes the fast path; the test is slot-uniform.
+            const bool in_pos = k >= wv.k_lo && k <= wv.k_hi;
+            const bool in_neg = k > 0 && -k >= wv.k_lo && -k <= wv.k_hi;
+            if (fixed && valid && wv.full_m && k > wv.k_ml && (in_pos || in_neg)) {
+                // accumulate P = sum |X|^2, Z = sum e, Q = sum e |X|^2 and
+                // apply the weight, 1/E^2 and eps once per row; e = exp(beta
+                // (a2 - mx)) from |X|^2 in one FMA; c = Kp (e - e0) + Ki
+                const float wrow = (in_pos && in_neg) ? 2.0f : 1.0f;
+                const float sh = mx * bl2;
+                const float e0 = ex2a(-sh);
                 const float Kp = (grad_row && psl_mode) ? wrow * cP : 0.0f;
                 const float Ki = (grad_row && !psl_mode) ? (wrow - wb) * cI : 0.0f;
                 const float Kc0 = fmaf(-e0, Kp, Ki);
-                const float kexp = invE2 * bl2, kofs = fmaf(eps_n, bl2, -sh);
+                const float kexp = s_k[5], kofs = fmaf(eps_n, bl2, -sh);
                 float rP[2] = {0.0f, 0.0f}, rZ[2] = {0.0f, 0.0f}, rQ[2] = {0.0f, 0.0f};
                 float rH[2] = {0.0f, 0.0f};
                 sfor<0, P::VALS>([&](auto w) {
                     constexpr int h = decltype(w)::value & 1;
                     const float2 x = v[w];
                     const float p2 = fmaf(x.x, x.x, x.y * x.y);
-                    const float e = ex2a(fmaf(p2, kexp, kofs));
+                    const float e = ex2v(fmaf(p2, kexp, kofs));
                     rH[h] = fmaxf(rH[h], p2);
                     rP[h] += p2;
                     rZ[h] += e;
@@ -671,18 +650,57 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
                 zs = fmaf(wrow, Zr, zs);
                 ts = fmaf(wrow, sea2, ts);
                 cs += fmaf(Kp, fmaf(-e0, sa2, sea2), Ki * sa2);
-                hm[0] = fmaxf(hm[0], fmaf(fmaxf(rH[0], rH[1]), invE2, eps_n));
+                hm = fmaxf(hm, fmaf(fmaxf(rH[0], rH[1]), invE2, eps_n));
             } else {
+                // column masks recomputed per row: kept live they would hold six
+                // registers through every transform
+                const RowMasks rmk = row_masks(wv, col_masks<M>(wv, t), k);
+                const bool uniform = !valid || (rmk.one == full_mask && (rmk.two == 0ull || rmk.two == full_mask));
+                const float wrow = valid ? (rmk.two != 0ull ? 2.0f : (rmk.one != 0ull ? 1.0f : 0.0f)) : 0.0f;
+                // pass 1 (running shift only): largest weighted a2 of the row
+                // (two independent chains)
+                float tmx[2] = {-CUDART_INF_F, -CUDART_INF_F};
+                if (!fixed) {
+                    sfor<0, P::VALS>([&](auto w) {
+                        const float2 x = v[w];
+                        const float a2 = fmaf(fmaf(x.x, x.x, x.y * x.y), invE2, eps_n);
+                        const float wt = uniform ? wrow : mweight<decltype(w)::value>(rmk);
+                        tmx[w & 1] = fmaxf(tmx[w & 1], wt > 0.0f ? a2 : -CUDART_INF_F);
+                    });
+                }
+                const float rmx = fixed ? mx : slot_max<P::TPR>(fmaxf(tmx[0], tmx[1]), red + 8, slot);
+                if (rmx > mx) {  // slot-uniform
+                    const float f = ex2a((mx - rmx) * bl2);  // 0 while mx = -inf
+                    zs *= f;
+                    ts *= f;
+                    if (psl_mode) {
+                        cs *= f;
+                        if (mx > -CUDART_INF_F) {  // the slot owns its accumulator on this path
+                            if (p.phase_only) {
+                                for (int n = t; n < wv.N; n += P::TPR) acc_r[n] *= f;
+                            } else {
+                                for (int n = t; n < wv.N; n += P::TPR) {
+                                    const float2 a = acc[n];
+                                    acc[n] = make_float2(a.x * f, a.y * f);
+                                }
+                            }
+                        }
+                    }
+                    mx = rmx;
+                }
+                // pass 2: loss partials and the gradient remainder, v = conj(c X)
+                const float sh = mx * bl2;
+                const float e0 = ex2a(-sh);
                 // row sums in two independent chains each (even / odd registers)
                 float r_isl[2] = {0.0f, 0.0f}, r_z[2] = {0.0f, 0.0f}, r_t[2] = {0.0f, 0.0f};
-                float r_c[2] = {0.0f, 0.0f};
+                float r_c[2] = {0.0f, 0.0f}, r_h[2] = {-CUDART_INF_F, -CUDART_INF_F};
                 sfor<0, P::VALS>([&](auto w) {
                     constexpr int h = decltype(w)::value & 1;
                     const float2 x = v[w];
                     const float a2 = fmaf(fmaf(x.x, x.x, x.y * x.y), invE2, eps_n);
                     const float wt = uniform ? wrow : mweight<decltype(w)::value>(rmk);
                     const float e = wt > 0.0f ? ex2a(fmaf(a2, bl2, -sh)) : 0.0f;
-                    hm[h] = fmaxf(hm[h], wt > 0.0f ? a2 : -CUDART_INF_F);
+                    r_h[h] = fmaxf(r_h[h], wt > 0.0f ? a2 : -CUDART_INF_F);
                     const float we = wt * e;
                     r_isl[h] = fmaf(wt, a2, r_isl[h]);
                     r_z[h] += we;
@@ -696,6 +714,7 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
                 zs += r_z[0] + r_z[1];
                 ts += r_t[0] + r_t[1];
                 cs += r_c[0] + r_c[1];
+                hm = fmaxf(hm, fmaxf(r_h[0], r_h[1]));
             }
             if constexpr (P::TPR >= 32) {
                 if (!grad_row) break;  // slot-uniform: the slot is one or more whole warps
@@ -708,7 +727,7 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
     }
     // bring every slot to the CTA's largest shift (fixed shift: the CTA's
     // largest weighted a2, the record's hard maximum)
-    float cmx = fixed ? fmaxf(hm[0], hm[1]) : mx;
+    float cmx = fixed ? hm : mx;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) cmx = fmaxf(cmx, __shfl_xor_sync(0xffffffffu, cmx, o));
     if ((tid & 31) == 0) red[tid >> 5] = cmx;
@@ -717,10 +736,10 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
 #pragma unroll
     for (int w = 1; w < NW; ++w) cmx = fmaxf(cmx, red[w]);
     __syncthreads();
-    const float fs = fixed ? 1.0f : (mx > -CUDART_INF_F) ? ex2a((mx - cmx) * bl2) : 0.0f;
+    const float fs = fixed ? 1.0f : (mx > -CUDART_INF_F) ? ex2a((mx - cmx) * s_k[2]) : 0.0f;
     zs *= fs;
     ts *= fs;
-    if (psl_mode && !fixed) {
+    if (wv.w_psl != 0.0f && !fixed) {
         cs *= fs;
         if (p.phase_only) {
             for (int n = t; n < wv.N; n += P::TPR) acc_r[n] *= fs;

@@ -217,6 +217,14 @@ __device__ __forceinline__ float ex2a(float x) {
     return y;
 }
 
+// The same, kept in program order: inside a long unrolled loop the scheduler
+// would otherwise issue every exponential early and hold all the results.
+__device__ __forceinline__ float ex2v(float x) {
+    float y;
+    asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Load s[0..N) of one waveform into shared memory (phases -> exp(j phi)) and
 // return E = sum |s|^2, reduced in a fixed order (identical in every CTA).
 __device__ __forceinline__ float load_signal(const Wave& wv, float2* s_sm, float* red) {
