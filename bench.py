@@ -44,6 +44,25 @@ def _env_rank():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def rank_seed(rank: int) -> int:
+    """Each rank draws its own batch (weak scaling: independent waveforms)."""
+    return SEED + 1000 * rank
+
+
+def reduce_max_ms(ms: float, dist, device) -> float:
+    """The slowest rank's time (the job's time); a no-op without a process group."""
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(world: int, cells_per_rank: float, steps: int, total_ms: float) -> float:
+    """Whole-job Gcells/s: every rank's cells over the slowest rank's time."""
+    return world * cells_per_rank * steps / (total_ms / 1e3) / 1e9
+
+
 def _measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -206,7 +225,7 @@ def run_graf(args):
 
     Bb = args.batch
     cells = Bb * (2 * N - 1) * M
-    phi_h = inputs.random_phases(SEED + 1000 * rank, Bb, N)
+    phi_h = inputs.random_phases(rank_seed(rank), Bb, N)
     x = torch.from_numpy(phi_h).to(dev)
     w, loss = g.Window.full(N, M), g.Loss(1.0, 1.0, BETA, EPS)
     wc, lc = w.c(), loss.c()
@@ -242,13 +261,9 @@ def run_graf(args):
         if dist:
             dist.barrier()
         torch.cuda.synchronize(dev)
-    step_ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
-    t = torch.tensor([step_ms], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    step_ms = t.item()
+    step_ms = reduce_max_ms(sum(e0.elapsed_time(e1) for e0, e1 in ev), dist, dev)
     ms_per_step = step_ms / args.steps
-    value = world * cells * args.steps / (step_ms / 1e3) / 1e9
+    value = weak_value(world, cells, args.steps, step_ms)
     assert torch.isfinite(out8).all() and torch.isfinite(grad).all()
 
     # end to end: pinned host phases in, loss scalars and gradient out, per step
@@ -274,10 +289,7 @@ def run_graf(args):
         b.record(stream)
         b.synchronize()
         e2e_ms += a.elapsed_time(b)
-    t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = world * cells * args.steps / (t.item() / 1e3) / 1e9
+    e2e_value = weak_value(world, cells, args.steps, reduce_max_ms(e2e_ms, dist, dev))
 
     if rank != 0:
         if dist:
