@@ -582,6 +582,7 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
     }
     __syncthreads();
     float2* buf = bufs + (size_t)slot * (P::SPLIT ? P::SMEM_ROW / 2 : P::SMEM_ROW);
+    const ColMasks cm = col_masks<M>(wv, t);
     constexpr unsigned long long full_mask = P::VALS == 64 ? ~0ull : ((1ull << P::VALS) - 1ull);
     const int turns = SLOTS / p.acc_copies;
     const int my_turn = slot / p.acc_copies;
@@ -652,9 +653,7 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
                 cs += fmaf(Kp, fmaf(-e0, sa2, sea2), Ki * sa2);
                 hm = fmaxf(hm, fmaf(fmaxf(rH[0], rH[1]), invE2, eps_n));
             } else {
-                // column masks recomputed per row: kept live they would hold six
-                // registers through every transform
-                const RowMasks rmk = row_masks(wv, col_masks<M>(wv, t), k);
+                const RowMasks rmk = row_masks(wv, cm, k);
                 const bool uniform = !valid || (rmk.one == full_mask && (rmk.two == 0ull || rmk.two == full_mask));
                 const float wrow = valid ? (rmk.two != 0ull ? 2.0f : (rmk.one != 0ull ? 1.0f : 0.0f)) : 0.0f;
                 // pass 1 (running shift only): largest weighted a2 of the row
