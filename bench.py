@@ -82,8 +82,9 @@ def _kernel_hash():
 
 
 def _traffic_record():
-    """DRAM bytes per launch of the backward kernel from the committed ncu
-    summary, valid only if the kernel sources are unchanged since."""
+    """DRAM bytes per launch of the fused kernel (from an ncu capture of a
+    32-code slice, scaled to the full batch), valid only if the kernel sources
+    are unchanged since the capture."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -91,7 +92,7 @@ def _traffic_record():
         rec = json.load(f)
     if rec.get("source_hash") != _kernel_hash():
         return None
-    return rec.get("af_backward_bytes_per_launch_full_batch")
+    return rec.get("af_fused_bytes_per_launch_full_batch")
 
 
 class ClockSampler:
