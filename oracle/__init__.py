@@ -68,8 +68,15 @@ def _load():
             lib.orc_fd_grad_s.argtypes = [_dp, _i64, _i64, _ip, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp,
                                           ctypes.c_int]
+            _c = ctypes.c_int
+            _d = ctypes.c_double
+            lib.orc_paf_complex.argtypes = [_dp, _i64, _c, _i64, _i64, _i64, _i64, _dp]
+            lib.orc_ploss.argtypes = [_dp, _i64, _c, _ip, _d, _d, _d, _d, _dp]
+            lib.orc_pgrad.argtypes = [_dp, _i64, _c, _ip, _d, _d, _d, _d, _dp, _dp, _dp]
+            lib.orc_pfd_grad_phi.argtypes = [_dp, _i64, _c, _ip, _d, _d, _d, _d, _d, _dp]
             for f in ("orc_af_complex", "orc_af_ahat", "orc_af_cells", "orc_loss", "orc_grad",
-                      "orc_fd_grad_phi", "orc_fd_grad_s"):
+                      "orc_fd_grad_phi", "orc_fd_grad_s", "orc_paf_complex", "orc_ploss", "orc_pgrad",
+                      "orc_pfd_grad_phi"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -226,3 +233,69 @@ def optimize_phases(phi0, M, window, w_psl, w_isl, beta, eps, steps, lr=1e-2, be
         hist.append(out[0])
         phi, m, v = adam_update(phi, m, v, gphi, t, lr, beta1, beta2, adam_eps)
     return phi, np.array(hist)
+
+
+# ----------------------------------------------------------- periodic AF
+# The paper's own discrete AF (Sec. 3.1 Eq. 2, Sec. 4.1 Eq. 7, Algorithm 1):
+# circular lag (n - k) mod N, N Doppler bins, exponent sign +1 (Eq. 7) or -1
+# (the FFT of Algorithm 1); delays and Doppler bins in fftshift order
+# [-N/2, N/2 - 1].
+
+def full_pwindow(N: int, k_ml: int = 0, m_ml: int = 0):
+    """Every delay and Doppler bin of the periodic AF; default box: the origin."""
+    return (-(N // 2), N - 1 - N // 2, -(N // 2), N - 1 - N // 2, k_ml, m_ml)
+
+
+def paf_complex(s, sign=1, k_lo=None, k_hi=None, m_lo=None, m_hi=None) -> np.ndarray:
+    """X[k,m] over the window (default all), shape (rows, cols), complex128."""
+    s, sv = _s_buf(s)
+    N = s.shape[0]
+    k_lo = -(N // 2) if k_lo is None else k_lo
+    k_hi = N - 1 - N // 2 if k_hi is None else k_hi
+    m_lo = -(N // 2) if m_lo is None else m_lo
+    m_hi = N - 1 - N // 2 if m_hi is None else m_hi
+    X = np.zeros((k_hi - k_lo + 1, m_hi - m_lo + 1), dtype=np.complex128)
+    _check(_load().orc_paf_complex(_ptr(sv), N, int(sign), k_lo, k_hi, m_lo, m_hi, _ptr(X.view(np.float64))),
+           "paf_complex")
+    return X
+
+
+def paf_chi(s, sign=1, normalise=True) -> np.ndarray:
+    """chi = |X|^2 (Eq. 12), divided by E^2 = chi[0,0] = max chi if normalise
+    (Eq. 17); [N][N], fftshift order (Algorithm 1 steps 4-5)."""
+    X = paf_complex(s, sign)
+    chi = np.abs(X) ** 2
+    if normalise:
+        chi = chi / energy(s) ** 2
+    return chi
+
+
+def ploss(s, window, w_psl=1.0, w_isl=1.0, beta=50.0, eps=1e-12, sign=1) -> np.ndarray:
+    s, sv = _s_buf(s)
+    w = _win(window)
+    out = np.zeros(8, dtype=np.float64)
+    _check(_load().orc_ploss(_ptr(sv), s.shape[0], int(sign), w.ctypes.data_as(_ip), w_psl, w_isl, beta, eps,
+                             _ptr(out)), "ploss")
+    return out
+
+
+def pgrad(s, window, w_psl=1.0, w_isl=1.0, beta=50.0, eps=1e-12, sign=1):
+    """(grad_s, grad_phi, out8) of the periodic-AF loss, conventions as grad."""
+    s, sv = _s_buf(s)
+    w = _win(window)
+    N = s.shape[0]
+    gs = np.zeros(N, dtype=np.complex128)
+    gp = np.zeros(N, dtype=np.float64)
+    out = np.zeros(8, dtype=np.float64)
+    _check(_load().orc_pgrad(_ptr(sv), N, int(sign), w.ctypes.data_as(_ip), w_psl, w_isl, beta, eps,
+                             _ptr(gs.view(np.float64)), _ptr(gp), _ptr(out)), "pgrad")
+    return gs, gp, out
+
+
+def pfd_grad_phi(phi, window, w_psl=1.0, w_isl=1.0, beta=50.0, eps=1e-12, sign=1, h=3e-5):
+    phi = np.ascontiguousarray(np.asarray(phi, dtype=np.float64))
+    w = _win(window)
+    g = np.zeros(phi.shape[0], dtype=np.float64)
+    _check(_load().orc_pfd_grad_phi(_ptr(phi), phi.shape[0], int(sign), w.ctypes.data_as(_ip), w_psl, w_isl,
+                                    beta, eps, h, _ptr(g)), "pfd_grad_phi")
+    return g

@@ -9,7 +9,7 @@
  * Definitions followed (paper section / equation):
  *   - lag product R[k,n] = s[n] * conj(s[n-k])                 (Sec. 4.1, Eq. 8)
  *     taken aperiodically: s[n] = 0 outside [0, N), delays k = -(N-1)..N-1
- *     (the non-periodic extension named in Sec. 8.5 "Limitations").
+ *     (the non-periodic extension named in Sec. 8.6 "Limitations").
  *   - row DFT X[k,m] = sum_n R[k,n] exp(-j 2 pi m n / M)        (Sec. 4.1, Eq. 11)
  *     with an M-point (zero padded) transform, m in [-M/2, M/2-1] (fftshift
  *     order, Algorithm 1 step 5).
@@ -24,6 +24,10 @@
  *   - Wirtinger adjoint (Sec. 3.3 Eq. 6, Sec. 4.2 Eqs. 13-15): the gradient
  *     exported is 2 dL/ds* = dL/dRe(s) + j dL/dIm(s), and for phase input
  *     s = exp(j phi), dL/dphi = 2 Im(dL/ds* . conj(s)).
+ *
+ * The periodic AF of the paper's own definition (Sec. 3.1 Eq. 2, Sec. 4.1
+ * Eq. 7, Algorithm 1) is at the end of the file: circular lag (n - k) mod N,
+ * N Doppler bins, exponent sign +j (Eq. 7) or -j (the FFT of Algorithm 1).
  *
  * Every sum is a direct double sum in the order the definition states; no FFT
  * is used anywhere in this file.  Threads only split independent delay rows;
@@ -443,5 +447,171 @@ int orc_fd_grad_s(const double* s, int64_t N, int64_t M, const int64_t win6[6], 
         grad_s[i] = (lp - lm) / (2.0 * h);
     }
     free(t);
+    return ORC_OK;
+}
+
+/* ============================================================ periodic AF */
+/* The paper's literal discrete AF (Sec. 3.1 Eq. 2, Sec. 4.1 Eqs. 7-12):
+ *   X[k,m] = sum_{n=0}^{N-1} s[n] conj(s[(n-k) mod N]) exp(sign j 2 pi m n / N)
+ * with sign = +1 (Eq. 7) or -1 (the FFT of Algorithm 1 step 3), chi = |X|^2,
+ * delays and Doppler bins both in fftshift order k, m in [-N/2, N/2-1]
+ * (Algorithm 1 step 5).  The losses use Ahat^2 = (|X|^2 + eps) / E^2 exactly
+ * as for the aperiodic AF; with eps = 0 that is chi / chi[0,0] = chi / max chi
+ * (Eq. 17: |X| <= E by Cauchy-Schwarz, with equality at the origin). */
+
+static int check_pwindow(int64_t N, const orc_window* w) {
+    if (N < 1) return ORC_EINVAL;
+    if (w->k_lo > w->k_hi || w->m_lo > w->m_hi) return ORC_EINVAL;
+    if (w->k_lo < -(N / 2) || w->k_hi > N - 1 - N / 2) return ORC_EINVAL;
+    if (w->m_lo < -(N / 2) || w->m_hi > N - 1 - N / 2) return ORC_EINVAL;
+    if (w->k_ml < -1 || w->m_ml < -1) return ORC_EINVAL;
+    return ORC_OK;
+}
+
+/* exp(sign j 2 pi q / N) for q in [0, N). */
+static double* make_pw_table(int64_t N, int sign) {
+    double* w = (double*)malloc(sizeof(double) * 2 * (size_t)N);
+    if (!w) return NULL;
+    for (int64_t q = 0; q < N; ++q) {
+        double a = 2.0 * ORC_PI * (double)q / (double)N;
+        w[2 * q] = cos(a);
+        w[2 * q + 1] = sign > 0 ? sin(a) : -sin(a);
+    }
+    return w;
+}
+
+static void paf_cell(const double* s, int64_t N, const double* W, int64_t k, int64_t m,
+                     double* xr, double* xi) {
+    int64_t mm = mod_i64(m, N);
+    double ar = 0.0, ai = 0.0;
+    for (int64_t n = 0; n < N; ++n) {
+        int64_t j = mod_i64(n - k, N);
+        double sr = s[2 * n], si = s[2 * n + 1];
+        double tr = s[2 * j], ti = -s[2 * j + 1];              /* conj(s[(n-k) mod N]) */
+        double rr = sr * tr - si * ti, ri = sr * ti + si * tr;  /* R[k,n], Eq. 8 */
+        int64_t q = (mm * n) % N;
+        double wr = W[2 * q], wi = W[2 * q + 1];
+        ar += rr * wr - ri * wi;
+        ai += rr * wi + ri * wr;
+    }
+    *xr = ar;
+    *xi = ai;
+}
+
+/* Complex periodic AF over a window (fftshift coordinates), [rows][cols][2]. */
+int orc_paf_complex(const double* s, int64_t N, int sign, int64_t k_lo, int64_t k_hi, int64_t m_lo,
+                    int64_t m_hi, double* X) {
+    orc_window w = {k_lo, k_hi, m_lo, m_hi, 0, 0};
+    if (check_pwindow(N, &w) || (sign != 1 && sign != -1)) return ORC_EINVAL;
+    double* W = make_pw_table(N, sign);
+    if (!W) return ORC_ENOMEM;
+    int64_t ncols = m_hi - m_lo + 1;
+    for (int64_t k = k_lo; k <= k_hi; ++k)
+        for (int64_t m = m_lo; m <= m_hi; ++m) {
+            double* o = X + 2 * ((k - k_lo) * ncols + (m - m_lo));
+            paf_cell(s, N, W, k, m, &o[0], &o[1]);
+        }
+    free(W);
+    return ORC_OK;
+}
+
+/* Loss scalars of the periodic AF, out8 as orc_loss. */
+int orc_ploss(const double* s, int64_t N, int sign, const int64_t win6[6], double w_psl,
+              double w_isl, double beta, double eps, double out[8]) {
+    orc_window w = {win6[0], win6[1], win6[2], win6[3], win6[4], win6[5]};
+    if (check_pwindow(N, &w) || !(beta > 0.0) || eps < 0.0) return ORC_EINVAL;
+    int64_t cells = (w.k_hi - w.k_lo + 1) * (w.m_hi - w.m_lo + 1);
+    double* X = (double*)malloc(sizeof(double) * 2 * (size_t)cells);
+    if (!X) return ORC_ENOMEM;
+    int st = orc_paf_complex(s, N, sign, w.k_lo, w.k_hi, w.m_lo, w.m_hi, X);
+    if (!st) st = loss_from_X(X, &w, orc_energy(s, N), eps, w_psl, w_isl, beta, out);
+    free(X);
+    return st;
+}
+
+/* Gradient of orc_ploss: the same cell adjoint and energy term as orc_grad;
+ * the row adjoint is G_R[k,n] = sum_m G[k,m] conj(exp(sign j 2 pi m n / N))
+ * and the product rule on R[k,n] = s[n] conj(s[(n-k) mod N]) scatters
+ *   G_R[k,n] s[(n-k) mod N]  into dL/ds*[n],
+ *   conj(G_R[k,n]) s[n]      into dL/ds*[(n-k) mod N]. */
+int orc_pgrad(const double* s, int64_t N, int sign, const int64_t win6[6], double w_psl,
+              double w_isl, double beta, double eps, double* grad_s, double* grad_phi,
+              double out[8]) {
+    orc_window w = {win6[0], win6[1], win6[2], win6[3], win6[4], win6[5]};
+    if (check_pwindow(N, &w) || !(beta > 0.0) || eps < 0.0) return ORC_EINVAL;
+    int64_t rows = w.k_hi - w.k_lo + 1, ncols = w.m_hi - w.m_lo + 1, cells = rows * ncols;
+    double* X = (double*)malloc(sizeof(double) * 2 * (size_t)cells);
+    double* W = make_pw_table(N, sign);
+    double* g = (double*)calloc(2 * (size_t)N, sizeof(double));
+    if (!X || !W || !g) { free(X); free(W); free(g); return ORC_ENOMEM; }
+    int st = orc_paf_complex(s, N, sign, w.k_lo, w.k_hi, w.m_lo, w.m_hi, X);
+    double E = orc_energy(s, N);
+    if (!st) st = loss_from_X(X, &w, E, eps, w_psl, w_isl, beta, out);
+    if (st) { free(X); free(W); free(g); return st; }
+    double psl_soft = out[1];
+    for (int64_t r = 0; r < rows; ++r)
+        for (int64_t c = 0; c < ncols; ++c) {
+            double* x = X + 2 * (r * ncols + c);
+            if (!in_omega(&w, w.k_lo + r, w.m_lo + c)) { x[0] = x[1] = 0.0; continue; }
+            double a2 = (x[0] * x[0] + x[1] * x[1] + eps) / (E * E);
+            double dl_da2 = w_isl + w_psl * exp(beta * (a2 - psl_soft));
+            x[0] *= dl_da2 / (E * E);
+            x[1] *= dl_da2 / (E * E);
+        }
+    for (int64_t r = 0; r < rows; ++r) {
+        int64_t k = w.k_lo + r;
+        for (int64_t n = 0; n < N; ++n) {
+            double gr = 0.0, gi = 0.0;
+            for (int64_t c = 0; c < ncols; ++c) {
+                const double* G = X + 2 * (r * ncols + c);
+                if (G[0] == 0.0 && G[1] == 0.0) continue;
+                int64_t q = (mod_i64(w.m_lo + c, N) * n) % N;
+                double wr = W[2 * q], wi = -W[2 * q + 1]; /* conj */
+                gr += G[0] * wr - G[1] * wi;
+                gi += G[0] * wi + G[1] * wr;
+            }
+            int64_t j = mod_i64(n - k, N);
+            double ar = s[2 * j], ai = s[2 * j + 1];
+            g[2 * n] += gr * ar - gi * ai;
+            g[2 * n + 1] += gr * ai + gi * ar;
+            double br = s[2 * n], bi = s[2 * n + 1];
+            g[2 * j] += gr * br + gi * bi;
+            g[2 * j + 1] += gr * bi - gi * br;
+        }
+    }
+    double dlde = -(2.0 / E) * (w_isl * out[2] + w_psl * out[6]);
+    for (int64_t n = 0; n < N; ++n) {
+        double gr = g[2 * n] + dlde * s[2 * n], gi = g[2 * n + 1] + dlde * s[2 * n + 1];
+        if (grad_s) { grad_s[2 * n] = 2.0 * gr; grad_s[2 * n + 1] = 2.0 * gi; }
+        if (grad_phi) grad_phi[n] = 2.0 * (gi * s[2 * n] - gr * s[2 * n + 1]);
+    }
+    free(X);
+    free(W);
+    free(g);
+    return ORC_OK;
+}
+
+/* Central finite differences of orc_ploss's L with respect to phi[p]. */
+int orc_pfd_grad_phi(const double* phi, int64_t N, int sign, const int64_t win6[6], double w_psl,
+                     double w_isl, double beta, double eps, double h, double* grad_phi) {
+    double* p = (double*)malloc(sizeof(double) * (size_t)N);
+    double* s = (double*)malloc(sizeof(double) * 2 * (size_t)N);
+    if (!p || !s) { free(p); free(s); return ORC_ENOMEM; }
+    for (int64_t i = 0; i < N; ++i) {
+        double o[8], lp, lm;
+        memcpy(p, phi, sizeof(double) * (size_t)N);
+        p[i] = phi[i] + h;
+        orc_signal_from_phase(p, N, s);
+        int st = orc_ploss(s, N, sign, win6, w_psl, w_isl, beta, eps, o);
+        if (st) { free(p); free(s); return st; }
+        lp = o[0];
+        p[i] = phi[i] - h;
+        orc_signal_from_phase(p, N, s);
+        orc_ploss(s, N, sign, win6, w_psl, w_isl, beta, eps, o);
+        lm = o[0];
+        grad_phi[i] = (lp - lm) / (2.0 * h);
+    }
+    free(p);
+    free(s);
     return ORC_OK;
 }
