@@ -6,7 +6,8 @@
  * Method (Bara et al., "GRAF: differentiable radar ambiguity functions"):
  *   lag product   R[k,n] = s[n] conj(s[n-k])                        Sec. 4.1, Eq. 8
  *                 aperiodic: s[n] = 0 outside [0,N), k = -(N-1)..N-1 (the
- *                 non-periodic extension listed in Sec. 8.5)
+ *                 non-periodic extension listed in Sec. 8.6); the paper's own
+ *                 circular form is the graf_paf_* family at the end
  *   row DFT       X[k,m] = sum_n R[k,n] exp(-2 pi j m n / M)          Sec. 4.1, Eq. 11
  *                 M-point (zero padded), m in [-M/2, M/2-1]         Algorithm 1 step 5
  *   magnitude     Ahat[k,m] = sqrt(|X[k,m]|^2 + eps) / E,           Eq. 12, Eq. 17
@@ -320,6 +321,37 @@ GRAF_API graf_status_t graf_af_loss_backward_noalloc(const void* x, graf_input_t
                                                      int32_t N, int32_t M, graf_window_t w,
                                                      graf_loss_t l, float* out8, const float* dL,
                                                      graf_c32* grad_s, float* grad_phi, void* stream);
+
+/*
+ * Periodic AF: the paper's own discrete definition (Sec. 3.1 Eq. 2, Sec. 4.1
+ * Eqs. 7-12, Algorithm 1):
+ *   X[k,m] = sum_{n=0}^{N-1} s[n] conj(s[(n-k) mod N]) exp(sign 2 pi j m n / N)
+ *   chi[k,m] = |X[k,m]|^2,  k, m in [-N/2, N/2-1] (fftshift order, Algorithm 1
+ *   step 5),  sign = +1 as in Eq. 7 or -1 as the FFT of Algorithm 1 step 3.
+ * Constraints as above with M = N: N a power of two in [GRAF_M_MIN,
+ * GRAF_M_MAX]; windows inside k, m in [-N/2, N/2-1]; sign = +1 or -1, else
+ * GRAF_ERR_INVALID_ARG.  The losses are those of the aperiodic calls with
+ * Ahat^2 = (|X|^2 + eps) / E^2 (= chi / max chi for eps = 0, Eq. 17) over the
+ * window minus the mainlobe box, and so are out8, dL, grad_s and grad_phi.
+ */
+
+/* chi_out [B][N][N] (row = delay k ascending, column = Doppler m ascending):
+ * chi / E^2 = chi / chi[0,0] = chi / max chi if normalise != 0 (Eq. 17),
+ * else chi itself. */
+GRAF_API graf_status_t graf_paf_forward(const void* x, graf_input_t kind, int32_t B, int32_t N, int32_t sign,
+                                        int32_t normalise, float* chi_out, void* stream);
+/* Workspace bytes for graf_paf_loss and graf_paf_loss_backward (0 = invalid
+ * shape or window). */
+GRAF_API size_t graf_paf_workspace_bytes(int32_t B, int32_t N, graf_window_t w);
+/* Loss scalars out8 [B][8] as graf_af_loss. */
+GRAF_API graf_status_t graf_paf_loss(const void* x, graf_input_t kind, int32_t B, int32_t N, int32_t sign,
+                                     graf_window_t w, graf_loss_t l, float* out8, void* workspace,
+                                     size_t workspace_bytes, void* stream);
+/* Loss scalars and gradients as graf_af_loss_backward. */
+GRAF_API graf_status_t graf_paf_loss_backward(const void* x, graf_input_t kind, int32_t B, int32_t N,
+                                              int32_t sign, graf_window_t w, graf_loss_t l, float* out8,
+                                              const float* dL, graf_c32* grad_s, float* grad_phi,
+                                              void* workspace, size_t workspace_bytes, void* stream);
 
 #ifdef __cplusplus
 }

@@ -97,13 +97,25 @@ __global__ void loss_finalize_kernel(AfParams p, float* out8) {
     }
 }
 
+// s[n] as the row kernels see it (conjugated for the +j periodic AF).
 __device__ __forceinline__ float2 signal_at(const Wave& wv, int n) {
+    float2 v;
     if (wv.kind == 1) {
         float sn, cs;
         sincosf(static_cast<const float*>(wv.x)[n], &sn, &cs);
-        return make_float2(cs, sn);
+        v = make_float2(cs, sn);
+    } else {
+        v = static_cast<const float2*>(wv.x)[n];
     }
-    return static_cast<const float2*>(wv.x)[n];
+    if (wv.pconj) v.y = -v.y;
+    return v;
+}
+
+// n +- k wrapped into [0, N) for the periodic AF; -1 where the aperiodic
+// lag product has no such sample.
+__device__ __forceinline__ int lag_index(const Wave& wv, int i) {
+    if (wv.periodic) return i < 0 ? i + wv.N : (i >= wv.N ? i - wv.N : i);
+    return (i < 0 || i >= wv.N) ? -1 : i;
 }
 
 // dL/ds* of the FFT part: scaled sum of the per-CTA partials of the first
@@ -151,7 +163,8 @@ __global__ void grad_phi_kernel(AfParams p, const float* dL, float* grad_phi) {
     float im;
     if (p.phase_only) im = g1.x + (g2.y * s.x - g2.x * s.y);
     else im = (g1.y + g2.y) * s.x - (g1.x + g2.x) * s.y;
-    grad_phi[wv.out_off + n] = scale * im;
+    // +j periodic AF: the kernels saw conj(s) = exp(-j phi), so dL/dphi flips sign
+    grad_phi[wv.out_off + n] = wv.pconj ? -scale * im : scale * im;
 }
 
 // Per waveform, in FP64: U = sum_k w_b(k) (C[k] + eps) over the transformed
@@ -172,7 +185,10 @@ __global__ void uniform_sum_kernel(AfParams p) {
         const int wb = base_weight(wv, k);
         if (wb == 0) continue;
         double c = 0.0;
-        for (int n = k; n < wv.N; ++n) c += a_sm[n] * a_sm[n - k];
+        for (int n = 0; n < wv.N; ++n) {
+            const int j = lag_index(wv, n - k);
+            if (j >= 0) c += a_sm[n] * a_sm[j];
+        }
         acc += wb * (c + (double)wv.eps);
     }
     // E in FP64 from the same |s|^2, so the closed form cancels exactly
@@ -233,8 +249,9 @@ __global__ void grad_s_kernel(AfParams p, const float* dL, float2* grad_s, float
         const int wb = base_weight(wv, k);
         if (wb == 0) continue;
         double t = 0.0;
-        if (n >= k) t += a_sm[n - k];
-        if (n + k < wv.N) t += a_sm[n + k];
+        const int j1 = lag_index(wv, n - k), j2 = lag_index(wv, n + k);
+        if (j1 >= 0) t += a_sm[j1];
+        if (j2 >= 0) t += a_sm[j2];
         corr += wb * t;
     }
     const double gu = Ap * (double)wv.M * (corr / (E * E) - 2.0 * p.usum[2 * b] / (E * E * E));
@@ -249,8 +266,13 @@ __global__ void grad_s_kernel(AfParams p, const float* dL, float2* grad_s, float
     }
     const double coef = -2.0 * E * cs + gu - 2.0 * (double)wv.eps * c00 / E;  // real multiplier of s[n]
     const double scale = 2.0 * (dL ? (double)dL[b] : 1.0);
-    grad_s[wv.out_off + n] = make_float2((float)(scale * (g.x + coef * s.x)), (float)(scale * (g.y + coef * s.y)));
-    if (grad_phi) grad_phi[wv.out_off + n] = (float)(scale * ((double)g.y * s.x - (double)g.x * s.y));
+    // +j periodic AF: everything above is the gradient with respect to u =
+    // conj(s); the gradient with respect to s is its conjugate, and dL/dphi
+    // flips sign
+    const float cj = wv.pconj ? -1.0f : 1.0f;
+    grad_s[wv.out_off + n] =
+        make_float2((float)(scale * (g.x + coef * s.x)), cj * (float)(scale * (g.y + coef * s.y)));
+    if (grad_phi) grad_phi[wv.out_off + n] = cj * (float)(scale * ((double)g.y * s.x - (double)g.x * s.y));
 }
 
 #define GRAF_DISPATCH_M(FN, M, ...)                      \

@@ -62,22 +62,24 @@ __device__ __forceinline__ void for_each_item(const AfParams& p, F&& body) {
 }
 
 // ---------------------------------------------------------- forward (store)
-// Ahat = sqrt(|X|^2 + eps) / E (Eq. 12, Eq. 17) for every window cell of
-// rows k and -k.  Stores are coalesced along m (consecutive threads hold
+// Ahat = sqrt(|X|^2 + eps) / E (Eq. 12, Eq. 17) -- or chi = |X|^2 (Eq. 12,
+// Algorithm 1 step 4), optionally over chi[0,0] = E^2 = max chi (Eq. 17) --
+// for every window cell of rows k and -k.  Stores are coalesced along m (consecutive threads hold
 // consecutive Doppler bins) and streaming (written once, never re-read here).
 template <int M, bool HALF>
 __global__ void __launch_bounds__(kThreads, 1) af_forward_kernel(AfParams p) {
     using P = RowPlan<M>;
     extern __shared__ __align__(256) unsigned char smem[];
     float2* s_sm = reinterpret_cast<float2*>(smem);
-    float2* bufs = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(p.N));
-    float* red = reinterpret_cast<float*>(smem + smem_signal_bytes<M>(p.N) + row_buffer_bytes<M>());
+    float2* bufs = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(sig_len(p)));
+    float* red = reinterpret_cast<float*>(smem + smem_signal_bytes<M>(sig_len(p)) + row_buffer_bytes<M>());
 
     const int tid = threadIdx.x, slot = tid / P::TPR, t = tid % P::TPR;
     const int b = blockIdx.x / p.tiles, tile = blockIdx.x % p.tiles;
     const Wave wv = wave_of(p, b);
     const float E = load_signal(wv, s_sm, red);
     const float invE = 1.0f / E;
+    const float sc = p.chi_out == 1 ? invE * invE : 1.0f;  // chi output: |X|^2 / E^2 or |X|^2
     float2* buf = bufs + (size_t)slot * (P::SPLIT ? P::SMEM_ROW / 2 : P::SMEM_ROW);
     const ColMasks cm = col_masks<M>(wv, t);
 
@@ -92,7 +94,7 @@ __global__ void __launch_bounds__(kThreads, 1) af_forward_kernel(AfParams p) {
     for (int it = 0; it < iters; ++it) {
         const int k = row0 + slot + it * (kThreads / P::TPR);
         const bool valid = k < row_end;
-        build_lag_row<M, HALF>(v, s_sm, p.N, k, t, valid);
+        build_lag_row<M, HALF>(v, s_sm, p.N, p.periodic ? k - p.N : k, t, valid);
         row_sync<P::TPR>(slot);
         row_fft<M, false, HALF, false>(v, buf, t, slot);
         if (valid) {
@@ -105,7 +107,8 @@ __global__ void __launch_bounds__(kThreads, 1) af_forward_kernel(AfParams p) {
                 constexpr int W = decltype(w)::value;
                 constexpr int off = P::TPR * W - (W >= P::VALS / 2 ? M : 0);  // m - t
                 const float2 x = v[w];
-                const float a = sqrtf(fmaf(x.x, x.x, fmaf(x.y, x.y, p.eps))) * invE;
+                const float a = p.chi_out == 0 ? sqrtf(fmaf(x.x, x.x, fmaf(x.y, x.y, p.eps))) * invE
+                                               : fmaf(x.x, x.x, x.y * x.y) * sc;
                 if (mbit<W>(rmk.pos)) __stcs(rp + off, a);
                 if (mbit<W>(rmk.neg)) {
                     float* dst = rn - off;
@@ -159,8 +162,8 @@ __device__ __forceinline__ void loss_item(const AfParams& p, int b, int tile, un
     __syncthreads();
     const Wave& wv = s_wave;
     float2* s_sm = reinterpret_cast<float2*>(smem);
-    float2* bufs = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(p.N));
-    float* red = reinterpret_cast<float*>(smem + smem_signal_bytes<M>(p.N) + row_buffer_bytes<M>());
+    float2* bufs = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(sig_len(p)));
+    float* red = reinterpret_cast<float*>(smem + smem_signal_bytes<M>(sig_len(p)) + row_buffer_bytes<M>());
 
     const int tid = threadIdx.x, slot = tid / P::TPR, t = tid % P::TPR;
     const float E = load_signal(wv, s_sm, red);
@@ -182,7 +185,7 @@ __device__ __forceinline__ void loss_item(const AfParams& p, int b, int tile, un
     for (int it = 0; it < iters; ++it) {
         const int k = row0 + slot + it * SLOTS;
         const bool valid = k < row_end;
-        build_lag_row<M, HALF>(v, s_sm, wv.N, k, t, valid);
+        build_lag_row<M, HALF>(v, s_sm, wv.N, wv.periodic ? k - wv.N : k, t, valid);
         row_sync<P::TPR>(slot);
         row_fft<M, false, HALF, false>(v, buf, t, slot);
         if (!valid) continue;
@@ -398,14 +401,18 @@ __device__ __forceinline__ void write_grad_partial(const AfParams& p, const Wave
         const float* acc_r = reinterpret_cast<const float*>(acc_all);
         for (int n = tid; n < wv.N; n += kThreads) {
             float a = acc_r[n];
-            for (int s = 1; s < p.acc_copies; ++s) a += acc_r[(size_t)s * wv.N + n];
+            for (int s = 1; s < p.acc_copies; ++s) a += acc_r[(size_t)s * wv.sN + n];
+            if (wv.periodic)  // fold the second copy: index n + N is n mod N
+                for (int s = 0; s < p.acc_copies; ++s) a += acc_r[(size_t)s * wv.sN + wv.N + n];
             out[n] = make_float2(a, 0.0f);
         }
         return;
     }
     for (int n = tid; n < wv.N; n += kThreads) {
         float2 a = acc_all[n];
-        for (int s = 1; s < p.acc_copies; ++s) a = cadd(a, acc_all[(size_t)s * wv.N + n]);
+        for (int s = 1; s < p.acc_copies; ++s) a = cadd(a, acc_all[(size_t)s * wv.sN + n]);
+        if (wv.periodic)
+            for (int s = 0; s < p.acc_copies; ++s) a = cadd(a, acc_all[(size_t)s * wv.sN + wv.N + n]);
         out[n] = a;
     }
 }
@@ -421,13 +428,13 @@ __device__ __forceinline__ void backward_item(const AfParams& p, int b, int tile
     __syncthreads();
     const Wave& wv = s_wave;
     float2* s_sm = reinterpret_cast<float2*>(smem);
-    float2* bufs = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(p.N));
-    float2* acc_all = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(p.N) + row_buffer_bytes<M>());
+    float2* bufs = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(sig_len(p)));
+    float2* acc_all = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(sig_len(p)) + row_buffer_bytes<M>());
     float* red = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(acc_all) +
-                                          (((size_t)p.acc_copies * p.N * sizeof(float2) + 255) & ~(size_t)255));
+                                          (((size_t)p.acc_copies * sig_len(p) * sizeof(float2) + 255) & ~(size_t)255));
 
     const int tid = threadIdx.x, slot = tid / P::TPR, t = tid % P::TPR;
-    for (int i = tid; i < p.acc_copies * wv.N; i += kThreads) acc_all[i] = make_float2(0.0f, 0.0f);
+    for (int i = tid; i < p.acc_copies * wv.sN; i += kThreads) acc_all[i] = make_float2(0.0f, 0.0f);
     const float E = load_signal(wv, s_sm, red);  // includes __syncthreads
     const float invE2 = 1.0f / (E * E);
     const float eps_n = wv.eps * invE2;
@@ -444,8 +451,8 @@ __device__ __forceinline__ void backward_item(const AfParams& p, int b, int tile
     // slots sharing an accumulator (when shared memory is short) take turns
     const int turns = SLOTS / p.acc_copies;
     const int my_turn = slot / p.acc_copies;
-    float2* acc = acc_all + (size_t)(slot % p.acc_copies) * wv.N;
-    float* acc_r = reinterpret_cast<float*>(acc_all) + (size_t)(slot % p.acc_copies) * wv.N;
+    float2* acc = acc_all + (size_t)(slot % p.acc_copies) * wv.sN;
+    float* acc_r = reinterpret_cast<float*>(acc_all) + (size_t)(slot % p.acc_copies) * wv.sN;
 
     const int row0 = wv.r_lo + tile * wv.rows_per_tile;
     const int row_end = min(row0 + wv.rows_per_tile, wv.r_hi + 1);
@@ -456,7 +463,7 @@ __device__ __forceinline__ void backward_item(const AfParams& p, int b, int tile
         const int k = row0 + slot + it * SLOTS;
         // row 0 is R[0,n] = |s[n]|^2: it does not depend on the phases
         const bool valid = k < row_end && !(p.phase_only && k == 0);
-        build_lag_row<M, HALF>(v, s_sm, wv.N, k, t, valid);
+        build_lag_row<M, HALF>(v, s_sm, wv.N, wv.periodic ? k - wv.N : k, t, valid);
         // one transform instance, run twice: recompute X, then the adjoint as
         // conj(DFT(conj(c X)))
 #pragma unroll 1
@@ -486,9 +493,9 @@ __device__ __forceinline__ void backward_item(const AfParams& p, int b, int tile
             });
         }
         if (p.phase_only)
-            scatter_row_real<M, HALF>(v, acc_r, s_sm, wv.N, k, t, valid, slot, turns, my_turn);
+            scatter_row_real<M, HALF>(v, acc_r, s_sm, wv.N, wv.periodic ? k - wv.N : k, t, valid, slot, turns, my_turn);
         else
-            scatter_row<M, HALF, true>(v, acc, s_sm, wv.N, k, t, valid, slot, turns, my_turn);
+            scatter_row<M, HALF, true>(v, acc, s_sm, wv.N, wv.periodic ? k - wv.N : k, t, valid, slot, turns, my_turn);
     }
     write_grad_partial<M>(p, wv, acc_all, red, csum, tile);
 }
@@ -556,15 +563,15 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
     __syncthreads();
     const Wave& wv = s_wave;
     float2* s_sm = reinterpret_cast<float2*>(smem);
-    float2* bufs = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(p.N));
-    float2* acc_all = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(p.N) + row_buffer_bytes<M>());
+    float2* bufs = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(sig_len(p)));
+    float2* acc_all = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(sig_len(p)) + row_buffer_bytes<M>());
     float* red = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(acc_all) +
-                                          (((size_t)p.acc_copies * p.N * sizeof(float2) + 255) & ~(size_t)255));
+                                          (((size_t)p.acc_copies * sig_len(p) * sizeof(float2) + 255) & ~(size_t)255));
     // red: [0,8) reductions, [8,16) slot-max scratch (TPR > 32), [64, 64+SLOTS) final slot shifts
     // (SLOTS <= 32 here unless M <= 64, where the shifts live in registers only), [128, 160) float4s
 
     const int tid = threadIdx.x, slot = tid / P::TPR, t = tid % P::TPR;
-    for (int i = tid; i < p.acc_copies * wv.N; i += kThreads) acc_all[i] = make_float2(0.0f, 0.0f);
+    for (int i = tid; i < p.acc_copies * wv.sN; i += kThreads) acc_all[i] = make_float2(0.0f, 0.0f);
     const float E = load_signal(wv, s_sm, red);  // includes __syncthreads
     // the item's constants live in shared memory and are re-read after each
     // transform, so that none of them occupies a register during the FFTs
@@ -586,8 +593,8 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
     constexpr unsigned long long full_mask = P::VALS == 64 ? ~0ull : ((1ull << P::VALS) - 1ull);
     const int turns = SLOTS / p.acc_copies;
     const int my_turn = slot / p.acc_copies;
-    float2* acc = acc_all + (size_t)(slot % p.acc_copies) * wv.N;
-    float* acc_r = reinterpret_cast<float*>(acc_all) + (size_t)(slot % p.acc_copies) * wv.N;
+    float2* acc = acc_all + (size_t)(slot % p.acc_copies) * wv.sN;
+    float* acc_r = reinterpret_cast<float*>(acc_all) + (size_t)(slot % p.acc_copies) * wv.sN;
 
     const int row0 = wv.r_lo + tile * wv.rows_per_tile;
     const int row_end = min(row0 + wv.rows_per_tile, wv.r_hi + 1);
@@ -602,7 +609,7 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
         const int k = row0 + slot + it * SLOTS;
         const bool valid = k < row_end;
         const bool grad_row = valid && k > wv.defer_hi && !(p.phase_only && k == 0);
-        build_lag_row<M, HALF>(v, s_sm, wv.N, k, t, valid);
+        build_lag_row<M, HALF>(v, s_sm, wv.N, wv.periodic ? k - wv.N : k, t, valid);
         // one transform instance, run twice: the forward DFT, then the adjoint
         // as conj(DFT(conj(c X))) -- the epilogue writes conj(c X) and the
         // scatter reads the conjugated result
@@ -676,9 +683,9 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
                         cs *= f;
                         if (mx > -CUDART_INF_F) {  // the slot owns its accumulator on this path
                             if (p.phase_only) {
-                                for (int n = t; n < wv.N; n += P::TPR) acc_r[n] *= f;
+                                for (int n = t; n < wv.sN; n += P::TPR) acc_r[n] *= f;
                             } else {
-                                for (int n = t; n < wv.N; n += P::TPR) {
+                                for (int n = t; n < wv.sN; n += P::TPR) {
                                     const float2 a = acc[n];
                                     acc[n] = make_float2(a.x * f, a.y * f);
                                 }
@@ -720,9 +727,9 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
             }
         }
         if (p.phase_only)
-            scatter_row_real<M, HALF>(v, acc_r, s_sm, wv.N, k, t, grad_row, slot, turns, my_turn);
+            scatter_row_real<M, HALF>(v, acc_r, s_sm, wv.N, wv.periodic ? k - wv.N : k, t, grad_row, slot, turns, my_turn);
         else
-            scatter_row<M, HALF, true>(v, acc, s_sm, wv.N, k, t, grad_row, slot, turns, my_turn);
+            scatter_row<M, HALF, true>(v, acc, s_sm, wv.N, wv.periodic ? k - wv.N : k, t, grad_row, slot, turns, my_turn);
     }
     // bring every slot to the CTA's largest shift (fixed shift: the CTA's
     // largest weighted a2, the record's hard maximum)
@@ -741,9 +748,9 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
     if (wv.w_psl != 0.0f && !fixed) {
         cs *= fs;
         if (p.phase_only) {
-            for (int n = t; n < wv.N; n += P::TPR) acc_r[n] *= fs;
+            for (int n = t; n < wv.sN; n += P::TPR) acc_r[n] *= fs;
         } else {
-            for (int n = t; n < wv.N; n += P::TPR) {
+            for (int n = t; n < wv.sN; n += P::TPR) {
                 const float2 a = acc[n];
                 acc[n] = make_float2(a.x * fs, a.y * fs);
             }
@@ -797,20 +804,20 @@ static cudaError_t launch_rows(K kernel, size_t smem, const AfParams& p, cudaStr
 
 template <int M>
 cudaError_t run_forward_m(const AfParams& p, cudaStream_t st) {
-    const size_t smem = forward_smem<M>(p.N);
+    const size_t smem = forward_smem<M>(sig_len(p));
     if (2 * p.N <= M) return launch_rows(af_forward_kernel<M, true>, smem, p, st);
     return launch_rows(af_forward_kernel<M, false>, smem, p, st);
 }
 template <int M>
 cudaError_t run_loss_m(const AfParams& p, cudaStream_t st) {
-    const size_t smem = forward_smem<M>(p.N);
+    const size_t smem = forward_smem<M>(sig_len(p));
     if (2 * p.N <= M) return launch_rows(af_loss_kernel<M, true>, smem, p, st);
     return launch_rows(af_loss_kernel<M, false>, smem, p, st);
 }
 template <int M>
 cudaError_t run_backward_m(const AfParams& p, cudaStream_t st) {
     if (p.acc_copies < 1 || (256 / RowPlan<M>::TPR) % p.acc_copies) return cudaErrorInvalidConfiguration;
-    const size_t smem = backward_smem<M>(p.N, p.acc_copies);
+    const size_t smem = backward_smem<M>(sig_len(p), p.acc_copies);
     return launch_rows(af_backward_kernel<M, false>, smem, p, st);
 }
 
@@ -822,7 +829,7 @@ cudaError_t run_backward_m(const AfParams& p, cudaStream_t st) {
 template <int M>
 cudaError_t run_fused_m(const AfParams& p, cudaStream_t st) {
     if (p.acc_copies < 1 || (256 / RowPlan<M>::TPR) % p.acc_copies) return cudaErrorInvalidConfiguration;
-    const size_t smem = backward_smem<M>(p.N, p.acc_copies);
+    const size_t smem = backward_smem<M>(sig_len(p), p.acc_copies);
     if (2 * p.N <= M) return launch_rows(af_fused_kernel<M, true>, smem, p, st);
     return launch_rows(af_fused_kernel<M, false>, smem, p, st);
 }

@@ -19,9 +19,24 @@ graf_status_t check_shape(int32_t B, int32_t N, int32_t M) {
     return GRAF_OK;
 }
 
-graf_status_t check_window(int32_t N, int32_t M, const graf_window_t& w) {
+// Which AF a call computes: the aperiodic AF (2N-1 delays, M Doppler bins) or
+// the periodic AF of Eq. 7 (circular lag, M = N, delays and Doppler bins in
+// [-N/2, N/2-1]), the latter with the +j exponent of Eq. 7 (pconj) or -j.
+struct Mode {
+    int periodic, pconj;
+};
+constexpr Mode kAperiodic{0, 0};
+
+// shared-memory length of the signal and of each accumulator
+int32_t store_len(const Mode& md, int32_t N) { return md.periodic ? 2 * N : N; }
+
+graf_status_t check_window(int32_t N, int32_t M, const graf_window_t& w, const Mode& md = kAperiodic) {
     if (w.k_lo > w.k_hi || w.m_lo > w.m_hi) return GRAF_ERR_INVALID_ARG;
-    if (w.k_lo < -(N - 1) || w.k_hi > N - 1) return GRAF_ERR_INVALID_ARG;
+    if (md.periodic) {
+        if (w.k_lo < -(N / 2) || w.k_hi > N / 2 - 1) return GRAF_ERR_INVALID_ARG;
+    } else if (w.k_lo < -(N - 1) || w.k_hi > N - 1) {
+        return GRAF_ERR_INVALID_ARG;
+    }
     if (w.m_lo < -(M / 2) || w.m_hi > M / 2 - 1) return GRAF_ERR_INVALID_ARG;
     if (w.k_ml < -1 || w.m_ml < -1) return GRAF_ERR_INVALID_ARG;
     return GRAF_OK;
@@ -37,8 +52,10 @@ graf_status_t check_loss(const graf_loss_t& l) {
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 AfParams base_params(const void* x, graf_input_t kind, int32_t B, int32_t N, int32_t M,
-                     const graf_window_t& w, const Tiling& T) {
+                     const graf_window_t& w, const Tiling& T, const Mode& md = kAperiodic) {
     AfParams p{};
+    p.periodic = md.periodic;
+    p.pconj = md.pconj;
     p.x = x;
     p.kind = kind == GRAF_IN_PHASE ? 1 : 0;
     p.B = B; p.N = N; p.M = M;
@@ -101,12 +118,13 @@ size_t fused_ws(int32_t B, int32_t N, const FusedPlan& f) {
 }
 
 graf_status_t check_common(const void* x, graf_input_t kind, int32_t B, int32_t N, int32_t M,
-                           const graf_window_t& w) {
+                           const graf_window_t& w, const Mode& md = kAperiodic) {
     if (!x) return GRAF_ERR_INVALID_ARG;
     if (kind != GRAF_IN_COMPLEX && kind != GRAF_IN_PHASE) return GRAF_ERR_INVALID_ARG;
     graf_status_t s = check_shape(B, N, M);
     if (s != GRAF_OK) return s;
-    return check_window(N, M, w);
+    if (md.periodic && M != N) return GRAF_ERR_INVALID_ARG;
+    return check_window(N, M, w, md);
 }
 
 }  // namespace
@@ -129,44 +147,48 @@ const char* graf_status_string(graf_status_t status) {
 
 int32_t graf_version(void) { return GRAF_VERSION; }
 
-graf_status_t graf_af_forward(const void* x, graf_input_t kind, int32_t B, int32_t N, int32_t M,
-                              graf_window_t w, float eps, float* af_out, void* stream) {
-    graf_status_t s = check_common(x, kind, B, N, M, w);
+}  // extern "C"
+
+static graf_status_t af_forward_impl(const Mode& md, const void* x, graf_input_t kind, int32_t B, int32_t N,
+                                     int32_t M, graf_window_t w, float eps, int chi_out, float* af_out,
+                                     void* stream) {
+    graf_status_t s = check_common(x, kind, B, N, M, w, md);
     if (s != GRAF_OK) return s;
     if (!af_out || !(eps >= 0.0f) || eps > 1e30f) return GRAF_ERR_INVALID_ARG;
-    if (graf::row_kernel_smem(M, N, 0) > graf::kMaxSmem) return GRAF_ERR_UNSUPPORTED;
+    if (graf::row_kernel_smem(M, store_len(md, N), 0) > graf::kMaxSmem) return GRAF_ERR_UNSUPPORTED;
     const Tiling T = graf::make_tiling(B, M, w.k_lo, w.k_hi);
-    AfParams p = base_params(x, kind, B, N, M, w, T);
+    AfParams p = base_params(x, kind, B, N, M, w, T, md);
     p.eps = eps;
+    p.chi_out = chi_out;
     p.af_out = af_out;
     return cuda_status(graf::run_forward(p, static_cast<cudaStream_t>(stream)));
 }
 
-size_t graf_af_loss_workspace_bytes(int32_t B, int32_t N, int32_t M, graf_window_t w) {
-    if (check_shape(B, N, M) != GRAF_OK || check_window(N, M, w) != GRAF_OK) return 0;
+static size_t loss_ws_impl(const Mode& md, int32_t B, int32_t N, int32_t M, graf_window_t w) {
+    if (check_shape(B, N, M) != GRAF_OK || check_window(N, M, w, md) != GRAF_OK) return 0;
     return loss_ws(B, graf::make_tiling(B, M, w.k_lo, w.k_hi));
 }
 
-graf_status_t graf_af_loss(const void* x, graf_input_t kind, int32_t B, int32_t N, int32_t M,
-                           graf_window_t w, graf_loss_t l, float* out8, void* workspace,
-                           size_t workspace_bytes, void* stream) {
-    graf_status_t s = check_common(x, kind, B, N, M, w);
+static graf_status_t af_loss_impl(const Mode& md, const void* x, graf_input_t kind, int32_t B, int32_t N,
+                                  int32_t M, graf_window_t w, graf_loss_t l, float* out8, void* workspace,
+                                  size_t workspace_bytes, void* stream) {
+    graf_status_t s = check_common(x, kind, B, N, M, w, md);
     if (s != GRAF_OK) return s;
     if ((s = check_loss(l)) != GRAF_OK) return s;
     if (!out8) return GRAF_ERR_INVALID_ARG;
-    if (graf::row_kernel_smem(M, N, 0) > graf::kMaxSmem) return GRAF_ERR_UNSUPPORTED;
+    if (graf::row_kernel_smem(M, store_len(md, N), 0) > graf::kMaxSmem) return GRAF_ERR_UNSUPPORTED;
     const Tiling T = graf::make_tiling(B, M, w.k_lo, w.k_hi);
     if (!workspace || workspace_bytes < loss_ws(B, T)) return GRAF_ERR_WORKSPACE;
     if (reinterpret_cast<uintptr_t>(workspace) & 255) return GRAF_ERR_WORKSPACE;
-    AfParams p = base_params(x, kind, B, N, M, w, T);
+    AfParams p = base_params(x, kind, B, N, M, w, T, md);
     p.eps = l.eps; p.beta = l.beta; p.w_psl = l.w_psl; p.w_isl = l.w_isl;
     p.rec = static_cast<float4*>(workspace);
     p.out8 = out8;
     return cuda_status(graf::run_loss(p, static_cast<cudaStream_t>(stream)));
 }
 
-size_t graf_af_backward_workspace_bytes(int32_t B, int32_t N, int32_t M, graf_window_t w) {
-    if (check_shape(B, N, M) != GRAF_OK || check_window(N, M, w) != GRAF_OK) return 0;
+static size_t backward_ws_impl(const Mode& md, int32_t B, int32_t N, int32_t M, graf_window_t w) {
+    if (check_shape(B, N, M) != GRAF_OK || check_window(N, M, w, md) != GRAF_OK) return 0;
     const Tiling T = graf::make_tiling(B, M, w.k_lo, w.k_hi);
     size_t s = loss_ws(B, T);
     const size_t b = backward_ws(B, N, T);
@@ -180,11 +202,11 @@ size_t graf_af_backward_workspace_bytes(int32_t B, int32_t N, int32_t M, graf_wi
     return s;
 }
 
-graf_status_t graf_af_backward(const void* x, graf_input_t kind, int32_t B, int32_t N, int32_t M,
-                               graf_window_t w, graf_loss_t l, const float* saved8, const float* dL,
-                               graf_c32* grad_s, float* grad_phi, void* workspace,
-                               size_t workspace_bytes, void* stream) {
-    graf_status_t s = check_common(x, kind, B, N, M, w);
+static graf_status_t af_backward_impl(const Mode& md, const void* x, graf_input_t kind, int32_t B, int32_t N,
+                                      int32_t M, graf_window_t w, graf_loss_t l, const float* saved8,
+                                      const float* dL, graf_c32* grad_s, float* grad_phi, void* workspace,
+                                      size_t workspace_bytes, void* stream) {
+    graf_status_t s = check_common(x, kind, B, N, M, w, md);
     if (s != GRAF_OK) return s;
     if ((s = check_loss(l)) != GRAF_OK) return s;
     if (!saved8 || (!grad_s && !grad_phi)) return GRAF_ERR_INVALID_ARG;
@@ -192,7 +214,7 @@ graf_status_t graf_af_backward(const void* x, graf_input_t kind, int32_t B, int3
     const Tiling T = graf::make_tiling(B, M, w.k_lo, w.k_hi);
     if (!workspace || workspace_bytes < backward_ws(B, N, T)) return GRAF_ERR_WORKSPACE;
     if (reinterpret_cast<uintptr_t>(workspace) & 255) return GRAF_ERR_WORKSPACE;
-    AfParams p = base_params(x, kind, B, N, M, w, T);
+    AfParams p = base_params(x, kind, B, N, M, w, T, md);
     p.eps = l.eps; p.beta = l.beta; p.w_psl = l.w_psl; p.w_isl = l.w_isl;
     p.saved8 = saved8;
     unsigned char* ws = static_cast<unsigned char*>(workspace);
@@ -200,38 +222,38 @@ graf_status_t graf_af_backward(const void* x, graf_input_t kind, int32_t B, int3
     p.csum = reinterpret_cast<float*>(ws + gpart_bytes(B, N, T));
     p.usum = reinterpret_cast<double*>(ws + gpart_bytes(B, N, T) + csum_bytes(B, T));
     p.phase_only = (kind == GRAF_IN_PHASE && grad_s == nullptr) ? 1 : 0;
-    p.acc_copies = graf::acc_copies_for(M, N);
+    p.acc_copies = graf::acc_copies_for(M, store_len(md, N));
     if (p.acc_copies < 1) return GRAF_ERR_UNSUPPORTED;
     return cuda_status(graf::run_backward(p, dL, reinterpret_cast<float2*>(grad_s), grad_phi,
                                           static_cast<cudaStream_t>(stream)));
 }
 
-graf_status_t graf_af_loss_backward(const void* x, graf_input_t kind, int32_t B, int32_t N,
-                                    int32_t M, graf_window_t w, graf_loss_t l, float* out8,
-                                    const float* dL, graf_c32* grad_s, float* grad_phi,
-                                    void* workspace, size_t workspace_bytes, void* stream) {
-    graf_status_t s = check_common(x, kind, B, N, M, w);
+static graf_status_t af_loss_backward_impl(const Mode& md, const void* x, graf_input_t kind, int32_t B,
+                                           int32_t N, int32_t M, graf_window_t w, graf_loss_t l, float* out8,
+                                           const float* dL, graf_c32* grad_s, float* grad_phi,
+                                           void* workspace, size_t workspace_bytes, void* stream) {
+    graf_status_t s = check_common(x, kind, B, N, M, w, md);
     if (s != GRAF_OK) return s;
     if ((s = check_loss(l)) != GRAF_OK) return s;
     if (!out8 || (!grad_s && !grad_phi)) return GRAF_ERR_INVALID_ARG;
     if (grad_phi && kind != GRAF_IN_PHASE) return GRAF_ERR_INVALID_ARG;
-    if (!workspace || workspace_bytes < graf_af_backward_workspace_bytes(B, N, M, w)) return GRAF_ERR_WORKSPACE;
+    if (!workspace || workspace_bytes < backward_ws_impl(md, B, N, M, w)) return GRAF_ERR_WORKSPACE;
     if (reinterpret_cast<uintptr_t>(workspace) & 255) return GRAF_ERR_WORKSPACE;
-    const int acc = graf::acc_copies_for(M, N);
+    const int acc = graf::acc_copies_for(M, store_len(md, N));
     if (acc < 1) return GRAF_ERR_UNSUPPORTED;
     const bool phase_only = kind == GRAF_IN_PHASE && grad_s == nullptr;
     FusedPlan f = fused_plan(B, N, M, w, l.w_psl != 0.0f, phase_only);
     // on the PSL path each row slot needs its own gradient accumulator
     if (l.w_psl != 0.0f && acc < graf::kThreads / graf::tpr_of(M)) f.fused = false;
     if (!f.fused) {
-        s = graf_af_loss(x, kind, B, N, M, w, l, out8, workspace, workspace_bytes, stream);
+        s = af_loss_impl(md, x, kind, B, N, M, w, l, out8, workspace, workspace_bytes, stream);
         if (s != GRAF_OK) return s;
-        return graf_af_backward(x, kind, B, N, M, w, l, out8, dL, grad_s, grad_phi, workspace,
+        return af_backward_impl(md, x, kind, B, N, M, w, l, out8, dL, grad_s, grad_phi, workspace,
                                 workspace_bytes, stream);
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     unsigned char* ws = static_cast<unsigned char*>(workspace);
-    AfParams p = base_params(x, kind, B, N, M, w, f.T1);
+    AfParams p = base_params(x, kind, B, N, M, w, f.T1, md);
     p.eps = l.eps; p.beta = l.beta; p.w_psl = l.w_psl; p.w_isl = l.w_isl;
     p.out8 = out8;
     p.saved8 = out8;
@@ -275,6 +297,74 @@ graf_status_t graf_af_loss_backward(const void* x, graf_input_t kind, int32_t B,
     if (e == cudaSuccess)
         e = graf::run_grad_reduce(p, dL, reinterpret_cast<float2*>(grad_s), grad_phi, st);
     return cuda_status(e);
+}
+
+
+extern "C" {
+
+graf_status_t graf_af_forward(const void* x, graf_input_t kind, int32_t B, int32_t N, int32_t M,
+                              graf_window_t w, float eps, float* af_out, void* stream) {
+    return af_forward_impl(kAperiodic, x, kind, B, N, M, w, eps, 0, af_out, stream);
+}
+
+size_t graf_af_loss_workspace_bytes(int32_t B, int32_t N, int32_t M, graf_window_t w) {
+    return loss_ws_impl(kAperiodic, B, N, M, w);
+}
+
+graf_status_t graf_af_loss(const void* x, graf_input_t kind, int32_t B, int32_t N, int32_t M,
+                           graf_window_t w, graf_loss_t l, float* out8, void* workspace,
+                           size_t workspace_bytes, void* stream) {
+    return af_loss_impl(kAperiodic, x, kind, B, N, M, w, l, out8, workspace, workspace_bytes, stream);
+}
+
+size_t graf_af_backward_workspace_bytes(int32_t B, int32_t N, int32_t M, graf_window_t w) {
+    return backward_ws_impl(kAperiodic, B, N, M, w);
+}
+
+graf_status_t graf_af_backward(const void* x, graf_input_t kind, int32_t B, int32_t N, int32_t M,
+                               graf_window_t w, graf_loss_t l, const float* saved8, const float* dL,
+                               graf_c32* grad_s, float* grad_phi, void* workspace,
+                               size_t workspace_bytes, void* stream) {
+    return af_backward_impl(kAperiodic, x, kind, B, N, M, w, l, saved8, dL, grad_s, grad_phi, workspace,
+                            workspace_bytes, stream);
+}
+
+graf_status_t graf_af_loss_backward(const void* x, graf_input_t kind, int32_t B, int32_t N,
+                                    int32_t M, graf_window_t w, graf_loss_t l, float* out8,
+                                    const float* dL, graf_c32* grad_s, float* grad_phi,
+                                    void* workspace, size_t workspace_bytes, void* stream) {
+    return af_loss_backward_impl(kAperiodic, x, kind, B, N, M, w, l, out8, dL, grad_s, grad_phi, workspace,
+                                 workspace_bytes, stream);
+}
+
+// ------------------------------------------------------------ periodic AF
+static Mode periodic_mode(int32_t sign) { return Mode{1, sign > 0 ? 1 : 0}; }
+
+graf_status_t graf_paf_forward(const void* x, graf_input_t kind, int32_t B, int32_t N, int32_t sign,
+                               int32_t normalise, float* chi_out, void* stream) {
+    if (sign != 1 && sign != -1) return GRAF_ERR_INVALID_ARG;
+    const graf_window_t w{-(N / 2), N / 2 - 1, -(N / 2), N / 2 - 1, -1, -1};
+    return af_forward_impl(periodic_mode(sign), x, kind, B, N, N, w, 0.0f, normalise ? 1 : 2, chi_out, stream);
+}
+
+size_t graf_paf_workspace_bytes(int32_t B, int32_t N, graf_window_t w) {
+    return backward_ws_impl(Mode{1, 0}, B, N, N, w);
+}
+
+graf_status_t graf_paf_loss(const void* x, graf_input_t kind, int32_t B, int32_t N, int32_t sign,
+                            graf_window_t w, graf_loss_t l, float* out8, void* workspace,
+                            size_t workspace_bytes, void* stream) {
+    if (sign != 1 && sign != -1) return GRAF_ERR_INVALID_ARG;
+    return af_loss_impl(periodic_mode(sign), x, kind, B, N, N, w, l, out8, workspace, workspace_bytes, stream);
+}
+
+graf_status_t graf_paf_loss_backward(const void* x, graf_input_t kind, int32_t B, int32_t N, int32_t sign,
+                                     graf_window_t w, graf_loss_t l, float* out8, const float* dL,
+                                     graf_c32* grad_s, float* grad_phi, void* workspace,
+                                     size_t workspace_bytes, void* stream) {
+    if (sign != 1 && sign != -1) return GRAF_ERR_INVALID_ARG;
+    return af_loss_backward_impl(periodic_mode(sign), x, kind, B, N, N, w, l, out8, dL, grad_s, grad_phi,
+                                 workspace, workspace_bytes, stream);
 }
 
 }  // extern "C"

@@ -58,12 +58,22 @@ struct AfParams {
     int tiles2;
     const float2* gpart2;  // [B][tiles2][N]
     const float* csum2;    // [B][tiles2]
+    // periodic AF (the paper's own definition, Eq. 7): circular lag mod N,
+    // M = N; the signal and the gradient accumulators are stored twice in
+    // shared memory so that s[(n-k) mod N] = s2[n - k + N] needs no index
+    // wrap.  pconj: the +j exponent of Eq. 7, computed as the -j transform of
+    // conj(s) (|X| and the losses are the same; the gradients are mapped back).
+    int periodic, pconj;
+    int chi_out;           // forward output: 0 Ahat, 1 |X|^2 / E^2, 2 |X|^2
     // batch plan
     const WaveDesc* waves;
     const int2* items;     // (waveform, tile) of this launch's work items, longest first
     int n_items;
     unsigned int* counter; // zeroed before the launch
 };
+
+// Shared-memory length of the signal and of each gradient accumulator.
+__host__ __device__ __forceinline__ int sig_len(const AfParams& p) { return p.periodic ? 2 * p.N : p.N; }
 
 // The view of one waveform a kernel works with, in either mode.
 struct Wave {
@@ -73,6 +83,8 @@ struct Wave {
     int kind, N, M;
     int k_lo, k_hi, m_lo, m_hi, k_ml, m_ml;
     int r_lo, r_hi, rows_per_tile, tiles, full_m, defer_hi, unscaled;
+    int periodic, pconj;
+    int sN;         // shared-memory length of the signal and of each accumulator: N, or 2N periodic
     float eps, beta, w_psl, w_isl;
     // Fixed log-sum-exp shift (in units of Ahat^2), 0 = none.  For phase
     // input E = N and every cell has a2 = |X|^2/E^2 + eps/E^2 <= 1 + eps/N^2
@@ -98,6 +110,8 @@ __host__ __device__ __forceinline__ Wave wave_of(const AfParams& p, int b) {
         w.defer_hi = d.defer_hi;
         w.unscaled = d.unscaled;
         w.eps = d.eps; w.beta = d.beta; w.w_psl = d.w_psl; w.w_isl = d.w_isl;
+        w.periodic = 0;
+        w.pconj = 0;
     } else {
         w.x = static_cast<const char*>(p.x) + (long long)b * p.N * (p.kind == 1 ? 4 : 8);
         w.out_off = (long long)b * p.N;
@@ -109,7 +123,10 @@ __host__ __device__ __forceinline__ Wave wave_of(const AfParams& p, int b) {
         w.defer_hi = p.defer_hi;
         w.unscaled = 0;
         w.eps = p.eps; w.beta = p.beta; w.w_psl = p.w_psl; w.w_isl = p.w_isl;
+        w.periodic = p.periodic;
+        w.pconj = p.pconj;
     }
+    w.sN = w.periodic ? 2 * w.N : w.N;
     w.full_m = (w.m_lo == -(w.M / 2) && w.m_hi == w.M / 2 - 1) ? 1 : 0;
     w.lse_fix = 0.0f;
     if (w.kind == 1) {
@@ -235,14 +252,18 @@ __device__ __forceinline__ float load_signal(const Wave& wv, float2* s_sm, float
         for (int n = tid; n < wv.N; n += kThreads) {
             float sn, cs;
             sincosf(__ldg(ph + n), &sn, &cs);
-            s_sm[n] = make_float2(cs, sn);
+            const float2 v = make_float2(cs, wv.pconj ? -sn : sn);
+            s_sm[n] = v;
+            if (wv.periodic) s_sm[n + wv.N] = v;
             e = fmaf(cs, cs, fmaf(sn, sn, e));
         }
     } else {
         const float2* xs = static_cast<const float2*>(wv.x);
         for (int n = tid; n < wv.N; n += kThreads) {
             float2 v = __ldg(xs + n);
+            if (wv.pconj) v.y = -v.y;
             s_sm[n] = v;
+            if (wv.periodic) s_sm[n + wv.N] = v;
             e = fmaf(v.x, v.x, fmaf(v.y, v.y, e));
         }
     }

@@ -76,6 +76,12 @@ _SIGS = {
                                              graf_loss_t, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "graf_af_loss_backward_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, _i32, _i32, _i32, graf_window_t,
                                                      graf_loss_t, _vp, _vp, _vp, _vp, _vp]),
+    "graf_paf_forward": (ctypes.c_int, [_vp, ctypes.c_int, _i32, _i32, _i32, _i32, _vp, _vp]),
+    "graf_paf_workspace_bytes": (_sz, [_i32, _i32, graf_window_t]),
+    "graf_paf_loss": (ctypes.c_int, [_vp, ctypes.c_int, _i32, _i32, _i32, graf_window_t, graf_loss_t, _vp, _vp,
+                                     _sz, _vp]),
+    "graf_paf_loss_backward": (ctypes.c_int, [_vp, ctypes.c_int, _i32, _i32, _i32, graf_window_t, graf_loss_t,
+                                              _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "graf_batch_plan_create": (ctypes.c_int, [_i32, _vp, _vp, _vp, _vp, _i32, ctypes.c_int, _vp]),
     "graf_batch_plan_destroy": (ctypes.c_int, [_vp]),
     "graf_batch_workspace_bytes": (_sz, [_vp]),
@@ -126,6 +132,24 @@ def graf_version() -> int:
 
 def graf_af_forward(x, kind, B, N, M, w, eps, af_out, stream) -> int:
     return load().graf_af_forward(x, kind, B, N, M, w, eps, af_out, stream)
+
+
+def graf_paf_forward(x, kind, B, N, sign, normalise, chi_out, stream) -> int:
+    return load().graf_paf_forward(x, kind, B, N, sign, normalise, chi_out, stream)
+
+
+def graf_paf_workspace_bytes(B, N, w) -> int:
+    return load().graf_paf_workspace_bytes(B, N, w)
+
+
+def graf_paf_loss(x, kind, B, N, sign, w, l, out8, workspace, workspace_bytes, stream) -> int:
+    return load().graf_paf_loss(x, kind, B, N, sign, w, l, out8, workspace, workspace_bytes, stream)
+
+
+def graf_paf_loss_backward(x, kind, B, N, sign, w, l, out8, dL, grad_s, grad_phi, workspace, workspace_bytes,
+                           stream) -> int:
+    return load().graf_paf_loss_backward(x, kind, B, N, sign, w, l, out8, dL, grad_s, grad_phi, workspace,
+                                         workspace_bytes, stream)
 
 
 def graf_af_loss_workspace_bytes(B, N, M, w) -> int:
@@ -241,6 +265,12 @@ class Window:
         if m_ml is None:
             m_ml = max(M // N - 1, 0)
         return Window(-(N - 1), N - 1, -(M // 2), M // 2 - 1, k_ml, m_ml)
+
+    @staticmethod
+    def periodic(N: int, k_ml: int = 0, m_ml: int = 0) -> "Window":
+        """Every delay and Doppler bin of the periodic AF (both in [-N/2,
+        N/2-1]) minus the box (default: the origin)."""
+        return Window(-(N // 2), N // 2 - 1, -(N // 2), N // 2 - 1, k_ml, m_ml)
 
     @staticmethod
     def masked(K: int, Mw: int, k_ml: int = 0, m_ml: int = 0) -> "Window":
@@ -375,6 +405,38 @@ def af_loss_backward(x, M: int, window: Window | None = None, loss: Loss = Loss(
     _check(graf_af_loss_backward(x.data_ptr(), kind, B, N, M, w.c(), loss.c(), out8.data_ptr(),
                                  None if dl is None else dl.data_ptr(), gs, gp, ws.data_ptr(), ws.numel(),
                                  _stream(x.device)), "graf_af_loss_backward")
+    return out8, grad
+
+
+def paf_forward(x, sign: int = 1, normalise: bool = True):
+    """Periodic AF chi [B, N, N] (Eq. 7, Algorithm 1), fftshift order, over
+    max chi = E^2 if normalise."""
+    torch = _torch()
+    x, kind, B, N = _prep(x)
+    out = torch.empty((B, N, N), dtype=torch.float32, device=x.device)
+    _check(graf_paf_forward(x.data_ptr(), kind, B, N, int(sign), 1 if normalise else 0, out.data_ptr(),
+                            _stream(x.device)), "graf_paf_forward")
+    return out
+
+
+def paf_loss_backward(x, window: Window | None = None, loss: Loss = Loss(), sign: int = 1, dL=None):
+    """Loss scalars and gradient of the periodic AF (default window: every
+    delay and Doppler bin minus the origin); returns (out8 [B,8], grad)."""
+    torch = _torch()
+    x, kind, B, N = _prep(x)
+    w = window or Window.periodic(N)
+    nb = graf_paf_workspace_bytes(B, N, w.c())
+    if nb == 0:
+        raise GrafError(1, "graf_paf_workspace_bytes")
+    ws = _workspace(nb, x.device)
+    out8 = torch.empty((B, GRAF_LOSS_OUT), dtype=torch.float32, device=x.device)
+    grad = torch.empty((B, N), dtype=torch.float32 if kind == GRAF_IN_PHASE else torch.complex64, device=x.device)
+    dl = None if dL is None else dL.reshape(B).to(torch.float32).contiguous()
+    gs = grad.data_ptr() if kind == GRAF_IN_COMPLEX else None
+    gp = grad.data_ptr() if kind == GRAF_IN_PHASE else None
+    _check(graf_paf_loss_backward(x.data_ptr(), kind, B, N, int(sign), w.c(), loss.c(), out8.data_ptr(),
+                                  None if dl is None else dl.data_ptr(), gs, gp, ws.data_ptr(), ws.numel(),
+                                  _stream(x.device)), "graf_paf_loss_backward")
     return out8, grad
 
 
