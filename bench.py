@@ -622,6 +622,60 @@ def run_ragged(args):
     print(json.dumps(line), flush=True)
 
 
+def run_periodic(args):
+    """The paper's own periodic AF (Eq. 7, +j exponent) at its experiments'
+    length N = 256 (Sec. 7.1.2): 4096 random polyphase codes, all N delays x N
+    Doppler bins minus the origin, PSL(beta = 50) + ISL, loss + gradient
+    w.r.t. the phases."""
+    import torch
+
+    from paper_2506_22935_gb300 import graf as g
+    from paper_2506_22935_gb300 import inputs
+
+    g.load()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    Bp, Np = 4096, 256
+    seed = 2506229350 + 6
+    x = torch.from_numpy(inputs.random_phases(seed, Bp, Np)).to(dev)
+    w, loss = g.Window.periodic(Np), g.Loss(1.0, 1.0, BETA, EPS)
+    nb = g.graf_paf_workspace_bytes(Bp, Np, w.c())
+    ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+    out8 = torch.empty((Bp, 8), dtype=torch.float32, device=dev)
+    grad = torch.empty((Bp, Np), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        st = g.graf_paf_loss_backward(x.data_ptr(), g.GRAF_IN_PHASE, Bp, Np, 1, w.c(), loss.c(), out8.data_ptr(),
+                                      None, None, grad.data_ptr(), ws.data_ptr(), nb, stream.cuda_stream)
+        assert st == 0, g.graf_status_string(st)
+
+    steps = max(3, min(args.steps, 100))
+    with ClockSampler(0) as clk:
+        ms = _timed_events(step, steps, 5, stream, flush)
+    cells = Bp * Np * Np
+    alg = Bp * 2 * Np * 5.0 * Np * math.log2(Np)   # forward + adjoint DFT of every delay row
+    peaks, src = _measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    achieved = alg / (ms / 1e3) / 1e12
+    chi = g.paf_forward(x[:64], 1, normalise=True)
+    torch.cuda.synchronize()
+    line = {"metric": "periodic AF fwd+bwd Gcells/s at N=256", "value": cells / (ms / 1e3) / 1e9,
+            "unit": UNIT, "higher_is_better": True, "n_gpus": 1, "steps": steps, "warmup": 5,
+            "ms_per_step": ms, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{Bp} random polyphase codes, periodic AF (Eq. 7, +j), N={Np}, "
+                                   "all delays and Doppler bins minus the origin, PSL(beta=50)+ISL, "
+                                   "loss + gradient w.r.t. phases", "seed": seed,
+                       "l2": "flushed between steps (256 MB write, outside the timed events)"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None, "algorithmic_flop_per_step": alg,
+                         "peak_source": f"FP32 FMA peak at {sm_max:.0f} MHz ({src})"},
+            "mean_psl_hard": float(out8[:, 3].mean()), "mean_chi_max": float(chi.amax(dim=(1, 2)).mean()),
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def run_learned(args):
     """Time to a masked-ISL target from the learned proposal vs from a random
     initialisation (the second half of the headline metric).  The proposal is
@@ -702,7 +756,7 @@ def main():
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison pipeline")
     ap.add_argument("--batch", type=int, default=B,
                     help="waveforms per GPU (default 256, the benchmark workload; smaller only for profiling)")
-    ap.add_argument("--workload", default="af", choices=["af", "learned", "optim", "ragged"])
+    ap.add_argument("--workload", default="af", choices=["af", "learned", "optim", "ragged", "periodic"])
     ap.add_argument("--optim-runs", type=int, default=3)
     ap.add_argument("--cufft-stride", type=int, default=50,
                     help="ragged workload: the cuFFT comparison runs on every n-th code")
@@ -726,6 +780,8 @@ def main():
         run_optim(args)
     elif args.workload == "ragged":
         run_ragged(args)
+    elif args.workload == "periodic":
+        run_periodic(args)
     else:
         run_graf(args)
 

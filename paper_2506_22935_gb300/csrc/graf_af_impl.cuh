@@ -88,7 +88,8 @@ __global__ void __launch_bounds__(kThreads, 1) af_forward_kernel(AfParams p) {
     float* out_b = p.af_out + (size_t)b * rows_out * ncols;
     const int row0 = p.r_lo + tile * p.rows_per_tile;
     const int row_end = min(row0 + p.rows_per_tile, p.r_hi + 1);
-    const int iters = (p.rows_per_tile + (kThreads / P::TPR) - 1) / (kThreads / P::TPR);
+    // iterations for the rows this tile actually holds (CTA-uniform)
+    const int iters = max(0, row_end - row0 + (kThreads / P::TPR) - 1) / (kThreads / P::TPR);
 
     float2 v[P::VALS];
     for (int it = 0; it < iters; ++it) {
@@ -178,7 +179,8 @@ __device__ __forceinline__ void loss_item(const AfParams& p, int b, int tile, un
     const int row0 = wv.r_lo + tile * wv.rows_per_tile;
     const int row_end = min(row0 + wv.rows_per_tile, wv.r_hi + 1);
     constexpr int SLOTS = kThreads / P::TPR;
-    const int iters = (wv.rows_per_tile + SLOTS - 1) / SLOTS;
+    // iterations for the rows this tile actually holds (CTA-uniform)
+    const int iters = max(0, row_end - row0 + SLOTS - 1) / SLOTS;
 
     float isl = 0.0f, mx = -CUDART_INF_F, sum = 0.0f, T = 0.0f;
     float2 v[P::VALS];
@@ -456,7 +458,8 @@ __device__ __forceinline__ void backward_item(const AfParams& p, int b, int tile
 
     const int row0 = wv.r_lo + tile * wv.rows_per_tile;
     const int row_end = min(row0 + wv.rows_per_tile, wv.r_hi + 1);
-    const int iters = (wv.rows_per_tile + SLOTS - 1) / SLOTS;
+    // iterations for the rows this tile actually holds (CTA-uniform)
+    const int iters = max(0, row_end - row0 + SLOTS - 1) / SLOTS;
 
     float2 v[P::VALS];
     for (int it = 0; it < iters; ++it) {
@@ -598,7 +601,8 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
 
     const int row0 = wv.r_lo + tile * wv.rows_per_tile;
     const int row_end = min(row0 + wv.rows_per_tile, wv.r_hi + 1);
-    const int iters = (wv.rows_per_tile + SLOTS - 1) / SLOTS;
+    // iterations for the rows this tile actually holds (CTA-uniform)
+    const int iters = max(0, row_end - row0 + SLOTS - 1) / SLOTS;
 
     float isl = 0.0f, zs = 0.0f, ts = 0.0f, cs = 0.0f;
     const bool fixed = wv.lse_fix > 0.0f;      // fixed shift: no running maximum

@@ -243,8 +243,10 @@ static graf_status_t af_loss_backward_impl(const Mode& md, const void* x, graf_i
     if (acc < 1) return GRAF_ERR_UNSUPPORTED;
     const bool phase_only = kind == GRAF_IN_PHASE && grad_s == nullptr;
     FusedPlan f = fused_plan(B, N, M, w, l.w_psl != 0.0f, phase_only);
-    // on the PSL path each row slot needs its own gradient accumulator
-    if (l.w_psl != 0.0f && acc < graf::kThreads / graf::tpr_of(M)) f.fused = false;
+    // on the PSL path with a running log-sum-exp shift each row slot needs its
+    // own gradient accumulator (it rescales it); a fixed shift rescales nothing
+    const bool fixed = graf::lse_fixed_shift(kind == GRAF_IN_PHASE ? 1 : 0, l.eps, l.beta, N) > 0.0f;
+    if (l.w_psl != 0.0f && !fixed && acc < graf::kThreads / graf::tpr_of(M)) f.fused = false;
     if (!f.fused) {
         s = af_loss_impl(md, x, kind, B, N, M, w, l, out8, workspace, workspace_bytes, stream);
         if (s != GRAF_OK) return s;

@@ -253,13 +253,15 @@ graf_status_t graf_batch_plan_create(int32_t B, const int32_t* N_host, const int
         }
         // fused unless a waveform has PSL over a window that does not span every
         // Doppler bin, or mainlobe-box rows beyond row 0 (row 0 carries no phase
-        // gradient), or the slots cannot each own an accumulator
+        // gradient), or its log-sum-exp shift is a running one (it rescales the
+        // accumulators) and the slots cannot each own an accumulator
         const int slots = graf::kThreads / graf::tpr_of(M);
         for (int b : bk.waves) {
             WaveDesc& d = P->waves[b];
             const bool full_m = d.m_lo == -(M / 2) && d.m_hi == M / 2 - 1;
+            const bool fixed = graf::lse_fixed_shift(P->kind == GRAF_IN_PHASE ? 1 : 0, d.eps, d.beta, d.N) > 0.0f;
             if (d.w_psl != 0.0f) {
-                if (!full_m || d.k_ml >= 1 || bk.acc_copies < slots) bk.fused = false;
+                if (!full_m || d.k_ml >= 1 || (!fixed && bk.acc_copies < slots)) bk.fused = false;
                 else if (d.k_ml == 0 && d.m_ml >= 0 && d.r_lo == 0) d.defer_hi = 0;
             }
         }

@@ -95,6 +95,15 @@ struct Wave {
     float lse_fix;
 };
 
+// The fixed log-sum-exp shift of a waveform (see Wave::lse_fix), 0 = none.
+// Host code uses it too: with a fixed shift no accumulator is ever rescaled,
+// so the fused PSL path may share gradient accumulators between row slots.
+__host__ __device__ __forceinline__ float lse_fixed_shift(int kind, float eps, float beta, int N) {
+    if (kind != 1) return 0.0f;
+    const float m = 0.5f * (1.0f + eps / ((float)N * (float)N));
+    return beta * 1.4426950408889634f * m <= 88.0f ? m : 0.0f;
+}
+
 __host__ __device__ __forceinline__ Wave wave_of(const AfParams& p, int b) {
     Wave w;
     w.kind = p.kind;
@@ -128,11 +137,7 @@ __host__ __device__ __forceinline__ Wave wave_of(const AfParams& p, int b) {
     }
     w.sN = w.periodic ? 2 * w.N : w.N;
     w.full_m = (w.m_lo == -(w.M / 2) && w.m_hi == w.M / 2 - 1) ? 1 : 0;
-    w.lse_fix = 0.0f;
-    if (w.kind == 1) {
-        const float m = 0.5f * (1.0f + w.eps / ((float)w.N * (float)w.N));
-        if (w.beta * 1.4426950408889634f * m <= 88.0f) w.lse_fix = m;
-    }
+    w.lse_fix = lse_fixed_shift(w.kind, w.eps, w.beta, w.N);
     return w;
 }
 
