@@ -353,6 +353,27 @@ GRAF_API graf_status_t graf_paf_loss_backward(const void* x, graf_input_t kind, 
                                               const float* dL, graf_c32* grad_s, float* grad_phi,
                                               void* workspace, size_t workspace_bytes, void* stream);
 
+/*
+ * Spectral variance: the LPI term of the paper's experiment loss (Sec. 7.1.1,
+ * Eq. 25), SV = var{|FFT(s)|^2 / sum |FFT(s)|^2} (population variance over the
+ * N bins of the N-point DFT), per waveform, and its gradient, so that
+ * L = PSL + lambda alpha SV is one graf_paf_loss_backward (or
+ * graf_af_loss_backward) followed by this call on the same stream.
+ *   x, kind, B, N: as above; N a power of two in [GRAF_M_MIN, GRAF_M_MAX].
+ *   weight: lambda alpha.
+ *   out8 [B][8] (nullable): out8[b][0] += weight * SV (the total loss) and
+ *     out8[b][7] = SV.
+ *   sv_out [B] (nullable): SV.
+ *   grad_s [B][N] (nullable): weight * 2 dSV/ds*, grad_phi [B][N] (nullable,
+ *     phase input only): weight * dSV/dphi; added to the arrays' contents if
+ *     accumulate != 0, else written.
+ * Errors: GRAF_ERR_INVALID_ARG for a violated constraint, GRAF_ERR_CUDA for a
+ * launch failure.
+ */
+GRAF_API graf_status_t graf_spectral_variance(const void* x, graf_input_t kind, int32_t B, int32_t N,
+                                              float weight, float* out8, float* sv_out, graf_c32* grad_s,
+                                              float* grad_phi, int32_t accumulate, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -299,3 +299,23 @@ def pfd_grad_phi(phi, window, w_psl=1.0, w_isl=1.0, beta=50.0, eps=1e-12, sign=1
     _check(_load().orc_pfd_grad_phi(_ptr(phi), phi.shape[0], int(sign), w.ctypes.data_as(_ip), w_psl, w_isl,
                                     beta, eps, h, _ptr(g)), "pfd_grad_phi")
     return g
+
+
+def optimize_experiment(phi0, window, w_psl, w_isl, beta, eps, spectral_weight, steps, sign=1, lr=1e-2,
+                        beta1=0.9, beta2=0.999, adam_eps=1e-8):
+    """The experiment of Sec. 7.1 restated: Adam (lr 0.01) on the phases for
+    L = L_AF(periodic AF of Eq. 7) + lambda alpha SpectralVariance (Eq. 25);
+    per step the loss and dL/dphi of both terms, then one Adam update.
+    Returns (phi after `steps` steps, loss before each step)."""
+    from . import spectral
+    phi = np.asarray(phi0, dtype=np.float64).copy()
+    m = np.zeros_like(phi)
+    v = np.zeros_like(phi)
+    hist = []
+    for t in range(1, steps + 1):
+        s = signal_from_phase(phi)
+        _, gphi, out = pgrad(s, window, w_psl, w_isl, beta, eps, sign)
+        sv, _, gsv = spectral.spectral_variance_grad(s)
+        hist.append(out[0] + spectral_weight * sv)
+        phi, m, v = adam_update(phi, m, v, gphi + spectral_weight * gsv, t, lr, beta1, beta2, adam_eps)
+    return phi, np.array(hist)

@@ -534,6 +534,131 @@ __device__ __forceinline__ float slot_max(float x, float* scratch, int slot) {
     }
 }
 
+// Sum over the TPR threads of one row slot, in a fixed order.
+template <int TPR>
+__device__ __forceinline__ float slot_sum(float x, float* scratch, int slot) {
+    if constexpr (TPR <= 32) {
+#pragma unroll
+        for (int o = TPR / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        return x;
+    } else {
+        constexpr int WPS = TPR / 32;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        const int wi = (threadIdx.x % TPR) >> 5;
+        float* sc = scratch + slot * WPS;
+        if ((threadIdx.x & 31) == 0) sc[wi] = x;
+        row_sync<TPR>(slot);
+        float s = sc[0];
+#pragma unroll
+        for (int i = 1; i < WPS; ++i) s += sc[i];
+        row_sync<TPR>(slot);
+        return s;
+    }
+}
+
+// ---------------------------------------------------------- spectral variance
+// One row slot per waveform (N = M):
+//   S = DFT_N(s), P = |S|^2, q = P / sum P, SV = (1/N) sum (q - 1/N)^2
+//   dSV/dP[g] = (2 / (N sum P)) (q[g] - sum_f q[f]^2)
+//             = (2 / (N sum P)) ((q[g] - 1/N) - N SV)        (no cancellation)
+//   dSV/ds*[n] = sum_g dSV/dP[g] S[g] exp(+j 2 pi g n / N)  (adjoint DFT, run
+//                as conj(DFT(conj(.))) on the same transform instance)
+template <int M>
+__global__ void __launch_bounds__(kThreads, 1) spectral_kernel(SpecParams q) {
+    using P = RowPlan<M>;
+    constexpr int SLOTS = kThreads / P::TPR;
+    extern __shared__ __align__(256) unsigned char smem[];
+    float2* bufs = reinterpret_cast<float2*>(smem);
+    float* red = reinterpret_cast<float*>(smem + row_buffer_bytes<M>());
+    const int tid = threadIdx.x, slot = tid / P::TPR, t = tid % P::TPR;
+    const int b = blockIdx.x * SLOTS + slot;
+    const bool valid = b < q.B;  // slot-uniform
+    float2* buf = bufs + (size_t)slot * (P::SPLIT ? P::SMEM_ROW / 2 : P::SMEM_ROW);
+    float2 v[P::VALS];
+    sfor<0, P::VALS>([&](auto w) {
+        const int n = t + P::TPR * decltype(w)::value;
+        float2 s = make_float2(0.0f, 0.0f);
+        if (valid) {
+            if (q.kind == 1) {
+                float sn, cs;
+                sincosf(__ldg(static_cast<const float*>(q.x) + (size_t)b * M + n), &sn, &cs);
+                s = make_float2(cs, sn);
+            } else {
+                s = __ldg(static_cast<const float2*>(q.x) + (size_t)b * M + n);
+            }
+        }
+        v[w] = s;
+    });
+    row_sync<P::TPR>(slot);
+    row_fft<M, false, false, false>(v, buf, t, slot);
+    float pt = 0.0f;
+    sfor<0, P::VALS>([&](auto w) { pt = fmaf(v[w].x, v[w].x, fmaf(v[w].y, v[w].y, pt)); });
+    const float ptot = slot_sum<P::TPR>(pt, red, slot);
+    const float inv = ptot > 0.0f ? 1.0f / ptot : 0.0f;
+    constexpr float invN = 1.0f / (float)M;
+    float d2 = 0.0f;
+    sfor<0, P::VALS>([&](auto w) {
+        const float d = fmaf(fmaf(v[w].x, v[w].x, v[w].y * v[w].y), inv, -invN);
+        d2 = fmaf(d, d, d2);
+    });
+    const float sv = slot_sum<P::TPR>(d2, red, slot) * invN;
+    const float kf = 2.0f * invN * inv;
+    const float nsv = (float)M * sv;
+    sfor<0, P::VALS>([&](auto w) {
+        const float2 x = v[w];
+        const float d = fmaf(fmaf(x.x, x.x, x.y * x.y), inv, -invN);
+        const float c = kf * (d - nsv);
+        v[w] = make_float2(c * x.x, -c * x.y);  // conj(dSV/dP S)
+    });
+    row_sync<P::TPR>(slot);
+    row_fft<M, false, false, false>(v, buf, t, slot);
+    if (!valid) return;
+    const float wt2 = 2.0f * q.weight;
+    sfor<0, P::VALS>([&](auto w) {
+        const int n = t + P::TPR * decltype(w)::value;
+        const float2 g = make_float2(v[w].x, -v[w].y);  // dSV/ds*[n]
+        const size_t i = (size_t)b * M + n;
+        if (q.grad_s) {
+            float2 o = make_float2(wt2 * g.x, wt2 * g.y);
+            if (q.accumulate) o = cadd(o, q.grad_s[i]);
+            q.grad_s[i] = o;
+        }
+        if (q.grad_phi) {
+            float2 s;
+            if (q.kind == 1) {
+                float sn, cs;
+                sincosf(static_cast<const float*>(q.x)[i], &sn, &cs);
+                s = make_float2(cs, sn);
+            } else {
+                s = static_cast<const float2*>(q.x)[i];
+            }
+            float o = wt2 * (g.y * s.x - g.x * s.y);
+            if (q.accumulate) o += q.grad_phi[i];
+            q.grad_phi[i] = o;
+        }
+    });
+    if (t == 0) {
+        if (q.out8) {
+            q.out8[(size_t)b * 8] += q.weight * sv;
+            q.out8[(size_t)b * 8 + 7] = sv;
+        }
+        if (q.sv) q.sv[b] = sv;
+    }
+}
+
+template <int M>
+cudaError_t run_spectral_m(const SpecParams& q, cudaStream_t st) {
+    using P = RowPlan<M>;
+    constexpr int SLOTS = kThreads / P::TPR;
+    const size_t smem = row_buffer_bytes<M>() + kRedBytes;
+    cudaError_t e = cudaFuncSetAttribute(spectral_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = (unsigned)((q.B + SLOTS - 1) / SLOTS);
+    spectral_kernel<M><<<grid, kThreads, smem, st>>>(q);
+    return cudaGetLastError();
+}
+
 // One pass per row: lag product, forward DFT, loss partials and, for rows
 // whose weights are uniform over the row, the gradient remainder of the split
 // adjoint (see af_backward_kernel) -- no recomputation, no stored AF.
@@ -844,4 +969,5 @@ cudaError_t run_fused_m(const AfParams& p, cudaStream_t st) {
     template cudaError_t graf::run_forward_m<M>(const graf::AfParams&, cudaStream_t);  \
     template cudaError_t graf::run_loss_m<M>(const graf::AfParams&, cudaStream_t);     \
     template cudaError_t graf::run_backward_m<M>(const graf::AfParams&, cudaStream_t); \
-    template cudaError_t graf::run_fused_m<M>(const graf::AfParams&, cudaStream_t);
+    template cudaError_t graf::run_fused_m<M>(const graf::AfParams&, cudaStream_t);    \
+    template cudaError_t graf::run_spectral_m<M>(const graf::SpecParams&, cudaStream_t);

@@ -339,6 +339,26 @@ graf_status_t graf_af_loss_backward(const void* x, graf_input_t kind, int32_t B,
                                  workspace_bytes, stream);
 }
 
+graf_status_t graf_spectral_variance(const void* x, graf_input_t kind, int32_t B, int32_t N, float weight,
+                                     float* out8, float* sv_out, graf_c32* grad_s, float* grad_phi,
+                                     int32_t accumulate, void* stream) {
+    if (!x || (kind != GRAF_IN_COMPLEX && kind != GRAF_IN_PHASE)) return GRAF_ERR_INVALID_ARG;
+    if (B < 1 || B > (1 << 20) || !is_pow2(N) || N < GRAF_M_MIN || N > GRAF_M_MAX) return GRAF_ERR_INVALID_ARG;
+    if (!(weight == weight) || (grad_phi && kind != GRAF_IN_PHASE)) return GRAF_ERR_INVALID_ARG;
+    graf::SpecParams q{};
+    q.x = x;
+    q.kind = kind == GRAF_IN_PHASE ? 1 : 0;
+    q.B = B;
+    q.N = N;
+    q.weight = weight;
+    q.out8 = out8;
+    q.sv = sv_out;
+    q.grad_s = reinterpret_cast<float2*>(grad_s);
+    q.grad_phi = grad_phi;
+    q.accumulate = accumulate ? 1 : 0;
+    return cuda_status(graf::run_spectral(q, static_cast<cudaStream_t>(stream)));
+}
+
 // ------------------------------------------------------------ periodic AF
 static Mode periodic_mode(int32_t sign) { return Mode{1, sign > 0 ? 1 : 0}; }
 

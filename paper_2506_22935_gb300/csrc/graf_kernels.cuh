@@ -72,6 +72,21 @@ struct AfParams {
     unsigned int* counter; // zeroed before the launch
 };
 
+// Spectral variance of the normalised power spectrum (the LPI term of the
+// experiment loss, Sec. 7.1.1 Eq. 25), one row slot per waveform.
+struct SpecParams {
+    const void* x;   // [B][N] phases (kind 1) or complex64 (kind 0)
+    int kind, B, N;
+    float weight;    // its weight in the loss (lambda alpha)
+    float* out8;     // nullable: out8[b][0] += weight SV, out8[b][7] = SV
+    float* sv;       // nullable: SV [B]
+    float2* grad_s;  // nullable: += or = weight * 2 dSV/ds*
+    float* grad_phi; // nullable: += or = weight * dSV/dphi
+    int accumulate;
+};
+cudaError_t run_spectral(const SpecParams& q, cudaStream_t st);
+template <int M> cudaError_t run_spectral_m(const SpecParams& q, cudaStream_t st);
+
 // Shared-memory length of the signal and of each gradient accumulator.
 __host__ __device__ __forceinline__ int sig_len(const AfParams& p) { return p.periodic ? 2 * p.N : p.N; }
 

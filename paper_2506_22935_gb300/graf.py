@@ -82,6 +82,8 @@ _SIGS = {
                                      _sz, _vp]),
     "graf_paf_loss_backward": (ctypes.c_int, [_vp, ctypes.c_int, _i32, _i32, _i32, graf_window_t, graf_loss_t,
                                               _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "graf_spectral_variance": (ctypes.c_int, [_vp, ctypes.c_int, _i32, _i32, ctypes.c_float, _vp, _vp, _vp, _vp,
+                                              _i32, _vp]),
     "graf_batch_plan_create": (ctypes.c_int, [_i32, _vp, _vp, _vp, _vp, _i32, ctypes.c_int, _vp]),
     "graf_batch_plan_destroy": (ctypes.c_int, [_vp]),
     "graf_batch_workspace_bytes": (_sz, [_vp]),
@@ -132,6 +134,24 @@ def graf_version() -> int:
 
 def graf_af_forward(x, kind, B, N, M, w, eps, af_out, stream) -> int:
     return load().graf_af_forward(x, kind, B, N, M, w, eps, af_out, stream)
+
+
+def graf_spectral_variance(x, kind, B, N, weight, out8, sv_out, grad_s, grad_phi, accumulate, stream) -> int:
+    return load().graf_spectral_variance(x, kind, B, N, weight, out8, sv_out, grad_s, grad_phi, accumulate,
+                                         stream)
+
+
+def spectral_variance(x, weight: float = 1.0):
+    """(SV [B], weighted gradient) of the normalised power spectrum (Eq. 25)."""
+    torch = _torch()
+    x, kind, B, N = _prep(x)
+    sv = torch.empty(B, dtype=torch.float32, device=x.device)
+    grad = torch.empty((B, N), dtype=torch.float32 if kind == GRAF_IN_PHASE else torch.complex64, device=x.device)
+    gs = grad.data_ptr() if kind == GRAF_IN_COMPLEX else None
+    gp = grad.data_ptr() if kind == GRAF_IN_PHASE else None
+    _check(graf_spectral_variance(x.data_ptr(), kind, B, N, float(weight), None, sv.data_ptr(), gs, gp, 0,
+                                  _stream(x.device)), "graf_spectral_variance")
+    return sv, grad
 
 
 def graf_paf_forward(x, kind, B, N, sign, normalise, chi_out, stream) -> int:

@@ -31,20 +31,31 @@ class PhaseOptimizer:
     """Adam on phases phi [B, N] (float32, CUDA, updated in place) for the loss
     ``loss`` over ``window`` with Doppler length M; or, with ``plan`` (a
     graf.BatchPlan), on the packed phases of a ragged batch whose windows and
-    losses the plan holds (phi then [sum N] or [B, N] for equal lengths)."""
+    losses the plan holds (phi then [sum N] or [B, N] for equal lengths).
+
+    ``periodic_sign`` (+1 or -1) selects the paper's periodic AF (Eq. 7, M = N)
+    instead of the aperiodic one; ``spectral_weight`` adds lambda alpha times
+    the spectral variance of Eq. 25 to the loss and its gradient (the
+    experiment loss of Sec. 7.1.1)."""
 
     def __init__(self, phi: torch.Tensor, M: int = 0, window: g.Window | None = None, loss: g.Loss | None = None,
-                 adam: Adam = Adam(), history_len: int = 1000, plan: "g.BatchPlan | None" = None):
+                 adam: Adam = Adam(), history_len: int = 1000, plan: "g.BatchPlan | None" = None,
+                 periodic_sign: int | None = None, spectral_weight: float = 0.0):
         if phi.dtype != torch.float32 or not phi.is_cuda or not phi.is_contiguous():
             raise ValueError("phi must be a contiguous CUDA float32 tensor")
         g.load()
         self.phi, self.M, self.window, self.loss, self.adam, self.plan = phi, M, window, loss, adam, plan
+        self.periodic_sign, self.spectral_weight = periodic_sign, float(spectral_weight)
         dev = phi.device
         if plan is None:
             if phi.dim() != 2:
                 raise ValueError("phi must be [B, N]")
             self.B, self.N = phi.shape
-            self.nb = g.graf_af_backward_workspace_bytes(self.B, self.N, M, window.c())
+            if periodic_sign is not None:
+                self.M = self.N
+                self.nb = g.graf_paf_workspace_bytes(self.B, self.N, window.c())
+            else:
+                self.nb = g.graf_af_backward_workspace_bytes(self.B, self.N, M, window.c())
             if self.nb == 0:
                 raise g.GrafError(1, "graf_af_backward_workspace_bytes")
             self.ws = torch.empty(self.nb, dtype=torch.uint8, device=dev)
@@ -66,7 +77,11 @@ class PhaseOptimizer:
     def enqueue_step(self) -> None:
         """Enqueue one optimisation step on torch's current stream."""
         st = torch.cuda.current_stream(self.phi.device).cuda_stream
-        if self.plan is None:
+        if self.plan is None and self.periodic_sign is not None:
+            r = g.graf_paf_loss_backward(self.phi.data_ptr(), g.GRAF_IN_PHASE, self.B, self.N, self.periodic_sign,
+                                         self._wc, self._lc, self.out8.data_ptr(), None, None, self.grad.data_ptr(),
+                                         self.ws.data_ptr(), self.nb, st)
+        elif self.plan is None:
             r = g.graf_af_loss_backward(self.phi.data_ptr(), g.GRAF_IN_PHASE, self.B, self.N, self.M, self._wc,
                                         self._lc, self.out8.data_ptr(), None, None, self.grad.data_ptr(),
                                         self.ws.data_ptr(), self.nb, st)
@@ -75,6 +90,13 @@ class PhaseOptimizer:
                                            self.grad.data_ptr(), self.ws.data_ptr(), self.nb, st)
         if r != 0:
             raise g.GrafError(r, "graf_af_loss_backward")
+        if self.spectral_weight != 0.0:
+            if self.plan is not None:
+                raise ValueError("the spectral term needs equal-length waveforms")
+            r = g.graf_spectral_variance(self.phi.data_ptr(), g.GRAF_IN_PHASE, self.B, self.N, self.spectral_weight,
+                                         self.out8.data_ptr(), None, None, self.grad.data_ptr(), 1, st)
+            if r != 0:
+                raise g.GrafError(r, "graf_spectral_variance")
         r = g.graf_record_loss(self.out8.data_ptr(), self.B, self.history.data_ptr(), self.history.shape[0],
                                self.step_counter.data_ptr(), st)
         if r != 0:
