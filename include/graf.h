@@ -374,6 +374,25 @@ GRAF_API graf_status_t graf_spectral_variance(const void* x, graf_input_t kind, 
                                               float weight, float* out8, float* sv_out, graf_c32* grad_s,
                                               float* grad_phi, int32_t accumulate, void* stream);
 
+/*
+ * Two more terms of the composite loss (Sec. 5.1 and Sec. 5.2, Eq. 22):
+ *   W = sum_{k=-(N-1)}^{N-1} |k| sigmoid(gamma (a2[k] - 1/2)), the
+ *       differentiable -3 dB mainlobe width of Sec. 5.1, with
+ *       a2[k] = (|r[k]|^2 + eps) / E^2 = chi(k, 0) / chi(0, 0) and
+ *       r[k] = sum_n s[n] conj(s[n-k]) the zero-Doppler column of the AF;
+ *   V = var(|s|), the constant-modulus penalty L_const of Eq. 22.
+ * Adds w_width W + w_const V to out8[b][0] (nullable), writes {W, V} to
+ * terms_out [B][2] (nullable), and the gradient of w_width W + w_const V to
+ * grad_s [B][N] (2 dL/ds*) or grad_phi [B][N] (phase input), added to their
+ * contents if accumulate != 0, else written; N <= GRAF_M_MAX / 2, gamma > 0,
+ * eps >= 0 (GRAF_ERR_INVALID_ARG otherwise).  Computed with transforms of
+ * length nextpow2(2N), so the lags do not wrap.
+ */
+GRAF_API graf_status_t graf_composite_terms(const void* x, graf_input_t kind, int32_t B, int32_t N,
+                                            float gamma, float eps, float w_width, float w_const, float* out8,
+                                            float* terms_out, graf_c32* grad_s, float* grad_phi,
+                                            int32_t accumulate, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -340,6 +340,7 @@ int acc_copies_for(int M, int N) {
 
 cudaError_t run_forward(const AfParams& p, cudaStream_t st) { GRAF_DISPATCH_M(run_forward_m, p.M, p, st) }
 cudaError_t run_spectral(const SpecParams& q, cudaStream_t st) { GRAF_DISPATCH_M(run_spectral_m, q.N, q, st) }
+cudaError_t run_composite(const CompParams& q, int M, cudaStream_t st) { GRAF_DISPATCH_M(run_composite_m, M, q, st) }
 cudaError_t run_loss(const AfParams& p, cudaStream_t st) {
     cudaError_t e;
     switch (p.M) {

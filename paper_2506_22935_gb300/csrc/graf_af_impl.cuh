@@ -659,6 +659,156 @@ cudaError_t run_spectral_m(const SpecParams& q, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------- composite terms
+// One row slot per waveform, row length M >= 2N - 1 (no circular wrap):
+//   S = DFT_M(s), r[k] = IDFT_M(|S|^2)[k] = sum_n s[n] conj(s[n-k]) (the
+//   zero-Doppler column of the AF, lag k at index k mod M),
+//   a2 = (|r|^2 + eps) / E^2, W = sum_{|k| < N} |k| sigmoid(gamma (a2 - 1/2)),
+//   G[k] = dL/dr*[k] = w_width |k| gamma sig (1 - sig) r[k] / E^2,
+//   dL/ds* = IDFT_M(2 Re(DFT_M(G)) S) + energy term + w_const dV/ds*,
+// the product rule on r[k] written as a convolution plus a correlation with
+// s.  Five transforms per waveform; Re(DFT(G)) waits in shared memory while
+// S is transformed again.
+template <int M>
+__global__ void __launch_bounds__(kThreads, 1) composite_kernel(CompParams q) {
+    using P = RowPlan<M>;
+    constexpr int SLOTS = kThreads / P::TPR;
+    extern __shared__ __align__(256) unsigned char smem[];
+    float2* bufs = reinterpret_cast<float2*>(smem);
+    float* stash = reinterpret_cast<float*>(smem + row_buffer_bytes<M>());
+    float* red = stash + (size_t)SLOTS * M;
+    const int tid = threadIdx.x, slot = tid / P::TPR, t = tid % P::TPR;
+    const int b = blockIdx.x * SLOTS + slot;
+    const bool valid = b < q.B;  // slot-uniform
+    const int N = q.N;
+    float2* buf = bufs + (size_t)slot * (P::SPLIT ? P::SMEM_ROW / 2 : P::SMEM_ROW);
+    float* st = stash + (size_t)slot * M;
+    auto load = [&](float2* v) {
+        sfor<0, P::VALS>([&](auto w) {
+            const int n = t + P::TPR * decltype(w)::value;
+            float2 s = make_float2(0.0f, 0.0f);
+            if (valid && n < N) {
+                if (q.kind == 1) {
+                    float sn, cs;
+                    sincosf(__ldg(static_cast<const float*>(q.x) + (size_t)b * N + n), &sn, &cs);
+                    s = make_float2(cs, sn);
+                } else {
+                    s = __ldg(static_cast<const float2*>(q.x) + (size_t)b * N + n);
+                }
+            }
+            v[w] = s;
+        });
+    };
+    float2 v[P::VALS];
+    load(v);
+    // energy and the modulus statistics
+    float e = 0.0f, am = 0.0f;
+    sfor<0, P::VALS>([&](auto w) {
+        const float a2 = fmaf(v[w].x, v[w].x, v[w].y * v[w].y);
+        e += a2;
+        am += sqrtf(a2);
+    });
+    const float E = slot_sum<P::TPR>(e, red, slot);
+    const float mu = slot_sum<P::TPR>(am, red, slot) / (float)N;
+    float vv = 0.0f;
+    sfor<0, P::VALS>([&](auto w) {
+        const int n = t + P::TPR * decltype(w)::value;
+        const float d = sqrtf(fmaf(v[w].x, v[w].x, v[w].y * v[w].y)) - mu;
+        if (n < N) vv = fmaf(d, d, vv);
+    });
+    const float V = slot_sum<P::TPR>(vv, red, slot) / (float)N;
+    // S, then r = conj(DFT(|S|^2)) / M
+    row_sync<P::TPR>(slot);
+    row_fft<M, false, false, false>(v, buf, t, slot);
+    sfor<0, P::VALS>([&](auto w) { v[w] = make_float2(fmaf(v[w].x, v[w].x, v[w].y * v[w].y), 0.0f); });
+    row_sync<P::TPR>(slot);
+    row_fft<M, false, false, false>(v, buf, t, slot);
+    const float invE2 = E > 0.0f ? 1.0f / (E * E) : 0.0f;
+    const float invM = 1.0f / (float)M;
+    float wsum = 0.0f, esum = 0.0f;
+    sfor<0, P::VALS>([&](auto w) {
+        const int i = t + P::TPR * decltype(w)::value;
+        const int k = i <= M / 2 ? i : i - M;
+        const int ak = k < 0 ? -k : k;
+        const float2 r = make_float2(v[w].x * invM, -v[w].y * invM);
+        float2 g = make_float2(0.0f, 0.0f);
+        if (ak < N) {
+            const float a2 = fmaf(fmaf(r.x, r.x, r.y * r.y), invE2, q.eps * invE2);
+            const float sg = 1.0f / (1.0f + __expf(-q.gamma * (a2 - 0.5f)));
+            wsum = fmaf((float)ak, sg, wsum);
+            const float d = (float)ak * q.gamma * sg * (1.0f - sg);
+            esum = fmaf(d, a2, esum);
+            const float c = q.w_width * d * invE2;
+            g = make_float2(c * r.x, c * r.y);
+        }
+        v[w] = g;
+    });
+    const float W = slot_sum<P::TPR>(wsum, red, slot);
+    const float dLdE = -2.0f * q.w_width * slot_sum<P::TPR>(esum, red, slot) / E;
+    // Re(DFT(G)) into the stash, S again, then the adjoint of 2 Re(G^) S
+    row_sync<P::TPR>(slot);
+    row_fft<M, false, false, false>(v, buf, t, slot);
+    sfor<0, P::VALS>([&](auto w) { st[t + P::TPR * decltype(w)::value] = 2.0f * v[w].x; });
+    load(v);
+    row_sync<P::TPR>(slot);
+    row_fft<M, false, false, false>(v, buf, t, slot);
+    sfor<0, P::VALS>([&](auto w) {
+        const float rg = st[t + P::TPR * decltype(w)::value] * invM;
+        v[w] = make_float2(rg * v[w].x, -rg * v[w].y);  // conj(y), y = 2 Re(G^) S / M
+    });
+    row_sync<P::TPR>(slot);
+    row_fft<M, false, false, false>(v, buf, t, slot);
+    if (!valid) return;
+    sfor<0, P::VALS>([&](auto w) {
+        const int n = t + P::TPR * decltype(w)::value;
+        if (n < N) {
+            float2 s;
+            if (q.kind == 1) {
+                float sn, cs;
+                sincosf(static_cast<const float*>(q.x)[(size_t)b * N + n], &sn, &cs);
+                s = make_float2(cs, sn);
+            } else {
+                s = static_cast<const float2*>(q.x)[(size_t)b * N + n];
+            }
+            const float as = sqrtf(fmaf(s.x, s.x, s.y * s.y));
+            const float cv = as > 0.0f ? q.w_const * (as - mu) / ((float)N * as) : 0.0f;
+            const float k2 = dLdE + cv;  // real multiplier of s[n]
+            const float2 gw = make_float2(fmaf(k2, s.x, v[w].x), fmaf(k2, s.y, -v[w].y));  // dL/ds*[n]
+            const size_t i = (size_t)b * N + n;
+            if (q.grad_s) {
+                float2 o = make_float2(2.0f * gw.x, 2.0f * gw.y);
+                if (q.accumulate) o = cadd(o, q.grad_s[i]);
+                q.grad_s[i] = o;
+            }
+            if (q.grad_phi) {
+                float o = 2.0f * (gw.y * s.x - gw.x * s.y);
+                if (q.accumulate) o += q.grad_phi[i];
+                q.grad_phi[i] = o;
+            }
+        }
+    });
+    if (t == 0) {
+        if (q.out8) q.out8[(size_t)b * 8] += q.w_width * W + q.w_const * V;
+        if (q.terms) {
+            q.terms[2 * (size_t)b] = W;
+            q.terms[2 * (size_t)b + 1] = V;
+        }
+    }
+}
+
+template <int M>
+cudaError_t run_composite_m(const CompParams& q, cudaStream_t st) {
+    using P = RowPlan<M>;
+    constexpr int SLOTS = kThreads / P::TPR;
+    const size_t smem = row_buffer_bytes<M>() + (size_t)SLOTS * M * sizeof(float) + kRedBytes;
+    if (smem > kMaxSmem) return cudaErrorInvalidConfiguration;
+    cudaError_t e = cudaFuncSetAttribute(composite_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = (unsigned)((q.B + SLOTS - 1) / SLOTS);
+    composite_kernel<M><<<grid, kThreads, smem, st>>>(q);
+    return cudaGetLastError();
+}
+
 // One pass per row: lag product, forward DFT, loss partials and, for rows
 // whose weights are uniform over the row, the gradient remainder of the split
 // adjoint (see af_backward_kernel) -- no recomputation, no stored AF.
@@ -970,4 +1120,5 @@ cudaError_t run_fused_m(const AfParams& p, cudaStream_t st) {
     template cudaError_t graf::run_loss_m<M>(const graf::AfParams&, cudaStream_t);     \
     template cudaError_t graf::run_backward_m<M>(const graf::AfParams&, cudaStream_t); \
     template cudaError_t graf::run_fused_m<M>(const graf::AfParams&, cudaStream_t);    \
-    template cudaError_t graf::run_spectral_m<M>(const graf::SpecParams&, cudaStream_t);
+    template cudaError_t graf::run_spectral_m<M>(const graf::SpecParams&, cudaStream_t);   \
+    template cudaError_t graf::run_composite_m<M>(const graf::CompParams&, cudaStream_t);

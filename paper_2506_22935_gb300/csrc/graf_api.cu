@@ -359,6 +359,33 @@ graf_status_t graf_spectral_variance(const void* x, graf_input_t kind, int32_t B
     return cuda_status(graf::run_spectral(q, static_cast<cudaStream_t>(stream)));
 }
 
+graf_status_t graf_composite_terms(const void* x, graf_input_t kind, int32_t B, int32_t N, float gamma,
+                                   float eps, float w_width, float w_const, float* out8, float* terms_out,
+                                   graf_c32* grad_s, float* grad_phi, int32_t accumulate, void* stream) {
+    if (!x || (kind != GRAF_IN_COMPLEX && kind != GRAF_IN_PHASE)) return GRAF_ERR_INVALID_ARG;
+    if (B < 1 || B > (1 << 20) || N < 1 || 2 * N > GRAF_M_MAX) return GRAF_ERR_INVALID_ARG;
+    if (!(gamma > 0.0f) || !(eps >= 0.0f) || !(w_width == w_width) || !(w_const == w_const))
+        return GRAF_ERR_INVALID_ARG;
+    if (grad_phi && kind != GRAF_IN_PHASE) return GRAF_ERR_INVALID_ARG;
+    int M = GRAF_M_MIN;
+    while (M < 2 * N) M *= 2;
+    graf::CompParams q{};
+    q.x = x;
+    q.kind = kind == GRAF_IN_PHASE ? 1 : 0;
+    q.B = B;
+    q.N = N;
+    q.gamma = gamma;
+    q.eps = eps;
+    q.w_width = w_width;
+    q.w_const = w_const;
+    q.out8 = out8;
+    q.terms = terms_out;
+    q.grad_s = reinterpret_cast<float2*>(grad_s);
+    q.grad_phi = grad_phi;
+    q.accumulate = accumulate ? 1 : 0;
+    return cuda_status(graf::run_composite(q, M, static_cast<cudaStream_t>(stream)));
+}
+
 // ------------------------------------------------------------ periodic AF
 static Mode periodic_mode(int32_t sign) { return Mode{1, sign > 0 ? 1 : 0}; }
 

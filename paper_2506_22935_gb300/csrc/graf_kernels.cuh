@@ -85,6 +85,22 @@ struct SpecParams {
     int accumulate;
 };
 cudaError_t run_spectral(const SpecParams& q, cudaStream_t st);
+
+// Two terms of the composite loss (Sec. 5.1, Eq. 22) from the zero-Doppler
+// autocorrelation and the modulus: W = sum_k |k| sigmoid(gamma (a2[k] - 1/2))
+// and V = var(|s|), one row slot per waveform on a row of M = nextpow2(2N).
+struct CompParams {
+    const void* x;
+    int kind, B, N;
+    float gamma, eps, w_width, w_const;
+    float* out8;     // nullable: out8[b][0] += w_width W + w_const V
+    float* terms;    // nullable: [B][2] = {W, V}
+    float2* grad_s;  // nullable: += or = 2 dL/ds*
+    float* grad_phi; // nullable: += or = dL/dphi
+    int accumulate;
+};
+cudaError_t run_composite(const CompParams& q, int M, cudaStream_t st);
+template <int M> cudaError_t run_composite_m(const CompParams& q, cudaStream_t st);
 template <int M> cudaError_t run_spectral_m(const SpecParams& q, cudaStream_t st);
 
 // Shared-memory length of the signal and of each gradient accumulator.

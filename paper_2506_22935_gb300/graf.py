@@ -84,6 +84,8 @@ _SIGS = {
                                               _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "graf_spectral_variance": (ctypes.c_int, [_vp, ctypes.c_int, _i32, _i32, ctypes.c_float, _vp, _vp, _vp, _vp,
                                               _i32, _vp]),
+    "graf_composite_terms": (ctypes.c_int, [_vp, ctypes.c_int, _i32, _i32, ctypes.c_float, ctypes.c_float,
+                                            ctypes.c_float, ctypes.c_float, _vp, _vp, _vp, _vp, _i32, _vp]),
     "graf_batch_plan_create": (ctypes.c_int, [_i32, _vp, _vp, _vp, _vp, _i32, ctypes.c_int, _vp]),
     "graf_batch_plan_destroy": (ctypes.c_int, [_vp]),
     "graf_batch_workspace_bytes": (_sz, [_vp]),
@@ -152,6 +154,26 @@ def spectral_variance(x, weight: float = 1.0):
     _check(graf_spectral_variance(x.data_ptr(), kind, B, N, float(weight), None, sv.data_ptr(), gs, gp, 0,
                                   _stream(x.device)), "graf_spectral_variance")
     return sv, grad
+
+
+def graf_composite_terms(x, kind, B, N, gamma, eps, w_width, w_const, out8, terms_out, grad_s, grad_phi,
+                         accumulate, stream) -> int:
+    return load().graf_composite_terms(x, kind, B, N, gamma, eps, w_width, w_const, out8, terms_out, grad_s,
+                                       grad_phi, accumulate, stream)
+
+
+def composite_terms(x, gamma: float = 50.0, eps: float = 0.0, w_width: float = 1.0, w_const: float = 0.0):
+    """({W, V} [B, 2], gradient of w_width W + w_const V): the differentiable
+    mainlobe width (Sec. 5.1) and var(|s|) (Eq. 22)."""
+    torch = _torch()
+    x, kind, B, N = _prep(x)
+    terms = torch.empty((B, 2), dtype=torch.float32, device=x.device)
+    grad = torch.empty((B, N), dtype=torch.float32 if kind == GRAF_IN_PHASE else torch.complex64, device=x.device)
+    gs = grad.data_ptr() if kind == GRAF_IN_COMPLEX else None
+    gp = grad.data_ptr() if kind == GRAF_IN_PHASE else None
+    _check(graf_composite_terms(x.data_ptr(), kind, B, N, float(gamma), float(eps), float(w_width), float(w_const),
+                                None, terms.data_ptr(), gs, gp, 0, _stream(x.device)), "graf_composite_terms")
+    return terms, grad
 
 
 def graf_paf_forward(x, kind, B, N, sign, normalise, chi_out, stream) -> int:
