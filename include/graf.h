@@ -221,6 +221,25 @@ GRAF_API graf_status_t graf_batch_plan_create(int32_t B, const int32_t* N_host, 
                                               int32_t losses_per_waveform, graf_input_t kind,
                                               graf_batch_plan_t* plan);
 
+/*
+ * graf_batch_plan_create_scenarios - a plan of S entries that score B_src
+ * source waveforms, each under several windows and loss weights (the
+ * multi-scenario loss of Eq. 24, L_j = sum over the entries b of source j of
+ * lambda_b L_b, lambda_b passed as dL[b] to graf_batch_loss_backward).
+ *   src_host   host int32[S], 0 <= src_b < B_src: the source of entry b
+ *   N_src_host host int32[B_src], 1 <= N_j
+ *   M_host, w_host as graf_batch_plan_create, per entry; l_host host
+ *   graf_loss_t[S], per entry.
+ * graf_batch_loss_backward then reads the packed sources (source j at
+ * [off_j, off_j + N_j), off_j = N_0 + ... + N_{j-1}), writes out8 per entry
+ * ([S][GRAF_LOSS_OUT]) and grad_phi per SOURCE (packed like the input):
+ * the sum over its entries, in ascending entry order, of dL_b dL_b/dphi.
+ */
+GRAF_API graf_status_t graf_batch_plan_create_scenarios(int32_t S, const int32_t* src_host, int32_t B_src,
+                                                        const int32_t* N_src_host, const int32_t* M_host,
+                                                        const graf_window_t* w_host, const graf_loss_t* l_host,
+                                                        graf_input_t kind, graf_batch_plan_t* plan);
+
 GRAF_API graf_status_t graf_batch_plan_destroy(graf_batch_plan_t plan);
 
 /* Device workspace for graf_batch_loss_backward (changes after autotuning). */

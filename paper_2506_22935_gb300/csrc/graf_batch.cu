@@ -54,6 +54,16 @@ struct graf_batch_plan_s {
     long long total_gpart = 0; // float2 count of all gradient partials
     int max_N = 0;
     size_t ws_rec = 0, ws_scale = 0, ws_csum = 0, ws_gpart = 0, ws_usum = 0;
+    // multi-scenario plans (Eq. 24): entry b scores source waveform src[b];
+    // entry gradients go to a scratch area and are summed per source
+    bool scenarios = false;
+    int B_src = 0;
+    std::vector<int> src;
+    std::vector<long long> src_off;   // [B_src + 1] packed offsets of the sources
+    int* d_src_entries = nullptr;     // entries grouped by source, ascending
+    int* d_src_first = nullptr;       // [B_src + 1] CSR into d_src_entries
+    long long* d_src_off = nullptr;   // [B_src + 1]
+    size_t ws_scratch = 0;            // float per entry sample
 };
 
 namespace {
@@ -101,6 +111,7 @@ graf_status_t layout(graf_batch_plan_s* P) {
     P->ws_csum = align256((size_t)rec * sizeof(float));
     P->ws_gpart = align256((size_t)gp * sizeof(float2));
     P->ws_usum = align256((size_t)2 * P->B * sizeof(double));
+    P->ws_scratch = P->scenarios ? align256((size_t)P->total_x * sizeof(float)) : 0;
     // device copies
     cudaError_t e = cudaMemcpy(P->d_waves, P->waves.data(), sizeof(WaveDesc) * P->B, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return GRAF_ERR_CUDA;
@@ -151,6 +162,25 @@ graf_status_t run_rows(const graf_batch_plan_s* P, const Bucket& bk, int bi, con
     return e == cudaSuccess ? GRAF_OK : GRAF_ERR_CUDA;
 }
 
+// Multi-scenario sum (Eq. 24): grad[j][n] = sum over the entries b of source
+// j, in ascending order, of the entry gradient at waves[b].out_off + n (each
+// already scaled by its weight dL[b] = lambda_b).  One thread per sample.
+__global__ void scenario_sum_kernel(const WaveDesc* waves, const int* entries, const int* first,
+                                    const long long* src_off, int B_src, const float* scratch, float* grad) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= src_off[B_src]) return;
+    int lo = 0, hi = B_src - 1;  // source j with src_off[j] <= i < src_off[j+1]
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (src_off[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    const long long n = i - src_off[lo];
+    float s = 0.0f;
+    for (int e = first[lo]; e < first[lo + 1]; ++e) s += scratch[waves[entries[e]].out_off + n];
+    grad[i] = s;
+}
+
 // The whole step for all buckets on one stream.
 graf_status_t batch_step(const graf_batch_plan_s* P, const float* x, float* out8, const float* dL,
                          float* grad_phi, void* ws, cudaStream_t st) {
@@ -172,8 +202,18 @@ graf_status_t batch_step(const graf_batch_plan_s* P, const float* x, float* out8
         for (size_t i = 0; i < P->buckets.size(); ++i)
             if (!P->buckets[i].fused && (s = run_rows(P, P->buckets[i], (int)i, x, ws, out8, 2, st)) != GRAF_OK)
                 return s;
-    if (graf::run_grad_reduce(q, dL, nullptr, grad_phi, st) != cudaSuccess) return GRAF_ERR_CUDA;
-    return GRAF_OK;
+    if (!P->scenarios) {
+        if (graf::run_grad_reduce(q, dL, nullptr, grad_phi, st) != cudaSuccess) return GRAF_ERR_CUDA;
+        return GRAF_OK;
+    }
+    float* scratch = reinterpret_cast<float*>(static_cast<unsigned char*>(ws) + P->ws_rec + P->ws_scale +
+                                              P->ws_csum + P->ws_gpart + P->ws_usum);
+    if (graf::run_grad_reduce(q, dL, nullptr, scratch, st) != cudaSuccess) return GRAF_ERR_CUDA;
+    const long long n_src = P->src_off[P->B_src];
+    const unsigned grid = (unsigned)((n_src + 255) / 256);
+    scenario_sum_kernel<<<grid, 256, 0, st>>>(P->d_waves, P->d_src_entries, P->d_src_first, P->d_src_off,
+                                              P->B_src, scratch, grad_phi);
+    return cudaGetLastError() == cudaSuccess ? GRAF_OK : GRAF_ERR_CUDA;
 }
 
 graf_status_t validate_window(int N, int M, const graf_window_t& w) {
@@ -188,23 +228,45 @@ graf_status_t validate_window(int N, int M, const graf_window_t& w) {
 
 extern "C" {
 
-graf_status_t graf_batch_plan_create(int32_t B, const int32_t* N_host, const int32_t* M_host,
-                                     const graf_window_t* w_host, const graf_loss_t* l_host,
-                                     int32_t losses_per_waveform, graf_input_t kind,
-                                     graf_batch_plan_t* plan) {
+// Plan entries b = 0..B-1.  Plain plans: entry b is waveform b of length
+// N_host[b].  Multi-scenario plans (src_host set): entry b scores source
+// waveform src_host[b] (length N_src_host[src]) with its own M, window and loss.
+static graf_status_t create_plan(int32_t B, const int32_t* N_host, const int32_t* M_host,
+                                 const graf_window_t* w_host, const graf_loss_t* l_host,
+                                 int32_t losses_per_waveform, graf_input_t kind, const int32_t* src_host,
+                                 int32_t B_src, const int32_t* N_src_host, graf_batch_plan_t* plan) {
     if (!plan) return GRAF_ERR_INVALID_ARG;
     *plan = nullptr;
-    if (B < 1 || B > (1 << 20) || !N_host || !l_host) return GRAF_ERR_INVALID_ARG;
+    if (B < 1 || B > (1 << 20) || !l_host) return GRAF_ERR_INVALID_ARG;
+    if (src_host ? (!N_src_host || B_src < 1 || B_src > (1 << 20)) : !N_host) return GRAF_ERR_INVALID_ARG;
     if (kind != GRAF_IN_PHASE) return GRAF_ERR_UNSUPPORTED;
     graf_batch_plan_s* P = new (std::nothrow) graf_batch_plan_s();
     if (!P) return GRAF_ERR_NOMEM;
     P->B = B;
     P->kind = kind;
     P->waves.resize(B);
+    if (src_host) {
+        P->scenarios = true;
+        P->B_src = B_src;
+        P->src.assign(src_host, src_host + B);
+        P->src_off.assign((size_t)B_src + 1, 0);
+        for (int j = 0; j < B_src; ++j) {
+            if (N_src_host[j] < 1) {
+                delete P;
+                return GRAF_ERR_INVALID_ARG;
+            }
+            P->src_off[j + 1] = P->src_off[j] + N_src_host[j];
+        }
+        for (int b = 0; b < B; ++b)
+            if (src_host[b] < 0 || src_host[b] >= B_src) {
+                delete P;
+                return GRAF_ERR_INVALID_ARG;
+            }
+    }
     long long off = 0;
     std::vector<int> Ms;
     for (int b = 0; b < B; ++b) {
-        const int N = N_host[b];
+        const int N = src_host ? N_src_host[src_host[b]] : N_host[b];
         const int M = M_host ? M_host[b] : next_pow2(2 * N);
         const graf_loss_t& l = l_host[losses_per_waveform ? b : 0];
         if (N < 1 || M < GRAF_M_MIN || M > GRAF_M_MAX || (M & (M - 1)) || N > M || !(l.beta > 0.0f) ||
@@ -221,8 +283,8 @@ graf_status_t graf_batch_plan_create(int32_t B, const int32_t* N_host, const int
         }
         WaveDesc& d = P->waves[b];
         std::memset(&d, 0, sizeof(d));
-        d.x_off = off;
-        d.out_off = off;
+        d.x_off = src_host ? P->src_off[src_host[b]] : off;
+        d.out_off = off;  // scenario plans: the entry's gradient in the scratch area
         off += N;
         d.N = N;
         d.M = M;
@@ -281,8 +343,47 @@ graf_status_t graf_batch_plan_create(int32_t B, const int32_t* N_host, const int
         graf_batch_plan_destroy(P);
         return s;
     }
+    if (P->scenarios) {
+        std::vector<int> first((size_t)B_src + 1, 0), entries;
+        for (int j = 0; j < B_src; ++j) {
+            first[j] = (int)entries.size();
+            for (int b = 0; b < B; ++b)
+                if (P->src[b] == j) entries.push_back(b);
+        }
+        first[B_src] = (int)entries.size();
+        if (cudaMalloc(&P->d_src_entries, sizeof(int) * entries.size()) != cudaSuccess ||
+            cudaMalloc(&P->d_src_first, sizeof(int) * first.size()) != cudaSuccess ||
+            cudaMalloc(&P->d_src_off, sizeof(long long) * P->src_off.size()) != cudaSuccess) {
+            graf_batch_plan_destroy(P);
+            return GRAF_ERR_NOMEM;
+        }
+        if (cudaMemcpy(P->d_src_entries, entries.data(), sizeof(int) * entries.size(), cudaMemcpyHostToDevice) !=
+                cudaSuccess ||
+            cudaMemcpy(P->d_src_first, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice) !=
+                cudaSuccess ||
+            cudaMemcpy(P->d_src_off, P->src_off.data(), sizeof(long long) * P->src_off.size(),
+                       cudaMemcpyHostToDevice) != cudaSuccess) {
+            graf_batch_plan_destroy(P);
+            return GRAF_ERR_CUDA;
+        }
+    }
     *plan = P;
     return GRAF_OK;
+}
+
+graf_status_t graf_batch_plan_create(int32_t B, const int32_t* N_host, const int32_t* M_host,
+                                     const graf_window_t* w_host, const graf_loss_t* l_host,
+                                     int32_t losses_per_waveform, graf_input_t kind,
+                                     graf_batch_plan_t* plan) {
+    return create_plan(B, N_host, M_host, w_host, l_host, losses_per_waveform, kind, nullptr, 0, nullptr, plan);
+}
+
+graf_status_t graf_batch_plan_create_scenarios(int32_t S, const int32_t* src_host, int32_t B_src,
+                                               const int32_t* N_src_host, const int32_t* M_host,
+                                               const graf_window_t* w_host, const graf_loss_t* l_host,
+                                               graf_input_t kind, graf_batch_plan_t* plan) {
+    if (!src_host) return GRAF_ERR_INVALID_ARG;
+    return create_plan(S, nullptr, M_host, w_host, l_host, 1, kind, src_host, B_src, N_src_host, plan);
 }
 
 graf_status_t graf_batch_plan_destroy(graf_batch_plan_t P) {
@@ -291,13 +392,16 @@ graf_status_t graf_batch_plan_destroy(graf_batch_plan_t P) {
         if (bk.d_items) cudaFree(bk.d_items);
     if (P->d_waves) cudaFree(P->d_waves);
     if (P->d_counters) cudaFree(P->d_counters);
+    if (P->d_src_entries) cudaFree(P->d_src_entries);
+    if (P->d_src_first) cudaFree(P->d_src_first);
+    if (P->d_src_off) cudaFree(P->d_src_off);
     delete P;
     return GRAF_OK;
 }
 
 size_t graf_batch_workspace_bytes(graf_batch_plan_t P) {
     if (!P) return 0;
-    return P->ws_rec + P->ws_scale + P->ws_csum + P->ws_gpart + P->ws_usum;
+    return P->ws_rec + P->ws_scale + P->ws_csum + P->ws_gpart + P->ws_usum + P->ws_scratch;
 }
 
 graf_status_t graf_batch_plan_info(graf_batch_plan_t P, int32_t* n_buckets, int32_t* M_out,

@@ -87,6 +87,7 @@ _SIGS = {
     "graf_composite_terms": (ctypes.c_int, [_vp, ctypes.c_int, _i32, _i32, ctypes.c_float, ctypes.c_float,
                                             ctypes.c_float, ctypes.c_float, _vp, _vp, _vp, _vp, _i32, _vp]),
     "graf_batch_plan_create": (ctypes.c_int, [_i32, _vp, _vp, _vp, _vp, _i32, ctypes.c_int, _vp]),
+    "graf_batch_plan_create_scenarios": (ctypes.c_int, [_i32, _vp, _i32, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
     "graf_batch_plan_destroy": (ctypes.c_int, [_vp]),
     "graf_batch_workspace_bytes": (_sz, [_vp]),
     "graf_batch_plan_info": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _i32]),
@@ -239,6 +240,10 @@ def graf_batch_workspace_bytes(plan) -> int:
 
 def graf_batch_plan_info(plan, n_buckets, M_out, rpt_out, items_out, fused_out, capacity) -> int:
     return load().graf_batch_plan_info(plan, n_buckets, M_out, rpt_out, items_out, fused_out, capacity)
+
+
+def graf_batch_plan_create_scenarios(S, src, B_src, N_src, M, w, l, kind, plan) -> int:
+    return load().graf_batch_plan_create_scenarios(S, src, B_src, N_src, M, w, l, kind, plan)
 
 
 def graf_batch_loss_backward(plan, phi, out8, dL, grad_phi, workspace, workspace_bytes, stream) -> int:
@@ -511,6 +516,34 @@ class BatchPlan:
         self.offsets = np.concatenate([[0], np.cumsum(self.N.astype(np.int64))])
         self.device = device or torch.device("cuda", torch.cuda.current_device())
         self._ws = None
+
+    @classmethod
+    def scenarios(cls, N_src, src, windows, losses, M=None, device=None) -> "BatchPlan":
+        """A multi-scenario plan (Eq. 24): entry b scores source src[b] of
+        lengths N_src with windows[b] and losses[b]; loss_backward then takes
+        the packed sources, the per-entry weights lambda as dL, and returns
+        the per-source summed gradient."""
+        torch = _torch()
+        import numpy as np
+        self = cls.__new__(cls)
+        src = np.ascontiguousarray(np.asarray(src, dtype=np.int32))
+        Ns = np.ascontiguousarray(np.asarray(N_src, dtype=np.int32))
+        S = len(src)
+        self.B = S
+        self.N = Ns[src]
+        Mc = None if M is None else np.ascontiguousarray(np.asarray(M, dtype=np.int32))
+        wc = (graf_window_t * S)(*[w.c() for w in windows])
+        lc = (graf_loss_t * S)(*[l.c() for l in losses])
+        h = ctypes.c_void_p()
+        _check(graf_batch_plan_create_scenarios(S, src.ctypes.data, len(Ns), Ns.ctypes.data,
+                                                None if Mc is None else Mc.ctypes.data, ctypes.addressof(wc),
+                                                ctypes.addressof(lc), GRAF_IN_PHASE, ctypes.byref(h)),
+               "graf_batch_plan_create_scenarios")
+        self.handle = h
+        self.offsets = np.concatenate([[0], np.cumsum(Ns.astype(np.int64))])  # of the sources
+        self.device = device or torch.device("cuda", torch.cuda.current_device())
+        self._ws = None
+        return self
 
     def workspace(self):
         torch = _torch()
