@@ -74,9 +74,10 @@ def _load():
             lib.orc_ploss.argtypes = [_dp, _i64, _c, _ip, _d, _d, _d, _d, _dp]
             lib.orc_pgrad.argtypes = [_dp, _i64, _c, _ip, _d, _d, _d, _d, _dp, _dp, _dp]
             lib.orc_pfd_grad_phi.argtypes = [_dp, _i64, _c, _ip, _d, _d, _d, _d, _d, _dp]
+            lib.orc_match.argtypes = [_dp, _i64, _i64, _ip, _dp, _d, _d, _dp, _dp, _dp, _c]
             for f in ("orc_af_complex", "orc_af_ahat", "orc_af_cells", "orc_loss", "orc_grad",
                       "orc_fd_grad_phi", "orc_fd_grad_s", "orc_paf_complex", "orc_ploss", "orc_pgrad",
-                      "orc_pfd_grad_phi"):
+                      "orc_pfd_grad_phi", "orc_match"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -319,3 +320,18 @@ def optimize_experiment(phi0, window, w_psl, w_isl, beta, eps, spectral_weight, 
         hist.append(out[0] + spectral_weight * sv)
         phi, m, v = adam_update(phi, m, v, gphi + spectral_weight * gsv, t, lr, beta1, beta2, adam_eps)
     return phi, np.array(hist)
+
+
+def match(s, M, window, target, weight=1.0, eps=1e-12, nthreads=None):
+    """(sum (Ahat^2 - target)^2, grad_s, grad_phi) of weight * that sum
+    (L_match of Eq. 22); target [rows][cols] over the window (box ignored)."""
+    s, sv = _s_buf(s)
+    w = _win(window)
+    N = s.shape[0]
+    tg = np.ascontiguousarray(np.asarray(target, dtype=np.float64))
+    gs = np.zeros(N, dtype=np.complex128)
+    gp = np.zeros(N, dtype=np.float64)
+    out = np.zeros(1, dtype=np.float64)
+    _check(_load().orc_match(_ptr(sv), N, M, w.ctypes.data_as(_ip), _ptr(tg), weight, eps,
+                             _ptr(gs.view(np.float64)), _ptr(gp), _ptr(out), _threads(nthreads)), "match")
+    return out[0], gs, gp

@@ -615,3 +615,62 @@ int orc_pfd_grad_phi(const double* phi, int64_t N, int sign, const int64_t win6[
     free(s);
     return ORC_OK;
 }
+
+/* ============================================================ match term */
+/* L_match = weight * sum_window (Ahat^2[k,m] - target[k,m])^2 (Sec. 5.2,
+ * Eq. 22, on Ahat^2 = (|X|^2 + eps) / E^2), target laid out [rows][cols] over
+ * the window.  Gradient by the same direct adjoint as orc_grad with the cell
+ * adjoint dL/dAhat^2 = 2 weight (Ahat^2 - target) and the energy term
+ * dL/dE = -(2/E) sum dL/dAhat^2 Ahat^2.  out[0] = the unweighted sum. */
+int orc_match(const double* s, int64_t N, int64_t M, const int64_t win6[6], const double* target,
+              double weight, double eps, double* grad_s, double* grad_phi, double out[1], int nthreads) {
+    orc_window w = {win6[0], win6[1], win6[2], win6[3], -1, -1};
+    if (check_window(N, M, &w) || eps < 0.0) return ORC_EINVAL;
+    int64_t rows = w.k_hi - w.k_lo + 1, ncols = w.m_hi - w.m_lo + 1, cells = rows * ncols;
+    double* X = (double*)malloc(sizeof(double) * 2 * (size_t)cells);
+    double* W = make_w_table(M);
+    if (!X || !W) { free(X); free(W); return ORC_ENOMEM; }
+    int st = orc_af_complex(s, N, M, w.k_lo, w.k_hi, w.m_lo, w.m_hi, X, nthreads);
+    if (st) { free(X); free(W); return st; }
+    double E = orc_energy(s, N);
+    double loss = 0.0, de = 0.0;
+    for (int64_t i = 0; i < cells; ++i) {
+        double* x = X + 2 * i;
+        double a2 = (x[0] * x[0] + x[1] * x[1] + eps) / (E * E);
+        double d = a2 - target[i];
+        loss += d * d;
+        double dl = 2.0 * weight * d;
+        de += dl * a2;
+        x[0] *= dl / (E * E);
+        x[1] *= dl / (E * E);
+    }
+    out[0] = loss;
+    if (grad_s || grad_phi) {
+        nthreads = clamp_threads(nthreads, rows);
+        double* gparts = (double*)calloc((size_t)nthreads * 2 * (size_t)N, sizeof(double));
+        if (!gparts) { free(X); free(W); return ORC_ENOMEM; }
+        adj_job jobs[256];
+        pthread_t th[256];
+        for (int t = 0; t < nthreads; ++t) {
+            jobs[t] = (adj_job){s, N, M, W, w, X, rows * t / nthreads, rows * (t + 1) / nthreads,
+                                gparts + (size_t)t * 2 * (size_t)N};
+            if (t > 0) pthread_create(&th[t], NULL, adj_worker, &jobs[t]);
+        }
+        adj_worker(&jobs[0]);
+        for (int t = 1; t < nthreads; ++t) pthread_join(th[t], NULL);
+        double dlde = -(2.0 / E) * de;
+        for (int64_t n = 0; n < N; ++n) {
+            double gr = dlde * s[2 * n], gi = dlde * s[2 * n + 1];
+            for (int t = 0; t < nthreads; ++t) {
+                gr += gparts[(size_t)t * 2 * (size_t)N + 2 * n];
+                gi += gparts[(size_t)t * 2 * (size_t)N + 2 * n + 1];
+            }
+            if (grad_s) { grad_s[2 * n] = 2.0 * gr; grad_s[2 * n + 1] = 2.0 * gi; }
+            if (grad_phi) grad_phi[n] = 2.0 * (gi * s[2 * n] - gr * s[2 * n + 1]);
+        }
+        free(gparts);
+    }
+    free(X);
+    free(W);
+    return ORC_OK;
+}
