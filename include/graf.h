@@ -412,6 +412,27 @@ GRAF_API graf_status_t graf_composite_terms(const void* x, graf_input_t kind, in
                                             float* terms_out, graf_c32* grad_s, float* grad_phi,
                                             int32_t accumulate, void* stream);
 
+/*
+ * graf_af_match - the target-matching term of the composite loss (Sec. 5.2,
+ * Eq. 22), L_match = weight * sum over the window of (Ahat^2[k,m] -
+ * target[k,m])^2 with Ahat^2 = (|X|^2 + eps) / E^2 = chi / chi(0,0), and its
+ * gradient.
+ *   target   device float[B][k_hi-k_lo+1][m_hi-m_lo+1], the designer's
+ *            reference surface in the layout of graf_af_forward's output,
+ *            in units of Ahat^2.
+ *   loss_out device float[B] (nullable): sum (Ahat^2 - target)^2, unweighted;
+ *   out8     device float[B][8] (nullable): out8[b][0] += weight * that sum;
+ *   grad_s / grad_phi as graf_af_backward, for weight * the sum, added to the
+ *   arrays' contents if accumulate != 0, else written (both may be NULL).
+ * Workspace from graf_af_match_workspace_bytes (256-byte aligned).  Errors
+ * as graf_af_backward.
+ */
+GRAF_API size_t graf_af_match_workspace_bytes(int32_t B, int32_t N, int32_t M, graf_window_t w);
+GRAF_API graf_status_t graf_af_match(const void* x, graf_input_t kind, int32_t B, int32_t N, int32_t M,
+                                     graf_window_t w, const float* target, float weight, float eps,
+                                     float* loss_out, float* out8, graf_c32* grad_s, float* grad_phi,
+                                     int32_t accumulate, void* workspace, size_t workspace_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

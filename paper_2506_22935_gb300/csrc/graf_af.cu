@@ -164,7 +164,8 @@ __global__ void grad_phi_kernel(AfParams p, const float* dL, float* grad_phi) {
     if (p.phase_only) im = g1.x + (g2.y * s.x - g2.x * s.y);
     else im = (g1.y + g2.y) * s.x - (g1.x + g2.x) * s.y;
     // +j periodic AF: the kernels saw conj(s) = exp(-j phi), so dL/dphi flips sign
-    grad_phi[wv.out_off + n] = wv.pconj ? -scale * im : scale * im;
+    const float val = wv.pconj ? -scale * im : scale * im;
+    grad_phi[wv.out_off + n] = p.grad_acc ? grad_phi[wv.out_off + n] + val : val;
 }
 
 // Per waveform, in FP64: U = sum_k w_b(k) (C[k] + eps) over the transformed
@@ -239,10 +240,10 @@ __global__ void grad_s_kernel(AfParams p, const float* dL, float2* grad_s, float
     sum_partials(p, wv, b, n, g1, g2, &cs);
     const float2 g = cadd(g1, g2);
     const float2 s = signal_at(wv, n);
-    const float* sv = p.saved8 + (size_t)b * 8;
+    const float psl_soft = p.saved8 ? p.saved8[(size_t)b * 8 + 1] : 0.0f;
     const double E = p.usum[2 * b + 1];
     const float bl2 = wv.beta * 1.4426950408889634f;
-    const float p0 = ex2a(-(sv[1] * bl2));
+    const float p0 = ex2a(-(psl_soft * bl2));
     const double Ap = (double)fmaf(wv.w_psl, p0, wv.w_isl);
     double corr = 0.0;
     for (int k = wv.r_lo; k <= wv.r_hi; ++k) {
@@ -260,7 +261,7 @@ __global__ void grad_s_kernel(AfParams p, const float* dL, float2* grad_s, float
     if (wv.k_lo <= 0 && wv.k_hi >= 0 && wv.m_lo <= 0 && wv.m_hi >= 0) {
         const int w00 = (wv.k_ml >= 0 && wv.m_ml >= 0) ? 0 : 1;
         const double a00 = 1.0 + (double)wv.eps / (E * E);
-        const double pr = exp((double)wv.beta * (a00 - (double)sv[1]));
+        const double pr = exp((double)wv.beta * (a00 - (double)psl_soft));
         c00 = ((w00 - base_weight(wv, 0)) * Ap + (w00 > 0 ? w00 * (double)wv.w_psl * (pr - (double)p0) : 0.0)) /
               (E * E);
     }
@@ -270,9 +271,24 @@ __global__ void grad_s_kernel(AfParams p, const float* dL, float2* grad_s, float
     // conj(s); the gradient with respect to s is its conjugate, and dL/dphi
     // flips sign
     const float cj = wv.pconj ? -1.0f : 1.0f;
-    grad_s[wv.out_off + n] =
-        make_float2((float)(scale * (g.x + coef * s.x)), cj * (float)(scale * (g.y + coef * s.y)));
-    if (grad_phi) grad_phi[wv.out_off + n] = cj * (float)(scale * ((double)g.y * s.x - (double)g.x * s.y));
+    float2 gv = make_float2((float)(scale * (g.x + coef * s.x)), cj * (float)(scale * (g.y + coef * s.y)));
+    if (p.grad_acc) gv = cadd(gv, grad_s[wv.out_off + n]);
+    grad_s[wv.out_off + n] = gv;
+    if (grad_phi) {
+        const float pv = cj * (float)(scale * ((double)g.y * s.x - (double)g.x * s.y));
+        grad_phi[wv.out_off + n] = p.grad_acc ? grad_phi[wv.out_off + n] + pv : pv;
+    }
+}
+
+// Per-waveform match loss: the tile partials summed in order.
+__global__ void match_finalize_kernel(AfParams p, float* loss_out) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= p.B) return;
+    const Wave wv = wave_of(p, b);
+    double s = 0.0;
+    for (int i = 0; i < wv.tiles; ++i) s += p.mpart[wv.rec_off + i];
+    if (loss_out) loss_out[b] = (float)s;
+    if (p.out8) p.out8[(size_t)b * 8] += (float)((double)p.match_w * s);
 }
 
 #define GRAF_DISPATCH_M(FN, M, ...)                      \
@@ -410,6 +426,15 @@ cudaError_t run_backward(const AfParams& p, const float* dL, float2* grad_s, flo
 }
 
 cudaError_t run_fused(const AfParams& p, cudaStream_t st) { GRAF_DISPATCH_M(run_fused_m, p.M, p, st) }
+
+static cudaError_t run_match_rows(const AfParams& p, cudaStream_t st) { GRAF_DISPATCH_M(run_match_m, p.M, p, st) }
+
+cudaError_t run_match(const AfParams& p, float* loss_out, cudaStream_t st) {
+    cudaError_t e = run_match_rows(p, st);
+    if (e != cudaSuccess) return e;
+    match_finalize_kernel<<<(p.B + 127) / 128, 128, 0, st>>>(p, loss_out);
+    return cudaGetLastError();
+}
 
 cudaError_t run_finalize(const AfParams& p, cudaStream_t st) {
     const int wpb = 4;

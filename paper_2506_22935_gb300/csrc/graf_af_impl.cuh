@@ -509,6 +509,110 @@ __global__ void __launch_bounds__(kThreads, 1) af_backward_kernel(AfParams p) {
     for_each_item(p, [&](int b, int tile) { backward_item<M, HALF>(p, b, tile, smem); });
 }
 
+// ---------------------------------------------------------- match to a target
+// L = lambda_1 sum_window (Ahat^2[k,m] - target[k,m])^2 (L_match of Eq. 22,
+// on the energy-normalised chi / chi(0,0) of Eq. 17).  Its cell adjoint is
+// local: c = 2 lambda_1 (Ahat^2 - target) / E^2 summed over the cell and its
+// mirror, so one pass per row recomputes X, forms c X, takes the adjoint DFT
+// and scatters (as the backward kernel), and adds the row's loss partial.
+template <int M, bool HALF>
+__device__ __forceinline__ void match_item(const AfParams& p, int b, int tile, unsigned char* smem) {
+    using P = RowPlan<M>;
+    constexpr int SLOTS = kThreads / P::TPR;
+    __shared__ Wave s_wave;
+    if (threadIdx.x == 0) s_wave = wave_of(p, b);
+    __syncthreads();
+    const Wave& wv = s_wave;
+    float2* s_sm = reinterpret_cast<float2*>(smem);
+    float2* bufs = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(sig_len(p)));
+    float2* acc_all = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(sig_len(p)) + row_buffer_bytes<M>());
+    float* red = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(acc_all) +
+                                          (((size_t)p.acc_copies * sig_len(p) * sizeof(float2) + 255) & ~(size_t)255));
+    const int tid = threadIdx.x, slot = tid / P::TPR, t = tid % P::TPR;
+    for (int i = tid; i < p.acc_copies * wv.sN; i += kThreads) acc_all[i] = make_float2(0.0f, 0.0f);
+    const float E = load_signal(wv, s_sm, red);  // includes __syncthreads
+    const float invE2 = 1.0f / (E * E);
+    const float eps_n = wv.eps * invE2;
+    const float c2 = 2.0f * p.match_w * invE2;
+    float2* buf = bufs + (size_t)slot * (P::SPLIT ? P::SMEM_ROW / 2 : P::SMEM_ROW);
+    const ColMasks cm = col_masks<M>(wv, t);
+    const int turns = SLOTS / p.acc_copies;
+    const int my_turn = slot / p.acc_copies;
+    float2* acc = acc_all + (size_t)(slot % p.acc_copies) * wv.sN;
+    float* acc_r = reinterpret_cast<float*>(acc_all) + (size_t)(slot % p.acc_copies) * wv.sN;
+    const int ncols = wv.m_hi - wv.m_lo + 1;
+    const float* tgt = p.target + (size_t)b * (wv.k_hi - wv.k_lo + 1) * ncols;
+
+    const int row0 = wv.r_lo + tile * wv.rows_per_tile;
+    const int row_end = min(row0 + wv.rows_per_tile, wv.r_hi + 1);
+    const int iters = max(0, row_end - row0 + SLOTS - 1) / SLOTS;
+    float msum = 0.0f, csum = 0.0f;
+    float2 v[P::VALS];
+    for (int it = 0; it < iters; ++it) {
+        const int k = row0 + slot + it * SLOTS;
+        const bool valid = k < row_end;
+        // row 0 is R[0,n] = |s[n]|^2: its loss counts, its phase gradient is 0
+        const bool grad_row = valid && !(p.phase_only && k == 0);
+        build_lag_row<M, HALF>(v, s_sm, wv.N, wv.periodic ? k - wv.N : k, t, valid);
+#pragma unroll 1
+        for (int ph = 0; ph < 2; ++ph) {
+            row_sync<P::TPR>(slot);
+            row_fft<M, false, false, false>(v, buf, t, slot);
+            if (ph == 1) break;
+            const RowMasks rmk = row_masks(wv, cm, k);
+            // row k at tp[m], row -k at tn[-m] (m = -M/2 maps to itself)
+            const float* tp = tgt + (rmk.pos ? (size_t)(k - wv.k_lo) * ncols : 0) - wv.m_lo;
+            const float* tn = tgt + (rmk.neg ? (size_t)(-k - wv.k_lo) * ncols : 0) - wv.m_lo;
+            sfor<0, P::VALS>([&](auto w) {
+                constexpr int W = decltype(w)::value;
+                const int m = doppler_of<M>(t, W);
+                const float2 x = v[w];
+                const float a2 = fmaf(fmaf(x.x, x.x, x.y * x.y), invE2, eps_n);
+                float d = 0.0f;
+                if (valid && mbit<W>(rmk.pos)) {
+                    const float dp = a2 - __ldg(tp + m);
+                    msum = fmaf(dp, dp, msum);
+                    d += dp;
+                }
+                if (valid && mbit<W>(rmk.neg)) {
+                    const float dn = a2 - __ldg(tn + (m == -(M / 2) ? m : -m));
+                    msum = fmaf(dn, dn, msum);
+                    d += dn;
+                }
+                const float c = grad_row ? c2 * d : 0.0f;
+                csum = fmaf(c, a2, csum);
+                v[w] = make_float2(c * x.x, -c * x.y);
+            });
+            if constexpr (P::TPR >= 32) {
+                if (!grad_row) break;  // slot-uniform
+            }
+        }
+        if (p.phase_only)
+            scatter_row_real<M, HALF>(v, acc_r, s_sm, wv.N, wv.periodic ? k - wv.N : k, t, grad_row, slot, turns,
+                                      my_turn);
+        else
+            scatter_row<M, HALF, true>(v, acc, s_sm, wv.N, wv.periodic ? k - wv.N : k, t, grad_row, slot, turns,
+                                       my_turn);
+    }
+    // the tile's loss partial, fixed order
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) msum += __shfl_xor_sync(0xffffffffu, msum, o);
+    if ((tid & 31) == 0) red[64 + (tid >> 5)] = msum;
+    __syncthreads();
+    if (tid == 0) {
+        float s = red[64];
+        for (int w = 1; w < kThreads / 32; ++w) s += red[64 + w];
+        p.mpart[wv.rec_off + tile] = s;
+    }
+    write_grad_partial<M>(p, wv, acc_all, red, csum, tile);
+}
+
+template <int M, bool HALF>
+__global__ void __launch_bounds__(kThreads, 1) af_match_kernel(AfParams p) {
+    extern __shared__ __align__(256) unsigned char smem[];
+    for_each_item(p, [&](int b, int tile) { match_item<M, HALF>(p, b, tile, smem); });
+}
+
 // ---------------------------------------------------------- fused loss + gradient
 // Maximum over the TPR threads of one row slot (slots are contiguous thread
 // ranges: a segment of a warp, one warp, or several warps).
@@ -1106,6 +1210,14 @@ cudaError_t run_backward_m(const AfParams& p, cudaStream_t st) {
 // spills); with N <= M/2 the fused kernel still skips the zero half in the
 // lag product and in the scatter.
 template <int M>
+cudaError_t run_match_m(const AfParams& p, cudaStream_t st) {
+    if (p.acc_copies < 1 || (256 / RowPlan<M>::TPR) % p.acc_copies) return cudaErrorInvalidConfiguration;
+    const size_t smem = backward_smem<M>(sig_len(p), p.acc_copies);
+    if (2 * p.N <= M && !p.periodic) return launch_rows(af_match_kernel<M, true>, smem, p, st);
+    return launch_rows(af_match_kernel<M, false>, smem, p, st);
+}
+
+template <int M>
 cudaError_t run_fused_m(const AfParams& p, cudaStream_t st) {
     if (p.acc_copies < 1 || (256 / RowPlan<M>::TPR) % p.acc_copies) return cudaErrorInvalidConfiguration;
     const size_t smem = backward_smem<M>(sig_len(p), p.acc_copies);
@@ -1121,4 +1233,5 @@ cudaError_t run_fused_m(const AfParams& p, cudaStream_t st) {
     template cudaError_t graf::run_backward_m<M>(const graf::AfParams&, cudaStream_t); \
     template cudaError_t graf::run_fused_m<M>(const graf::AfParams&, cudaStream_t);    \
     template cudaError_t graf::run_spectral_m<M>(const graf::SpecParams&, cudaStream_t);   \
-    template cudaError_t graf::run_composite_m<M>(const graf::CompParams&, cudaStream_t);
+    template cudaError_t graf::run_composite_m<M>(const graf::CompParams&, cudaStream_t);   \
+    template cudaError_t graf::run_match_m<M>(const graf::AfParams&, cudaStream_t);

@@ -386,6 +386,47 @@ graf_status_t graf_composite_terms(const void* x, graf_input_t kind, int32_t B, 
     return cuda_status(graf::run_composite(q, M, static_cast<cudaStream_t>(stream)));
 }
 
+// ------------------------------------------------------------ match term
+size_t graf_af_match_workspace_bytes(int32_t B, int32_t N, int32_t M, graf_window_t w) {
+    if (check_shape(B, N, M) != GRAF_OK || check_window(N, M, w) != GRAF_OK) return 0;
+    const Tiling T = graf::make_tiling(B, M, w.k_lo, w.k_hi);
+    return backward_ws(B, N, T) + csum_bytes(B, T);
+}
+
+graf_status_t graf_af_match(const void* x, graf_input_t kind, int32_t B, int32_t N, int32_t M, graf_window_t w,
+                            const float* target, float weight, float eps, float* loss_out, float* out8,
+                            graf_c32* grad_s, float* grad_phi, int32_t accumulate, void* workspace,
+                            size_t workspace_bytes, void* stream) {
+    graf_status_t s = check_common(x, kind, B, N, M, w);
+    if (s != GRAF_OK) return s;
+    if (!target || !(weight == weight) || !(eps >= 0.0f) || eps > 1e30f) return GRAF_ERR_INVALID_ARG;
+    if (grad_phi && kind != GRAF_IN_PHASE) return GRAF_ERR_INVALID_ARG;
+    const Tiling T = graf::make_tiling(B, M, w.k_lo, w.k_hi);
+    if (!workspace || workspace_bytes < graf_af_match_workspace_bytes(B, N, M, w)) return GRAF_ERR_WORKSPACE;
+    if (reinterpret_cast<uintptr_t>(workspace) & 255) return GRAF_ERR_WORKSPACE;
+    const int acc = graf::acc_copies_for(M, N);
+    if (acc < 1) return GRAF_ERR_UNSUPPORTED;
+    AfParams p = base_params(x, kind, B, N, M, w, T);
+    p.eps = eps;
+    p.beta = 1.0f;  // no log-sum-exp term: w_psl = w_isl = 0
+    p.target = target;
+    p.match_w = weight;
+    p.out8 = out8;
+    p.acc_copies = acc;
+    p.phase_only = (kind == GRAF_IN_PHASE && grad_s == nullptr) ? 1 : 0;
+    p.grad_acc = accumulate ? 1 : 0;
+    unsigned char* ws = static_cast<unsigned char*>(workspace);
+    p.gpart = reinterpret_cast<float2*>(ws);
+    p.csum = reinterpret_cast<float*>(ws + gpart_bytes(B, N, T));
+    p.usum = reinterpret_cast<double*>(ws + gpart_bytes(B, N, T) + csum_bytes(B, T));
+    p.mpart = reinterpret_cast<float*>(ws + backward_ws(B, N, T));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = graf::run_match(p, loss_out, st);
+    if (e == cudaSuccess && (grad_s || grad_phi))
+        e = graf::run_grad_reduce(p, nullptr, reinterpret_cast<float2*>(grad_s), grad_phi, st);
+    return cuda_status(e);
+}
+
 // ------------------------------------------------------------ periodic AF
 static Mode periodic_mode(int32_t sign) { return Mode{1, sign > 0 ? 1 : 0}; }
 

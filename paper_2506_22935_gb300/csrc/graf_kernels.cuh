@@ -65,6 +65,11 @@ struct AfParams {
     // conj(s) (|X| and the losses are the same; the gradients are mapped back).
     int periodic, pconj;
     int chi_out;           // forward output: 0 Ahat, 1 |X|^2 / E^2, 2 |X|^2
+    // match to a target surface (L_match of Eq. 22)
+    const float* target;   // [B][k_hi-k_lo+1][m_hi-m_lo+1] target Ahat^2 over the window
+    float match_w;         // its weight lambda_1
+    float* mpart;          // per-CTA partial sums of (Ahat^2 - target)^2
+    int grad_acc;          // gradient reduction adds to the output instead of writing it
     // batch plan
     const WaveDesc* waves;
     const int2* items;     // (waveform, tile) of this launch's work items, longest first
@@ -100,6 +105,8 @@ struct CompParams {
     int accumulate;
 };
 cudaError_t run_composite(const CompParams& q, int M, cudaStream_t st);
+template <int M> cudaError_t run_match_m(const AfParams& p, cudaStream_t st);
+cudaError_t run_match(const AfParams& p, float* loss_out, cudaStream_t st);
 template <int M> cudaError_t run_composite_m(const CompParams& q, cudaStream_t st);
 template <int M> cudaError_t run_spectral_m(const SpecParams& q, cudaStream_t st);
 

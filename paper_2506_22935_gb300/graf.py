@@ -86,6 +86,9 @@ _SIGS = {
                                               _i32, _vp]),
     "graf_composite_terms": (ctypes.c_int, [_vp, ctypes.c_int, _i32, _i32, ctypes.c_float, ctypes.c_float,
                                             ctypes.c_float, ctypes.c_float, _vp, _vp, _vp, _vp, _i32, _vp]),
+    "graf_af_match_workspace_bytes": (_sz, [_i32, _i32, _i32, graf_window_t]),
+    "graf_af_match": (ctypes.c_int, [_vp, ctypes.c_int, _i32, _i32, _i32, graf_window_t, _vp, ctypes.c_float,
+                                     ctypes.c_float, _vp, _vp, _vp, _vp, _i32, _vp, _sz, _vp]),
     "graf_batch_plan_create": (ctypes.c_int, [_i32, _vp, _vp, _vp, _vp, _i32, ctypes.c_int, _vp]),
     "graf_batch_plan_create_scenarios": (ctypes.c_int, [_i32, _vp, _i32, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
     "graf_batch_plan_destroy": (ctypes.c_int, [_vp]),
@@ -175,6 +178,35 @@ def composite_terms(x, gamma: float = 50.0, eps: float = 0.0, w_width: float = 1
     _check(graf_composite_terms(x.data_ptr(), kind, B, N, float(gamma), float(eps), float(w_width), float(w_const),
                                 None, terms.data_ptr(), gs, gp, 0, _stream(x.device)), "graf_composite_terms")
     return terms, grad
+
+
+def graf_af_match_workspace_bytes(B, N, M, w) -> int:
+    return load().graf_af_match_workspace_bytes(B, N, M, w)
+
+
+def graf_af_match(x, kind, B, N, M, w, target, weight, eps, loss_out, out8, grad_s, grad_phi, accumulate,
+                  workspace, workspace_bytes, stream) -> int:
+    return load().graf_af_match(x, kind, B, N, M, w, target, weight, eps, loss_out, out8, grad_s, grad_phi,
+                                accumulate, workspace, workspace_bytes, stream)
+
+
+def af_match(x, M: int, window: Window, target, weight: float = 1.0, eps: float = 1e-12):
+    """(sum (Ahat^2 - target)^2 [B], gradient of weight * that sum)."""
+    torch = _torch()
+    x, kind, B, N = _prep(x)
+    nb = graf_af_match_workspace_bytes(B, N, M, window.c())
+    if nb == 0:
+        raise GrafError(1, "graf_af_match_workspace_bytes")
+    ws = _workspace(nb, x.device)
+    target = target.contiguous().to(torch.float32)
+    loss = torch.empty(B, dtype=torch.float32, device=x.device)
+    grad = torch.empty((B, N), dtype=torch.float32 if kind == GRAF_IN_PHASE else torch.complex64, device=x.device)
+    gs = grad.data_ptr() if kind == GRAF_IN_COMPLEX else None
+    gp = grad.data_ptr() if kind == GRAF_IN_PHASE else None
+    _check(graf_af_match(x.data_ptr(), kind, B, N, M, window.c(), target.data_ptr(), float(weight), float(eps),
+                         loss.data_ptr(), None, gs, gp, 0, ws.data_ptr(), ws.numel(), _stream(x.device)),
+           "graf_af_match")
+    return loss, grad
 
 
 def graf_paf_forward(x, kind, B, N, sign, normalise, chi_out, stream) -> int:
