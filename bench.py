@@ -71,13 +71,16 @@ def _measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+# the sources af_fused_kernel<2048> is compiled from
+_FUSED_SOURCES = ("graf_af_impl.cuh", "graf_fft.cuh", "graf_kernels.cuh", "graf_af_m2048.cu", "gen_twiddles.py")
+
+
 def _kernel_hash():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2506_22935_gb300", "csrc")
-    for name in sorted(os.listdir(d)):
-        if name.endswith((".cu", ".cuh", ".py")):
-            with open(os.path.join(d, name), "rb") as f:
-                h.update(name.encode() + f.read())
+    for name in _FUSED_SOURCES:
+        with open(os.path.join(d, name), "rb") as f:
+            h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
 
 
@@ -749,6 +752,87 @@ def run_lpi(args):
     print(json.dumps(line), flush=True)
 
 
+def run_terms(args):
+    """The composite and multi-scenario terms at the benchmark size (256 codes,
+    N = 1024, M = 2048): mainlobe width + modulus variance (Sec. 5.1, Eq. 22),
+    the target match over the whole AF (Eq. 22), and a three-scenario plan
+    (Eq. 24: the whole AF with PSL + ISL, a range-Doppler box with ISL, a
+    velocity band with PSL + ISL) with loss and summed gradient."""
+    import numpy as np
+    import torch
+
+    from paper_2506_22935_gb300 import graf as g
+    from paper_2506_22935_gb300 import inputs
+
+    g.load()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    x = torch.from_numpy(inputs.random_phases(SEED + 20, B, N)).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    grad = torch.empty((B, N), device=dev)
+    out8 = torch.zeros((B, 8), device=dev)
+    terms = torch.empty((B, 2), device=dev)
+    steps = max(3, min(args.steps, 50))
+    res = {}
+
+    def comp():
+        st = g.graf_composite_terms(x.data_ptr(), g.GRAF_IN_PHASE, B, N, 50.0, EPS, 1.0, 1.0, out8.data_ptr(),
+                                    terms.data_ptr(), None, grad.data_ptr(), 1, sp)
+        assert st == 0, g.graf_status_string(st)
+
+    ms = _timed_events(comp, steps, 3, stream, flush)
+    res["composite_width_modvar"] = {"ms": ms, "codes_per_s": B / (ms / 1e3)}
+    w = g.Window.full(N, M, k_ml=-1, m_ml=-1)
+    target = torch.zeros((B, 2 * N - 1, M), device=dev)  # 4.3 GB: a sidelobe-free ideal
+    nb = g.graf_af_match_workspace_bytes(B, N, M, w.c())
+    ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+    loss = torch.empty(B, device=dev)
+
+    def match():
+        st = g.graf_af_match(x.data_ptr(), g.GRAF_IN_PHASE, B, N, M, w.c(), target.data_ptr(), 1.0, EPS,
+                             loss.data_ptr(), None, None, grad.data_ptr(), 0, ws.data_ptr(), nb, sp)
+        assert st == 0, g.graf_status_string(st)
+
+    ms = _timed_events(match, steps, 3, stream, flush)
+    cells = B * (2 * N - 1) * M
+    res["match_full_af"] = {"ms": ms, "Gcells_per_s": cells / (ms / 1e3) / 1e9,
+                            "target_GB_per_s": target.numel() * 4 / (ms / 1e3) / 1e9}
+    del target, ws
+    torch.cuda.empty_cache()
+    src = np.repeat(np.arange(B), 3)
+    windows, losses = [], []
+    for i in range(3 * B):
+        if i % 3 == 0:
+            windows.append(g.Window.full(N, M))
+            losses.append(g.Loss(1.0, 1.0, BETA, EPS))
+        elif i % 3 == 1:
+            windows.append(g.Window(-256, 256, -128, 128, 0, 0))
+            losses.append(g.Loss(0.0, 1.0, BETA, EPS))
+        else:
+            windows.append(g.Window(-(N - 1), N - 1, 64, 512, -1, -1))
+            losses.append(g.Loss(0.5, 1.0, BETA, EPS))
+    plan = g.BatchPlan.scenarios([N] * B, src, windows, losses, M=[M] * (3 * B))
+    lam = torch.tensor([1.0, 0.5, 0.25] * B, device=dev)
+    o8 = torch.empty((3 * B, 8), device=dev)
+    gsum = torch.empty(B * N, device=dev)
+    xs = x.reshape(-1)
+
+    def scen():
+        plan.loss_backward(xs, dL=lam, out8=o8, grad=gsum)
+
+    ms = _timed_events(scen, steps, 3, stream, flush)
+    res["scenarios_3_per_code"] = {"ms": ms, "codes_per_s": B / (ms / 1e3),
+                                   "plan": plan.info()}
+    plan.close()
+    line = {"metric": "composite and multi-scenario terms at N=1024 M=2048", "value": res["match_full_af"]["Gcells_per_s"],
+            "unit": "Gcells/s (target match over the whole AF, fwd+bwd)", "higher_is_better": True, "n_gpus": 1,
+            "steps": steps, "warmup": 3, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{B} random codes, N={N}, M={M}", "l2": "flushed between steps"},
+            "terms": res}
+    print(json.dumps(line), flush=True)
+
+
 def run_learned(args):
     """Time to a masked-ISL target from the learned proposal vs from a random
     initialisation (the second half of the headline metric).  The proposal is
@@ -829,7 +913,8 @@ def main():
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison pipeline")
     ap.add_argument("--batch", type=int, default=B,
                     help="waveforms per GPU (default 256, the benchmark workload; smaller only for profiling)")
-    ap.add_argument("--workload", default="af", choices=["af", "learned", "optim", "ragged", "periodic", "lpi"])
+    ap.add_argument("--workload", default="af", choices=["af", "learned", "optim", "ragged", "periodic", "lpi",
+                                                                 "terms"])
     ap.add_argument("--optim-runs", type=int, default=3)
     ap.add_argument("--cufft-stride", type=int, default=50,
                     help="ragged workload: the cuFFT comparison runs on every n-th code")
@@ -857,6 +942,8 @@ def main():
         run_periodic(args)
     elif args.workload == "lpi":
         run_lpi(args)
+    elif args.workload == "terms":
+        run_terms(args)
     else:
         run_graf(args)
 
