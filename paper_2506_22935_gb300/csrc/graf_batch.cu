@@ -300,38 +300,53 @@ static graf_status_t create_plan(int32_t B, const int32_t* N_host, const int32_t
     P->total_x = off;
     std::sort(Ms.begin(), Ms.end(), [](int a, int c) { return a > c; });  // largest rows first
     for (int M : Ms) {
-        Bucket bk;
-        bk.M = M;
-        bk.rps = 4;
+        std::vector<int> all;
+        int max_N = 0;
         for (int b = 0; b < B; ++b)
             if (P->waves[b].M == M) {
-                bk.waves.push_back(b);
-                bk.max_N = std::max(bk.max_N, P->waves[b].N);
+                all.push_back(b);
+                max_N = std::max(max_N, P->waves[b].N);
             }
-        bk.acc_copies = graf::acc_copies_for(M, bk.max_N);
-        if (bk.acc_copies < 1 || graf::row_kernel_smem(M, bk.max_N, 0) > graf::kMaxSmem) {
+        const int acc = graf::acc_copies_for(M, max_N);
+        if (acc < 1 || graf::row_kernel_smem(M, max_N, 0) > graf::kMaxSmem) {
             delete P;
             return GRAF_ERR_UNSUPPORTED;
         }
-        // fused unless a waveform has PSL over a window that does not span every
-        // Doppler bin, or mainlobe-box rows beyond row 0 (row 0 carries no phase
-        // gradient), or its log-sum-exp shift is a running one (it rescales the
-        // accumulators) and the slots cannot each own an accumulator
+        // A waveform runs fused unless it has PSL over a window that does not
+        // span every Doppler bin, or mainlobe-box rows beyond row 0 (row 0
+        // carries no phase gradient), or its log-sum-exp shift is a running one
+        // (it rescales the accumulators) and the slots cannot each own an
+        // accumulator.  The fused and the two-pass waveforms of one M go to
+        // separate buckets, so one of the latter does not slow the rest.
         const int slots = graf::kThreads / graf::tpr_of(M);
-        for (int b : bk.waves) {
+        std::vector<int> fused, two_pass;
+        for (int b : all) {
             WaveDesc& d = P->waves[b];
             const bool full_m = d.m_lo == -(M / 2) && d.m_hi == M / 2 - 1;
             const bool fixed = graf::lse_fixed_shift(P->kind == GRAF_IN_PHASE ? 1 : 0, d.eps, d.beta, d.N) > 0.0f;
+            bool ok = true;
             if (d.w_psl != 0.0f) {
-                if (!full_m || d.k_ml >= 1 || (!fixed && bk.acc_copies < slots)) bk.fused = false;
+                if (!full_m || d.k_ml >= 1 || (!fixed && acc < slots)) ok = false;
                 else if (d.k_ml == 0 && d.m_ml >= 0 && d.r_lo == 0) d.defer_hi = 0;
             }
+            (ok ? fused : two_pass).push_back(b);
         }
-        for (int b : bk.waves) {
-            P->waves[b].unscaled = bk.fused ? 0 : 1;
-            if (!bk.fused) P->waves[b].defer_hi = -1;
+        for (int pass = 0; pass < 2; ++pass) {
+            const std::vector<int>& ws = pass == 0 ? fused : two_pass;
+            if (ws.empty()) continue;
+            Bucket bk;
+            bk.M = M;
+            bk.rps = 4;
+            bk.fused = pass == 0;
+            bk.waves = ws;
+            for (int b : ws) bk.max_N = std::max(bk.max_N, P->waves[b].N);
+            bk.acc_copies = graf::acc_copies_for(M, bk.max_N);
+            for (int b : ws) {
+                P->waves[b].unscaled = bk.fused ? 0 : 1;
+                if (!bk.fused) P->waves[b].defer_hi = -1;
+            }
+            P->buckets.push_back(bk);
         }
-        P->buckets.push_back(bk);
     }
     if (cudaMalloc(&P->d_waves, sizeof(WaveDesc) * B) != cudaSuccess ||
         cudaMalloc(&P->d_counters, sizeof(unsigned int) * P->buckets.size()) != cudaSuccess) {
