@@ -65,3 +65,21 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     with contextlib.redirect_stdout(buf):
         bench.run_reference(type("A", (), {"steps": 1, "warmup": 0, "gpus": 2})())
     assert buf.getvalue() == ""
+
+
+def test_reference_arm_prints_the_contract_line(monkeypatch):
+    """Rank 0 of the reference arm prints one JSON line with the metric, the
+    oracle as cpu_baseline and a zero-copy e2e block (small oracle budget)."""
+    import json
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    monkeypatch.setattr(bench, "_oracle_budget_cols", lambda seconds: 4)
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        bench.run_reference(type("A", (), {"steps": 1, "warmup": 3, "gpus": 1})())
+    line = json.loads(buf.getvalue().strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["value"] > 0 and line["higher_is_better"] is True
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
