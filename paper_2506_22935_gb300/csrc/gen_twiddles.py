@@ -12,9 +12,9 @@ an exact integer ratio and rounded once to float32:
   W_(Ns_p R_p)^(i r) for r in [1, R_p), i in [0, Ns_p).  Consecutive threads
   read consecutive i, so the loads coalesce.
 
-The radix plan must match ``graf_fft.cuh``: R_0 = min(M, 64) and the rest of
-M / R_0 is split into radices that divide 64 (one pass if it is <= 64, else
-16 x (M/1024)).
+The radix plan must match ``graf_fft.cuh``: R_0 = the values per thread
+(32 for M in [128, 8192], else min(M, 64)) and the rest of M / R_0 is one
+pass if it is <= R_0, else 16 x (M / (16 R_0)).
 """
 from __future__ import annotations
 
@@ -25,11 +25,11 @@ M_ALL = [8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 8192, 16384]
 
 
 def radix_plan(M: int) -> list[int]:
-    r0 = min(M, 64)
+    r0 = 32 if 128 <= M <= 8192 else min(M, 64)
     rest = M // r0
     if rest == 1:
         return [r0]
-    if rest <= 64:
+    if rest <= r0:
         return [r0, rest]
     return [r0, 16, rest // 16]
 

@@ -336,20 +336,20 @@ static size_t smem_need(int M, int N, int which) {
 
 size_t row_kernel_smem(int M, int N, int which) { return smem_need(M, N, which); }
 
-int acc_copies_for(int M, int N) {
+int acc_copies_for(int M, int N, int real) {
     switch (M) {
-        case 8: return backward_acc_copies<8>(N);
-        case 16: return backward_acc_copies<16>(N);
-        case 32: return backward_acc_copies<32>(N);
-        case 64: return backward_acc_copies<64>(N);
-        case 128: return backward_acc_copies<128>(N);
-        case 256: return backward_acc_copies<256>(N);
-        case 512: return backward_acc_copies<512>(N);
-        case 1024: return backward_acc_copies<1024>(N);
-        case 2048: return backward_acc_copies<2048>(N);
-        case 4096: return backward_acc_copies<4096>(N);
-        case 8192: return backward_acc_copies<8192>(N);
-        case 16384: return backward_acc_copies<16384>(N);
+        case 8: return backward_acc_copies<8>(N, real);
+        case 16: return backward_acc_copies<16>(N, real);
+        case 32: return backward_acc_copies<32>(N, real);
+        case 64: return backward_acc_copies<64>(N, real);
+        case 128: return backward_acc_copies<128>(N, real);
+        case 256: return backward_acc_copies<256>(N, real);
+        case 512: return backward_acc_copies<512>(N, real);
+        case 1024: return backward_acc_copies<1024>(N, real);
+        case 2048: return backward_acc_copies<2048>(N, real);
+        case 4096: return backward_acc_copies<4096>(N, real);
+        case 8192: return backward_acc_copies<8192>(N, real);
+        case 16384: return backward_acc_copies<16384>(N, real);
         default: return 0;
     }
 }

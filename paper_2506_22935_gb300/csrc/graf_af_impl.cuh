@@ -67,7 +67,7 @@ __device__ __forceinline__ void for_each_item(const AfParams& p, F&& body) {
 // for every window cell of rows k and -k.  Stores are coalesced along m (consecutive threads hold
 // consecutive Doppler bins) and streaming (written once, never re-read here).
 template <int M, bool HALF>
-__global__ void __launch_bounds__(kThreads, 1) af_forward_kernel(AfParams p) {
+__global__ void __launch_bounds__(kThreads, RowPlan<M>::MIN_BLOCKS) af_forward_kernel(AfParams p) {
     using P = RowPlan<M>;
     extern __shared__ __align__(256) unsigned char smem[];
     float2* s_sm = reinterpret_cast<float2*>(smem);
@@ -246,7 +246,7 @@ __device__ __forceinline__ void loss_item(const AfParams& p, int b, int tile, un
 }
 
 template <int M, bool HALF>
-__global__ void __launch_bounds__(kThreads, 1) af_loss_kernel(AfParams p) {
+__global__ void __launch_bounds__(kThreads, RowPlan<M>::MIN_BLOCKS) af_loss_kernel(AfParams p) {
     extern __shared__ __align__(256) unsigned char smem[];
     for_each_item(p, [&](int b, int tile) { loss_item<M, HALF>(p, b, tile, smem); });
 }
@@ -433,10 +433,11 @@ __device__ __forceinline__ void backward_item(const AfParams& p, int b, int tile
     float2* bufs = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(sig_len(p)));
     float2* acc_all = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(sig_len(p)) + row_buffer_bytes<M>());
     float* red = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(acc_all) +
-                                          (((size_t)p.acc_copies * sig_len(p) * sizeof(float2) + 255) & ~(size_t)255));
+                                          acc_region_bytes(p));
 
     const int tid = threadIdx.x, slot = tid / P::TPR, t = tid % P::TPR;
-    for (int i = tid; i < p.acc_copies * wv.sN; i += kThreads) acc_all[i] = make_float2(0.0f, 0.0f);
+    for (int i = tid; i < (int)(acc_region_bytes(p) / sizeof(float2)); i += kThreads)
+        acc_all[i] = make_float2(0.0f, 0.0f);
     const float E = load_signal(wv, s_sm, red);  // includes __syncthreads
     const float invE2 = 1.0f / (E * E);
     const float eps_n = wv.eps * invE2;
@@ -504,7 +505,7 @@ __device__ __forceinline__ void backward_item(const AfParams& p, int b, int tile
 }
 
 template <int M, bool HALF>
-__global__ void __launch_bounds__(kThreads, 1) af_backward_kernel(AfParams p) {
+__global__ void __launch_bounds__(kThreads, RowPlan<M>::MIN_BLOCKS) af_backward_kernel(AfParams p) {
     extern __shared__ __align__(256) unsigned char smem[];
     for_each_item(p, [&](int b, int tile) { backward_item<M, HALF>(p, b, tile, smem); });
 }
@@ -527,9 +528,10 @@ __device__ __forceinline__ void match_item(const AfParams& p, int b, int tile, u
     float2* bufs = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(sig_len(p)));
     float2* acc_all = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(sig_len(p)) + row_buffer_bytes<M>());
     float* red = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(acc_all) +
-                                          (((size_t)p.acc_copies * sig_len(p) * sizeof(float2) + 255) & ~(size_t)255));
+                                          acc_region_bytes(p));
     const int tid = threadIdx.x, slot = tid / P::TPR, t = tid % P::TPR;
-    for (int i = tid; i < p.acc_copies * wv.sN; i += kThreads) acc_all[i] = make_float2(0.0f, 0.0f);
+    for (int i = tid; i < (int)(acc_region_bytes(p) / sizeof(float2)); i += kThreads)
+        acc_all[i] = make_float2(0.0f, 0.0f);
     const float E = load_signal(wv, s_sm, red);  // includes __syncthreads
     const float invE2 = 1.0f / (E * E);
     const float eps_n = wv.eps * invE2;
@@ -608,7 +610,7 @@ __device__ __forceinline__ void match_item(const AfParams& p, int b, int tile, u
 }
 
 template <int M, bool HALF>
-__global__ void __launch_bounds__(kThreads, 1) af_match_kernel(AfParams p) {
+__global__ void __launch_bounds__(kThreads, RowPlan<M>::MIN_BLOCKS) af_match_kernel(AfParams p) {
     extern __shared__ __align__(256) unsigned char smem[];
     for_each_item(p, [&](int b, int tile) { match_item<M, HALF>(p, b, tile, smem); });
 }
@@ -669,7 +671,7 @@ __device__ __forceinline__ float slot_sum(float x, float* scratch, int slot) {
 //   dSV/ds*[n] = sum_g dSV/dP[g] S[g] exp(+j 2 pi g n / N)  (adjoint DFT, run
 //                as conj(DFT(conj(.))) on the same transform instance)
 template <int M>
-__global__ void __launch_bounds__(kThreads, 1) spectral_kernel(SpecParams q) {
+__global__ void __launch_bounds__(kThreads, RowPlan<M>::MIN_BLOCKS) spectral_kernel(SpecParams q) {
     using P = RowPlan<M>;
     constexpr int SLOTS = kThreads / P::TPR;
     extern __shared__ __align__(256) unsigned char smem[];
@@ -774,7 +776,7 @@ cudaError_t run_spectral_m(const SpecParams& q, cudaStream_t st) {
 // s.  Five transforms per waveform; Re(DFT(G)) waits in shared memory while
 // S is transformed again.
 template <int M>
-__global__ void __launch_bounds__(kThreads, 1) composite_kernel(CompParams q) {
+__global__ void __launch_bounds__(kThreads, RowPlan<M>::MIN_BLOCKS) composite_kernel(CompParams q) {
     using P = RowPlan<M>;
     constexpr int SLOTS = kThreads / P::TPR;
     extern __shared__ __align__(256) unsigned char smem[];
@@ -948,12 +950,13 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
     float2* bufs = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(sig_len(p)));
     float2* acc_all = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(sig_len(p)) + row_buffer_bytes<M>());
     float* red = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(acc_all) +
-                                          (((size_t)p.acc_copies * sig_len(p) * sizeof(float2) + 255) & ~(size_t)255));
+                                          acc_region_bytes(p));
     // red: [0,8) reductions, [8,16) slot-max scratch (TPR > 32), [64, 64+SLOTS) final slot shifts
     // (SLOTS <= 32 here unless M <= 64, where the shifts live in registers only), [128, 160) float4s
 
     const int tid = threadIdx.x, slot = tid / P::TPR, t = tid % P::TPR;
-    for (int i = tid; i < p.acc_copies * wv.sN; i += kThreads) acc_all[i] = make_float2(0.0f, 0.0f);
+    for (int i = tid; i < (int)(acc_region_bytes(p) / sizeof(float2)); i += kThreads)
+        acc_all[i] = make_float2(0.0f, 0.0f);
     const float E = load_signal(wv, s_sm, red);  // includes __syncthreads
     // the item's constants live in shared memory and are re-read after each
     // transform, so that none of them occupies a register during the FFTs
@@ -1162,7 +1165,7 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
 }
 
 template <int M, bool HALF>
-__global__ void __launch_bounds__(kThreads, 1) af_fused_kernel(AfParams p) {
+__global__ void __launch_bounds__(kThreads, RowPlan<M>::MIN_BLOCKS) af_fused_kernel(AfParams p) {
     extern __shared__ __align__(256) unsigned char smem[];
     for_each_item(p, [&](int b, int tile) { fused_item<M, HALF>(p, b, tile, smem); });
 }
@@ -1200,7 +1203,7 @@ cudaError_t run_loss_m(const AfParams& p, cudaStream_t st) {
 template <int M>
 cudaError_t run_backward_m(const AfParams& p, cudaStream_t st) {
     if (p.acc_copies < 1 || (256 / RowPlan<M>::TPR) % p.acc_copies) return cudaErrorInvalidConfiguration;
-    const size_t smem = backward_smem<M>(sig_len(p), p.acc_copies);
+    const size_t smem = backward_smem<M>(sig_len(p), p.acc_copies, p.phase_only);
     return launch_rows(af_backward_kernel<M, false>, smem, p, st);
 }
 
@@ -1212,7 +1215,7 @@ cudaError_t run_backward_m(const AfParams& p, cudaStream_t st) {
 template <int M>
 cudaError_t run_match_m(const AfParams& p, cudaStream_t st) {
     if (p.acc_copies < 1 || (256 / RowPlan<M>::TPR) % p.acc_copies) return cudaErrorInvalidConfiguration;
-    const size_t smem = backward_smem<M>(sig_len(p), p.acc_copies);
+    const size_t smem = backward_smem<M>(sig_len(p), p.acc_copies, p.phase_only);
     if (2 * p.N <= M && !p.periodic) return launch_rows(af_match_kernel<M, true>, smem, p, st);
     return launch_rows(af_match_kernel<M, false>, smem, p, st);
 }
@@ -1220,7 +1223,7 @@ cudaError_t run_match_m(const AfParams& p, cudaStream_t st) {
 template <int M>
 cudaError_t run_fused_m(const AfParams& p, cudaStream_t st) {
     if (p.acc_copies < 1 || (256 / RowPlan<M>::TPR) % p.acc_copies) return cudaErrorInvalidConfiguration;
-    const size_t smem = backward_smem<M>(sig_len(p), p.acc_copies);
+    const size_t smem = backward_smem<M>(sig_len(p), p.acc_copies, p.phase_only);
     if (2 * p.N <= M) return launch_rows(af_fused_kernel<M, true>, smem, p, st);
     return launch_rows(af_fused_kernel<M, false>, smem, p, st);
 }

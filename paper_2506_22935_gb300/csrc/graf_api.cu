@@ -222,7 +222,7 @@ static graf_status_t af_backward_impl(const Mode& md, const void* x, graf_input_
     p.csum = reinterpret_cast<float*>(ws + gpart_bytes(B, N, T));
     p.usum = reinterpret_cast<double*>(ws + gpart_bytes(B, N, T) + csum_bytes(B, T));
     p.phase_only = (kind == GRAF_IN_PHASE && grad_s == nullptr) ? 1 : 0;
-    p.acc_copies = graf::acc_copies_for(M, store_len(md, N));
+    p.acc_copies = graf::acc_copies_for(M, store_len(md, N), p.phase_only);
     if (p.acc_copies < 1) return GRAF_ERR_UNSUPPORTED;
     return cuda_status(graf::run_backward(p, dL, reinterpret_cast<float2*>(grad_s), grad_phi,
                                           static_cast<cudaStream_t>(stream)));
@@ -239,9 +239,9 @@ static graf_status_t af_loss_backward_impl(const Mode& md, const void* x, graf_i
     if (grad_phi && kind != GRAF_IN_PHASE) return GRAF_ERR_INVALID_ARG;
     if (!workspace || workspace_bytes < backward_ws_impl(md, B, N, M, w)) return GRAF_ERR_WORKSPACE;
     if (reinterpret_cast<uintptr_t>(workspace) & 255) return GRAF_ERR_WORKSPACE;
-    const int acc = graf::acc_copies_for(M, store_len(md, N));
-    if (acc < 1) return GRAF_ERR_UNSUPPORTED;
     const bool phase_only = kind == GRAF_IN_PHASE && grad_s == nullptr;
+    const int acc = graf::acc_copies_for(M, store_len(md, N), phase_only ? 1 : 0);
+    if (acc < 1) return GRAF_ERR_UNSUPPORTED;
     FusedPlan f = fused_plan(B, N, M, w, l.w_psl != 0.0f, phase_only);
     // on the PSL path with a running log-sum-exp shift each row slot needs its
     // own gradient accumulator (it rescales it); a fixed shift rescales nothing
@@ -291,6 +291,8 @@ static graf_status_t af_loss_backward_impl(const Mode& md, const void* x, graf_i
         q.csum = csum2;
         q.scale = nullptr;
         q.phase_only = 0;  // its rows all need their gradient
+        q.acc_copies = graf::acc_copies_for(M, store_len(md, N), 0);  // complex accumulators
+        if (q.acc_copies < 1) return GRAF_ERR_UNSUPPORTED;
         e = graf::run_backward(q, nullptr, nullptr, nullptr, st);
         p.tiles2 = f.T2.tiles;
         p.gpart2 = gpart2;
@@ -404,7 +406,8 @@ graf_status_t graf_af_match(const void* x, graf_input_t kind, int32_t B, int32_t
     const Tiling T = graf::make_tiling(B, M, w.k_lo, w.k_hi);
     if (!workspace || workspace_bytes < graf_af_match_workspace_bytes(B, N, M, w)) return GRAF_ERR_WORKSPACE;
     if (reinterpret_cast<uintptr_t>(workspace) & 255) return GRAF_ERR_WORKSPACE;
-    const int acc = graf::acc_copies_for(M, N);
+    const int phase_only = (kind == GRAF_IN_PHASE && grad_s == nullptr) ? 1 : 0;
+    const int acc = graf::acc_copies_for(M, N, phase_only);
     if (acc < 1) return GRAF_ERR_UNSUPPORTED;
     AfParams p = base_params(x, kind, B, N, M, w, T);
     p.eps = eps;
@@ -413,7 +416,7 @@ graf_status_t graf_af_match(const void* x, graf_input_t kind, int32_t B, int32_t
     p.match_w = weight;
     p.out8 = out8;
     p.acc_copies = acc;
-    p.phase_only = (kind == GRAF_IN_PHASE && grad_s == nullptr) ? 1 : 0;
+    p.phase_only = phase_only;
     p.grad_acc = accumulate ? 1 : 0;
     unsigned char* ws = static_cast<unsigned char*>(workspace);
     p.gpart = reinterpret_cast<float2*>(ws);

@@ -307,7 +307,7 @@ static graf_status_t create_plan(int32_t B, const int32_t* N_host, const int32_t
                 all.push_back(b);
                 max_N = std::max(max_N, P->waves[b].N);
             }
-        const int acc = graf::acc_copies_for(M, max_N);
+        const int acc = graf::acc_copies_for(M, max_N, 1);
         if (acc < 1 || graf::row_kernel_smem(M, max_N, 0) > graf::kMaxSmem) {
             delete P;
             return GRAF_ERR_UNSUPPORTED;
@@ -340,7 +340,7 @@ static graf_status_t create_plan(int32_t B, const int32_t* N_host, const int32_t
             bk.fused = pass == 0;
             bk.waves = ws;
             for (int b : ws) bk.max_N = std::max(bk.max_N, P->waves[b].N);
-            bk.acc_copies = graf::acc_copies_for(M, bk.max_N);
+            bk.acc_copies = graf::acc_copies_for(M, bk.max_N, 1);
             for (int b : ws) {
                 P->waves[b].unscaled = bk.fused ? 0 : 1;
                 if (!bk.fused) P->waves[b].defer_hi = -1;

@@ -186,21 +186,28 @@ __host__ __device__ __forceinline__ void dft(float2* v) {
 template <int M>
 struct RowPlan {
     static_assert(M >= 8 && M <= 16384 && (M & (M - 1)) == 0, "M must be a power of two in [8,16384]");
-    static constexpr int VALS = M < 64 ? M : 64;  // values per thread
+    // values per thread: 32 for M in [128, 8192], where half the registers let
+    // two CTAs (16 warps) share an SM (from M = 2048 on at the price of a
+    // third pass); 64 for M = 16384 (a row of 512 threads would not fit a
+    // CTA); M below 64
+    static constexpr int VALS = (M >= 128 && M <= 8192) ? 32 : (M < 64 ? M : 64);
     static constexpr int TPR = M / VALS;           // threads per row
-    static constexpr int NPASS = TPR == 1 ? 1 : (TPR <= 64 ? 2 : 3);
+    static constexpr int NPASS = TPR == 1 ? 1 : (TPR <= VALS ? 2 : 3);
     static constexpr int R0 = VALS;
     static constexpr int R1 = NPASS == 1 ? 1 : (NPASS == 2 ? TPR : 16);
     static constexpr int R2 = NPASS == 3 ? TPR / 16 : 1;
-    // shared-memory row buffer (float2 units): one pad slot per 64 values keeps
-    // the stride-64 stores of the first pass free of bank conflicts
-    static constexpr int SMEM_ROW = NPASS == 1 ? 0 : M + M / 64;
+    static constexpr int MIN_BLOCKS = VALS == 32 ? 2 : 1;  // CTAs per SM the registers allow
+    // shared-memory row buffer (float2 units): one pad slot per VALS values
+    // keeps the stride-VALS stores of the first pass free of bank conflicts
+    static constexpr int PAD = VALS < 32 ? 64 : VALS;
+    static constexpr int SMEM_ROW = NPASS == 1 ? 0 : M + M / PAD;
     // exchange real and imaginary halves separately (half the buffer) for the
     // largest rows so that the backward's accumulators still fit
     static constexpr bool SPLIT = M >= 8192;
 };
 
-__device__ __forceinline__ int padi(int i) { return i + (i >> 6); }
+template <int PAD>
+__device__ __forceinline__ int padi(int i) { return i + i / PAD; }
 
 template <int M, int P>
 __device__ __forceinline__ const float2* tw_table() {
@@ -230,18 +237,19 @@ template <int M, int R, int NS, bool SPLIT_PART_RE, bool SPLIT>
 __device__ __forceinline__ void pass_store(const float2* v, float2* buf, int t) {
     using P = RowPlan<M>;
     constexpr int NB = P::VALS / R;
-    static_assert(NS == 1 || NS % 64 == 0, "pass span must be 1 or a multiple of 64");
-    static_assert(NS != 1 || (R == 64 && NB == 1), "first pass must be radix 64");
+    constexpr int PAD = P::PAD;
+    static_assert(NS == 1 || NS % PAD == 0, "pass span must be 1 or a multiple of the pad period");
+    static_assert(NS != 1 || (R == PAD && NB == 1), "first pass must be radix VALS");
     sfor<0, NB>([&](auto u) {
         const int j = t + P::TPR * decltype(u)::value;
         int base;
         if constexpr (NS == 1) {
-            base = 65 * j;
+            base = (PAD + 1) * j;
         } else {
-            base = padi((j / NS) * NS * R + (j % NS));
+            base = padi<PAD>((j / NS) * NS * R + (j % NS));
         }
         sfor<0, R>([&](auto r) {
-            constexpr int off = NS == 1 ? decltype(r)::value : decltype(r)::value * (NS + NS / 64);
+            constexpr int off = NS == 1 ? decltype(r)::value : decltype(r)::value * (NS + NS / PAD);
             const float2 x = v[decltype(u)::value * R + decltype(r)::value];
             if constexpr (!SPLIT) buf[base + off] = x;
             else reinterpret_cast<float*>(buf)[base + off] = SPLIT_PART_RE ? x.x : x.y;
@@ -257,12 +265,12 @@ __device__ __forceinline__ void pass_load(float2* v, const float2* buf, int t) {
     using P = RowPlan<M>;
     constexpr int NB = P::VALS / R;
     constexpr int STRIDE = M / R;
-    static_assert(STRIDE % 64 == 0, "load stride must be a multiple of 64");
+    static_assert(STRIDE % P::PAD == 0, "load stride must be a multiple of the pad period");
     sfor<0, NB>([&](auto u) {
         const int j = t + P::TPR * decltype(u)::value;
-        const int base = padi(j);
+        const int base = padi<P::PAD>(j);
         sfor<0, R>([&](auto r) {
-            constexpr int off = decltype(r)::value * (STRIDE + STRIDE / 64);
+            constexpr int off = decltype(r)::value * (STRIDE + STRIDE / P::PAD);
             float2& x = v[decltype(u)::value * R + decltype(r)::value];
             if constexpr (!SPLIT) x = buf[base + off];
             else if constexpr (SPLIT_PART_RE) x.x = reinterpret_cast<const float*>(buf)[base + off];
@@ -290,9 +298,9 @@ __device__ __forceinline__ void exchange(float2* v, float2* buf, int t, int slot
             constexpr int NB = P::VALS / RL;
             constexpr int STRIDE = M / RL;
             sfor<0, NB>([&](auto u) {
-                const int base = padi(t + P::TPR * decltype(u)::value);
+                const int base = padi<P::PAD>(t + P::TPR * decltype(u)::value);
                 sfor<0, RL>([&](auto r) {
-                    constexpr int off = decltype(r)::value * (STRIDE + STRIDE / 64);
+                    constexpr int off = decltype(r)::value * (STRIDE + STRIDE / P::PAD);
                     lre[decltype(u)::value * RL + decltype(r)::value] = reinterpret_cast<const float*>(buf)[base + off];
                 });
             });

@@ -112,6 +112,11 @@ template <int M> cudaError_t run_spectral_m(const SpecParams& q, cudaStream_t st
 
 // Shared-memory length of the signal and of each gradient accumulator.
 __host__ __device__ __forceinline__ int sig_len(const AfParams& p) { return p.periodic ? 2 * p.N : p.N; }
+// Bytes of all gradient accumulators of a CTA (256-byte aligned).
+__host__ __device__ __forceinline__ size_t acc_region_bytes(const AfParams& p) {
+    return ((size_t)p.acc_copies * sig_len(p) * (p.phase_only ? sizeof(float) : sizeof(float2)) + 255) &
+           ~(size_t)255;
+}
 
 // The view of one waveform a kernel works with, in either mode.
 struct Wave {
@@ -212,24 +217,26 @@ template <int M>
 constexpr size_t forward_smem(int N) {
     return smem_signal_bytes<M>(N) + row_buffer_bytes<M>() + kRedBytes;
 }
+// Gradient accumulators: complex (float2) in general, real (float) when only
+// the phase gradient is wanted (see scatter_row_real).
 template <int M>
-constexpr size_t backward_smem(int N, int acc_copies) {
+constexpr size_t backward_smem(int N, int acc_copies, int real = 0) {
     return smem_signal_bytes<M>(N) + row_buffer_bytes<M>() +
-           (((size_t)acc_copies * N * sizeof(float2) + 255) & ~(size_t)255) + kRedBytes;
+           (((size_t)acc_copies * N * (real ? sizeof(float) : sizeof(float2)) + 255) & ~(size_t)255) + kRedBytes;
 }
 // Largest power-of-two number of gradient accumulators (<= slots) that fits
 // in shared memory; 0 if even one does not.
 template <int M>
-int backward_acc_copies(int N) {
+int backward_acc_copies(int N, int real = 0) {
     for (int a = 256 / RowPlan<M>::TPR; a >= 1; a /= 2)
-        if (backward_smem<M>(N, a) <= kMaxSmem) return a;
+        if (backward_smem<M>(N, a, real) <= kMaxSmem) return a;
     return 0;
 }
 
 size_t row_kernel_smem(int M, int N, int which);  // which: 0 forward/loss, 2 backward
 cudaError_t run_loss_rows(const AfParams& p, cudaStream_t st);      // loss row kernel only
 cudaError_t run_backward_rows(const AfParams& p, cudaStream_t st);  // backward row kernel only
-int acc_copies_for(int M, int N);                  // backward accumulators, 0 = unsupported
+int acc_copies_for(int M, int N, int real = 0);    // backward accumulators, 0 = unsupported
 template <int M> cudaError_t run_forward_m(const AfParams& p, cudaStream_t st);
 template <int M> cudaError_t run_loss_m(const AfParams& p, cudaStream_t st);
 template <int M> cudaError_t run_backward_m(const AfParams& p, cudaStream_t st);
