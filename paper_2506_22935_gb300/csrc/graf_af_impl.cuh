@@ -67,7 +67,7 @@ __device__ __forceinline__ void for_each_item(const AfParams& p, F&& body) {
 // for every window cell of rows k and -k.  Stores are coalesced along m (consecutive threads hold
 // consecutive Doppler bins) and streaming (written once, never re-read here).
 template <int M, bool HALF>
-__global__ void __launch_bounds__(kThreads, RowPlan<M>::MIN_BLOCKS) af_forward_kernel(AfParams p) {
+__global__ void __launch_bounds__(RowPlan<M>::THREADS, RowPlan<M>::MIN_BLOCKS) af_forward_kernel(AfParams p) {
     using P = RowPlan<M>;
     extern __shared__ __align__(256) unsigned char smem[];
     float2* s_sm = reinterpret_cast<float2*>(smem);
@@ -89,11 +89,11 @@ __global__ void __launch_bounds__(kThreads, RowPlan<M>::MIN_BLOCKS) af_forward_k
     const int row0 = p.r_lo + tile * p.rows_per_tile;
     const int row_end = min(row0 + p.rows_per_tile, p.r_hi + 1);
     // iterations for the rows this tile actually holds (CTA-uniform)
-    const int iters = max(0, row_end - row0 + (kThreads / P::TPR) - 1) / (kThreads / P::TPR);
+    const int iters = max(0, row_end - row0 + (P::THREADS / P::TPR) - 1) / (P::THREADS / P::TPR);
 
     float2 v[P::VALS];
     for (int it = 0; it < iters; ++it) {
-        const int k = row0 + slot + it * (kThreads / P::TPR);
+        const int k = row0 + slot + it * (P::THREADS / P::TPR);
         const bool valid = k < row_end;
         build_lag_row<M, HALF>(v, s_sm, p.N, p.periodic ? k - p.N : k, t, valid);
         row_sync<P::TPR>(slot);
@@ -178,7 +178,7 @@ __device__ __forceinline__ void loss_item(const AfParams& p, int b, int tile, un
 
     const int row0 = wv.r_lo + tile * wv.rows_per_tile;
     const int row_end = min(row0 + wv.rows_per_tile, wv.r_hi + 1);
-    constexpr int SLOTS = kThreads / P::TPR;
+    constexpr int SLOTS = P::THREADS / P::TPR;
     // iterations for the rows this tile actually holds (CTA-uniform)
     const int iters = max(0, row_end - row0 + SLOTS - 1) / SLOTS;
 
@@ -232,7 +232,7 @@ __device__ __forceinline__ void loss_item(const AfParams& p, int b, int tile, un
     __syncthreads();
     if (tid == 0) {
         float4 a = wred[0];
-        for (int w = 1; w < kThreads / 32; ++w) {
+        for (int w = 1; w < P::THREADS / 32; ++w) {
             const float4 c = wred[w];
             lse_merge(a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w, bl2);
         }
@@ -246,7 +246,7 @@ __device__ __forceinline__ void loss_item(const AfParams& p, int b, int tile, un
 }
 
 template <int M, bool HALF>
-__global__ void __launch_bounds__(kThreads, RowPlan<M>::MIN_BLOCKS) af_loss_kernel(AfParams p) {
+__global__ void __launch_bounds__(RowPlan<M>::THREADS, RowPlan<M>::MIN_BLOCKS) af_loss_kernel(AfParams p) {
     extern __shared__ __align__(256) unsigned char smem[];
     for_each_item(p, [&](int b, int tile) { loss_item<M, HALF>(p, b, tile, smem); });
 }
@@ -388,6 +388,7 @@ __device__ __forceinline__ void scatter_row_real(const float2* v, float* acc, co
 template <int M>
 __device__ __forceinline__ void write_grad_partial(const AfParams& p, const Wave& wv, const float2* acc_all,
                                                    float* red, float cs, int tile) {
+    using P = RowPlan<M>;
     const int tid = threadIdx.x;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
@@ -395,13 +396,13 @@ __device__ __forceinline__ void write_grad_partial(const AfParams& p, const Wave
     __syncthreads();
     if (tid == 0) {
         float s = red[0];
-        for (int w = 1; w < kThreads / 32; ++w) s += red[w];
+        for (int w = 1; w < P::THREADS / 32; ++w) s += red[w];
         p.csum[wv.rec_off + tile] = s;
     }
     float2* out = p.gpart + wv.gpart_off + (long long)tile * wv.N;
     if (p.phase_only) {
         const float* acc_r = reinterpret_cast<const float*>(acc_all);
-        for (int n = tid; n < wv.N; n += kThreads) {
+        for (int n = tid; n < wv.N; n += P::THREADS) {
             float a = acc_r[n];
             for (int s = 1; s < p.acc_copies; ++s) a += acc_r[(size_t)s * wv.sN + n];
             if (wv.periodic)  // fold the second copy: index n + N is n mod N
@@ -410,7 +411,7 @@ __device__ __forceinline__ void write_grad_partial(const AfParams& p, const Wave
         }
         return;
     }
-    for (int n = tid; n < wv.N; n += kThreads) {
+    for (int n = tid; n < wv.N; n += P::THREADS) {
         float2 a = acc_all[n];
         for (int s = 1; s < p.acc_copies; ++s) a = cadd(a, acc_all[(size_t)s * wv.sN + n]);
         if (wv.periodic)
@@ -422,7 +423,7 @@ __device__ __forceinline__ void write_grad_partial(const AfParams& p, const Wave
 template <int M, bool HALF>
 __device__ __forceinline__ void backward_item(const AfParams& p, int b, int tile, unsigned char* smem) {
     using P = RowPlan<M>;
-    constexpr int SLOTS = kThreads / P::TPR;
+    constexpr int SLOTS = P::THREADS / P::TPR;
     // the waveform's parameters live in shared memory (CTA-uniform), so they
     // are re-read after barriers instead of occupying registers
     __shared__ Wave s_wave;
@@ -436,7 +437,7 @@ __device__ __forceinline__ void backward_item(const AfParams& p, int b, int tile
                                           acc_region_bytes(p));
 
     const int tid = threadIdx.x, slot = tid / P::TPR, t = tid % P::TPR;
-    for (int i = tid; i < (int)(acc_region_bytes(p) / sizeof(float2)); i += kThreads)
+    for (int i = tid; i < (int)(acc_region_bytes(p) / sizeof(float2)); i += P::THREADS)
         acc_all[i] = make_float2(0.0f, 0.0f);
     const float E = load_signal(wv, s_sm, red);  // includes __syncthreads
     const float invE2 = 1.0f / (E * E);
@@ -505,7 +506,7 @@ __device__ __forceinline__ void backward_item(const AfParams& p, int b, int tile
 }
 
 template <int M, bool HALF>
-__global__ void __launch_bounds__(kThreads, RowPlan<M>::MIN_BLOCKS) af_backward_kernel(AfParams p) {
+__global__ void __launch_bounds__(RowPlan<M>::THREADS, RowPlan<M>::MIN_BLOCKS) af_backward_kernel(AfParams p) {
     extern __shared__ __align__(256) unsigned char smem[];
     for_each_item(p, [&](int b, int tile) { backward_item<M, HALF>(p, b, tile, smem); });
 }
@@ -519,7 +520,7 @@ __global__ void __launch_bounds__(kThreads, RowPlan<M>::MIN_BLOCKS) af_backward_
 template <int M, bool HALF>
 __device__ __forceinline__ void match_item(const AfParams& p, int b, int tile, unsigned char* smem) {
     using P = RowPlan<M>;
-    constexpr int SLOTS = kThreads / P::TPR;
+    constexpr int SLOTS = P::THREADS / P::TPR;
     __shared__ Wave s_wave;
     if (threadIdx.x == 0) s_wave = wave_of(p, b);
     __syncthreads();
@@ -530,7 +531,7 @@ __device__ __forceinline__ void match_item(const AfParams& p, int b, int tile, u
     float* red = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(acc_all) +
                                           acc_region_bytes(p));
     const int tid = threadIdx.x, slot = tid / P::TPR, t = tid % P::TPR;
-    for (int i = tid; i < (int)(acc_region_bytes(p) / sizeof(float2)); i += kThreads)
+    for (int i = tid; i < (int)(acc_region_bytes(p) / sizeof(float2)); i += P::THREADS)
         acc_all[i] = make_float2(0.0f, 0.0f);
     const float E = load_signal(wv, s_sm, red);  // includes __syncthreads
     const float invE2 = 1.0f / (E * E);
@@ -603,14 +604,14 @@ __device__ __forceinline__ void match_item(const AfParams& p, int b, int tile, u
     __syncthreads();
     if (tid == 0) {
         float s = red[64];
-        for (int w = 1; w < kThreads / 32; ++w) s += red[64 + w];
+        for (int w = 1; w < P::THREADS / 32; ++w) s += red[64 + w];
         p.mpart[wv.rec_off + tile] = s;
     }
     write_grad_partial<M>(p, wv, acc_all, red, csum, tile);
 }
 
 template <int M, bool HALF>
-__global__ void __launch_bounds__(kThreads, RowPlan<M>::MIN_BLOCKS) af_match_kernel(AfParams p) {
+__global__ void __launch_bounds__(RowPlan<M>::THREADS, RowPlan<M>::MIN_BLOCKS) af_match_kernel(AfParams p) {
     extern __shared__ __align__(256) unsigned char smem[];
     for_each_item(p, [&](int b, int tile) { match_item<M, HALF>(p, b, tile, smem); });
 }
@@ -671,9 +672,9 @@ __device__ __forceinline__ float slot_sum(float x, float* scratch, int slot) {
 //   dSV/ds*[n] = sum_g dSV/dP[g] S[g] exp(+j 2 pi g n / N)  (adjoint DFT, run
 //                as conj(DFT(conj(.))) on the same transform instance)
 template <int M>
-__global__ void __launch_bounds__(kThreads, RowPlan<M>::MIN_BLOCKS) spectral_kernel(SpecParams q) {
+__global__ void __launch_bounds__(RowPlan<M>::THREADS, RowPlan<M>::MIN_BLOCKS) spectral_kernel(SpecParams q) {
     using P = RowPlan<M>;
-    constexpr int SLOTS = kThreads / P::TPR;
+    constexpr int SLOTS = P::THREADS / P::TPR;
     extern __shared__ __align__(256) unsigned char smem[];
     float2* bufs = reinterpret_cast<float2*>(smem);
     float* red = reinterpret_cast<float*>(smem + row_buffer_bytes<M>());
@@ -756,12 +757,12 @@ __global__ void __launch_bounds__(kThreads, RowPlan<M>::MIN_BLOCKS) spectral_ker
 template <int M>
 cudaError_t run_spectral_m(const SpecParams& q, cudaStream_t st) {
     using P = RowPlan<M>;
-    constexpr int SLOTS = kThreads / P::TPR;
+    constexpr int SLOTS = P::THREADS / P::TPR;
     const size_t smem = row_buffer_bytes<M>() + kRedBytes;
     cudaError_t e = cudaFuncSetAttribute(spectral_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)((q.B + SLOTS - 1) / SLOTS);
-    spectral_kernel<M><<<grid, kThreads, smem, st>>>(q);
+    spectral_kernel<M><<<grid, P::THREADS, smem, st>>>(q);
     return cudaGetLastError();
 }
 
@@ -776,9 +777,9 @@ cudaError_t run_spectral_m(const SpecParams& q, cudaStream_t st) {
 // s.  Five transforms per waveform; Re(DFT(G)) waits in shared memory while
 // S is transformed again.
 template <int M>
-__global__ void __launch_bounds__(kThreads, RowPlan<M>::MIN_BLOCKS) composite_kernel(CompParams q) {
+__global__ void __launch_bounds__(RowPlan<M>::THREADS, RowPlan<M>::MIN_BLOCKS) composite_kernel(CompParams q) {
     using P = RowPlan<M>;
-    constexpr int SLOTS = kThreads / P::TPR;
+    constexpr int SLOTS = P::THREADS / P::TPR;
     extern __shared__ __align__(256) unsigned char smem[];
     float2* bufs = reinterpret_cast<float2*>(smem);
     float* stash = reinterpret_cast<float*>(smem + row_buffer_bytes<M>());
@@ -905,13 +906,13 @@ __global__ void __launch_bounds__(kThreads, RowPlan<M>::MIN_BLOCKS) composite_ke
 template <int M>
 cudaError_t run_composite_m(const CompParams& q, cudaStream_t st) {
     using P = RowPlan<M>;
-    constexpr int SLOTS = kThreads / P::TPR;
+    constexpr int SLOTS = P::THREADS / P::TPR;
     const size_t smem = row_buffer_bytes<M>() + (size_t)SLOTS * M * sizeof(float) + kRedBytes;
     if (smem > kMaxSmem) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(composite_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)((q.B + SLOTS - 1) / SLOTS);
-    composite_kernel<M><<<grid, kThreads, smem, st>>>(q);
+    composite_kernel<M><<<grid, P::THREADS, smem, st>>>(q);
     return cudaGetLastError();
 }
 
@@ -938,8 +939,8 @@ cudaError_t run_composite_m(const CompParams& q, cudaStream_t st) {
 template <int M, bool HALF>
 __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, unsigned char* smem) {
     using P = RowPlan<M>;
-    constexpr int SLOTS = kThreads / P::TPR;
-    constexpr int NW = kThreads / 32;
+    constexpr int SLOTS = P::THREADS / P::TPR;
+    constexpr int NW = P::THREADS / 32;
     // the waveform's parameters live in shared memory (CTA-uniform), so they
     // are re-read after barriers instead of occupying registers
     __shared__ Wave s_wave;
@@ -951,11 +952,11 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
     float2* acc_all = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(sig_len(p)) + row_buffer_bytes<M>());
     float* red = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(acc_all) +
                                           acc_region_bytes(p));
-    // red: [0,8) reductions, [8,16) slot-max scratch (TPR > 32), [64, 64+SLOTS) final slot shifts
-    // (SLOTS <= 32 here unless M <= 64, where the shifts live in registers only), [128, 160) float4s
+    // red: [0,16) reductions, [32,48) slot-max scratch (TPR > 32), [64, 64+SLOTS) final slot shifts
+    // (SLOTS <= 64), [128, 128 + 4 NW) float4s
 
     const int tid = threadIdx.x, slot = tid / P::TPR, t = tid % P::TPR;
-    for (int i = tid; i < (int)(acc_region_bytes(p) / sizeof(float2)); i += kThreads)
+    for (int i = tid; i < (int)(acc_region_bytes(p) / sizeof(float2)); i += P::THREADS)
         acc_all[i] = make_float2(0.0f, 0.0f);
     const float E = load_signal(wv, s_sm, red);  // includes __syncthreads
     // the item's constants live in shared memory and are re-read after each
@@ -1060,7 +1061,7 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
                         tmx[w & 1] = fmaxf(tmx[w & 1], wt > 0.0f ? a2 : -CUDART_INF_F);
                     });
                 }
-                const float rmx = fixed ? mx : slot_max<P::TPR>(fmaxf(tmx[0], tmx[1]), red + 8, slot);
+                const float rmx = fixed ? mx : slot_max<P::TPR>(fmaxf(tmx[0], tmx[1]), red + 32, slot);
                 if (rmx > mx) {  // slot-uniform
                     const float f = ex2a((mx - rmx) * bl2);  // 0 while mx = -inf
                     zs *= f;
@@ -1165,46 +1166,51 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
 }
 
 template <int M, bool HALF>
-__global__ void __launch_bounds__(kThreads, RowPlan<M>::MIN_BLOCKS) af_fused_kernel(AfParams p) {
+__global__ void __launch_bounds__(RowPlan<M>::THREADS, RowPlan<M>::MIN_BLOCKS) af_fused_kernel(AfParams p) {
     extern __shared__ __align__(256) unsigned char smem[];
     for_each_item(p, [&](int b, int tile) { fused_item<M, HALF>(p, b, tile, smem); });
 }
 
 // ---------------------------------------------------------- host launchers
-template <class K>
+template <int M, class K>
 static cudaError_t launch_rows(K kernel, size_t smem, const AfParams& p, cudaStream_t st) {
+    using P = RowPlan<M>;
     if (smem > kMaxSmem) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     long long grid = (long long)p.B * p.tiles;
-    if (p.items) {  // persistent: one CTA per SM (the row kernels fill an SM each)
-        int dev = 0, sms = kSmsTarget;
+    if (p.items) {  // persistent: as many CTAs as fit on the SMs at once
+        int dev = 0, sms = kSmsTarget, per_sm = 1;
         if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        grid = p.n_items < sms ? p.n_items : sms;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, P::THREADS, smem) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        const long long cap = (long long)sms * per_sm;
+        grid = p.n_items < cap ? p.n_items : cap;
         if (grid < 1) return cudaSuccess;
     }
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    kernel<<<(unsigned)grid, kThreads, smem, st>>>(p);
+    kernel<<<(unsigned)grid, P::THREADS, smem, st>>>(p);
     return cudaGetLastError();
 }
 
 template <int M>
 cudaError_t run_forward_m(const AfParams& p, cudaStream_t st) {
     const size_t smem = forward_smem<M>(sig_len(p));
-    if (2 * p.N <= M) return launch_rows(af_forward_kernel<M, true>, smem, p, st);
-    return launch_rows(af_forward_kernel<M, false>, smem, p, st);
+    if (2 * p.N <= M) return launch_rows<M>(af_forward_kernel<M, true>, smem, p, st);
+    return launch_rows<M>(af_forward_kernel<M, false>, smem, p, st);
 }
 template <int M>
 cudaError_t run_loss_m(const AfParams& p, cudaStream_t st) {
     const size_t smem = forward_smem<M>(sig_len(p));
-    if (2 * p.N <= M) return launch_rows(af_loss_kernel<M, true>, smem, p, st);
-    return launch_rows(af_loss_kernel<M, false>, smem, p, st);
+    if (2 * p.N <= M) return launch_rows<M>(af_loss_kernel<M, true>, smem, p, st);
+    return launch_rows<M>(af_loss_kernel<M, false>, smem, p, st);
 }
 template <int M>
 cudaError_t run_backward_m(const AfParams& p, cudaStream_t st) {
-    if (p.acc_copies < 1 || (256 / RowPlan<M>::TPR) % p.acc_copies) return cudaErrorInvalidConfiguration;
+    if (p.acc_copies < 1 || (RowPlan<M>::THREADS / RowPlan<M>::TPR) % p.acc_copies) return cudaErrorInvalidConfiguration;
     const size_t smem = backward_smem<M>(sig_len(p), p.acc_copies, p.phase_only);
-    return launch_rows(af_backward_kernel<M, false>, smem, p, st);
+    return launch_rows<M>(af_backward_kernel<M, false>, smem, p, st);
 }
 
 // The kernels that run two transforms per row use one transform instance for
@@ -1214,18 +1220,18 @@ cudaError_t run_backward_m(const AfParams& p, cudaStream_t st) {
 // lag product and in the scatter.
 template <int M>
 cudaError_t run_match_m(const AfParams& p, cudaStream_t st) {
-    if (p.acc_copies < 1 || (256 / RowPlan<M>::TPR) % p.acc_copies) return cudaErrorInvalidConfiguration;
+    if (p.acc_copies < 1 || (RowPlan<M>::THREADS / RowPlan<M>::TPR) % p.acc_copies) return cudaErrorInvalidConfiguration;
     const size_t smem = backward_smem<M>(sig_len(p), p.acc_copies, p.phase_only);
-    if (2 * p.N <= M && !p.periodic) return launch_rows(af_match_kernel<M, true>, smem, p, st);
-    return launch_rows(af_match_kernel<M, false>, smem, p, st);
+    if (2 * p.N <= M && !p.periodic) return launch_rows<M>(af_match_kernel<M, true>, smem, p, st);
+    return launch_rows<M>(af_match_kernel<M, false>, smem, p, st);
 }
 
 template <int M>
 cudaError_t run_fused_m(const AfParams& p, cudaStream_t st) {
-    if (p.acc_copies < 1 || (256 / RowPlan<M>::TPR) % p.acc_copies) return cudaErrorInvalidConfiguration;
+    if (p.acc_copies < 1 || (RowPlan<M>::THREADS / RowPlan<M>::TPR) % p.acc_copies) return cudaErrorInvalidConfiguration;
     const size_t smem = backward_smem<M>(sig_len(p), p.acc_copies, p.phase_only);
-    if (2 * p.N <= M) return launch_rows(af_fused_kernel<M, true>, smem, p, st);
-    return launch_rows(af_fused_kernel<M, false>, smem, p, st);
+    if (2 * p.N <= M) return launch_rows<M>(af_fused_kernel<M, true>, smem, p, st);
+    return launch_rows<M>(af_fused_kernel<M, false>, smem, p, st);
 }
 
 }  // namespace graf

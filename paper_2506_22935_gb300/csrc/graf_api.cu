@@ -246,7 +246,7 @@ static graf_status_t af_loss_backward_impl(const Mode& md, const void* x, graf_i
     // on the PSL path with a running log-sum-exp shift each row slot needs its
     // own gradient accumulator (it rescales it); a fixed shift rescales nothing
     const bool fixed = graf::lse_fixed_shift(kind == GRAF_IN_PHASE ? 1 : 0, l.eps, l.beta, N) > 0.0f;
-    if (l.w_psl != 0.0f && !fixed && acc < graf::kThreads / graf::tpr_of(M)) f.fused = false;
+    if (l.w_psl != 0.0f && !fixed && acc < graf::slots_of(M)) f.fused = false;
     if (!f.fused) {
         s = af_loss_impl(md, x, kind, B, N, M, w, l, out8, workspace, workspace_bytes, stream);
         if (s != GRAF_OK) return s;

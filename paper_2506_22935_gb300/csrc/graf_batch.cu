@@ -73,7 +73,7 @@ graf_status_t layout(graf_batch_plan_s* P) {
     P->total_items = 0;
     P->total_gpart = 0;
     for (Bucket& bk : P->buckets) {
-        const int slots = graf::kThreads / graf::tpr_of(bk.M);
+        const int slots = graf::slots_of(bk.M);
         const int rpt = slots * bk.rps;
         bk.items.clear();
         std::vector<std::pair<long long, int2>> cost;
@@ -318,7 +318,7 @@ static graf_status_t create_plan(int32_t B, const int32_t* N_host, const int32_t
         // (it rescales the accumulators) and the slots cannot each own an
         // accumulator.  The fused and the two-pass waveforms of one M go to
         // separate buckets, so one of the latter does not slow the rest.
-        const int slots = graf::kThreads / graf::tpr_of(M);
+        const int slots = graf::slots_of(M);
         std::vector<int> fused, two_pass;
         for (int b : all) {
             WaveDesc& d = P->waves[b];
@@ -427,7 +427,7 @@ graf_status_t graf_batch_plan_info(graf_batch_plan_t P, int32_t* n_buckets, int3
     for (int i = 0; i < (int)P->buckets.size() && i < capacity; ++i) {
         const Bucket& bk = P->buckets[i];
         if (M_out) M_out[i] = bk.M;
-        if (rows_per_tile_out) rows_per_tile_out[i] = bk.rps * (graf::kThreads / graf::tpr_of(bk.M));
+        if (rows_per_tile_out) rows_per_tile_out[i] = bk.rps * graf::slots_of(bk.M);
         if (items_out) items_out[i] = (int32_t)bk.items.size();
         if (fused_out) fused_out[i] = bk.fused ? 1 : 0;
     }

@@ -186,17 +186,18 @@ __host__ __device__ __forceinline__ void dft(float2* v) {
 template <int M>
 struct RowPlan {
     static_assert(M >= 8 && M <= 16384 && (M & (M - 1)) == 0, "M must be a power of two in [8,16384]");
-    // values per thread: 32 for M in [128, 8192], where half the registers let
-    // two CTAs (16 warps) share an SM (from M = 2048 on at the price of a
-    // third pass); 64 for M = 16384 (a row of 512 threads would not fit a
-    // CTA); M below 64
-    static constexpr int VALS = (M >= 128 && M <= 8192) ? 32 : (M < 64 ? M : 64);
+    // values per thread: 32 from M = 128 on, so that a thread needs at most
+    // 128 registers and 16 warps share an SM (two CTAs of 256 threads, or one
+    // of 512 threads for M = 16384, whose row spans 512 threads); a third FFT
+    // pass from M = 2048 on is the price.  64 for M = 64, M below.
+    static constexpr int VALS = M >= 128 ? 32 : (M < 64 ? M : 64);
     static constexpr int TPR = M / VALS;           // threads per row
+    static constexpr int THREADS = TPR > 256 ? TPR : 256;  // threads per CTA
     static constexpr int NPASS = TPR == 1 ? 1 : (TPR <= VALS ? 2 : 3);
     static constexpr int R0 = VALS;
     static constexpr int R1 = NPASS == 1 ? 1 : (NPASS == 2 ? TPR : 16);
     static constexpr int R2 = NPASS == 3 ? TPR / 16 : 1;
-    static constexpr int MIN_BLOCKS = VALS == 32 ? 2 : 1;  // CTAs per SM the registers allow
+    static constexpr int MIN_BLOCKS = (VALS == 32 && THREADS == 256) ? 2 : 1;  // CTAs per SM the registers allow
     // shared-memory row buffer (float2 units): one pad slot per VALS values
     // keeps the stride-VALS stores of the first pass free of bank conflicts
     static constexpr int PAD = VALS < 32 ? 64 : VALS;

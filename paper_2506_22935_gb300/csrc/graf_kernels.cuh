@@ -10,7 +10,7 @@
 
 namespace graf {
 
-constexpr int kThreads = 256;     // threads per CTA of the row kernels
+constexpr int kThreads = 256;     // threads per CTA of the row kernels (RowPlan<M>::THREADS for the largest M)
 constexpr int kSmsTarget = 152;   // GB300 SM count, used to size tiles
 
 // Per-waveform parameters of a batch of unequal waveforms (device table, one
@@ -198,7 +198,10 @@ struct Tiling {
     int r_lo, r_hi, nrows, slots, rows_per_tile, tiles;
 };
 
-inline int tpr_of(int M) { return M < 64 ? 1 : M / 64; }
+// Host mirrors of RowPlan<M>: threads per row and per CTA.
+inline int tpr_of(int M) { return M >= 128 ? M / 32 : (M < 64 ? 1 : M / 64); }
+inline int threads_of(int M) { return tpr_of(M) > 256 ? tpr_of(M) : 256; }
+inline int slots_of(int M) { return threads_of(M) / tpr_of(M); }
 
 constexpr size_t kMaxSmem = 232448;  // opt-in dynamic shared memory per CTA (227 KB)
 constexpr size_t kRedBytes = 1024;   // block-reduction scratch
@@ -210,7 +213,7 @@ __host__ __device__ constexpr size_t smem_signal_bytes(int N) {
 template <int M>
 __host__ __device__ constexpr size_t row_buffer_bytes() {
     using P = RowPlan<M>;
-    return (((size_t)P::SMEM_ROW * (P::SPLIT ? sizeof(float) : sizeof(float2)) * (256 / P::TPR)) + 255) &
+    return (((size_t)P::SMEM_ROW * (P::SPLIT ? sizeof(float) : sizeof(float2)) * (P::THREADS / P::TPR)) + 255) &
            ~(size_t)255;
 }
 template <int M>
@@ -228,7 +231,7 @@ constexpr size_t backward_smem(int N, int acc_copies, int real = 0) {
 // in shared memory; 0 if even one does not.
 template <int M>
 int backward_acc_copies(int N, int real = 0) {
-    for (int a = 256 / RowPlan<M>::TPR; a >= 1; a /= 2)
+    for (int a = RowPlan<M>::THREADS / RowPlan<M>::TPR; a >= 1; a /= 2)
         if (backward_smem<M>(N, a, real) <= kMaxSmem) return a;
     return 0;
 }
@@ -257,8 +260,10 @@ inline Tiling make_tiling_rows(int B, int M, int r_lo, int r_hi) {
     T.r_lo = r_lo;
     T.r_hi = r_hi;
     T.nrows = T.r_hi - T.r_lo + 1;
-    T.slots = kThreads / tpr_of(M);
-    int rps = 8;
+    T.slots = slots_of(M);
+    // up to 512 rows per tile over 64 slots' worth of threads (16 rows per slot
+    // when a row has 32 values per thread, 8 when it has 64)
+    int rps = M >= 128 ? 16 : 8;
     while (rps > 1) {
         long long tiles = (T.nrows + (long long)T.slots * rps - 1) / ((long long)T.slots * rps);
         if ((long long)B * tiles >= 4LL * kSmsTarget) break;
@@ -299,7 +304,7 @@ __device__ __forceinline__ float load_signal(const Wave& wv, float2* s_sm, float
     float e = 0.0f;
     if (wv.kind == 1) {
         const float* ph = static_cast<const float*>(wv.x);
-        for (int n = tid; n < wv.N; n += kThreads) {
+        for (int n = tid; n < wv.N; n += (int)blockDim.x) {
             float sn, cs;
             sincosf(__ldg(ph + n), &sn, &cs);
             const float2 v = make_float2(cs, wv.pconj ? -sn : sn);
@@ -309,7 +314,7 @@ __device__ __forceinline__ float load_signal(const Wave& wv, float2* s_sm, float
         }
     } else {
         const float2* xs = static_cast<const float2*>(wv.x);
-        for (int n = tid; n < wv.N; n += kThreads) {
+        for (int n = tid; n < wv.N; n += (int)blockDim.x) {
             float2 v = __ldg(xs + n);
             if (wv.pconj) v.y = -v.y;
             s_sm[n] = v;
@@ -323,7 +328,7 @@ __device__ __forceinline__ float load_signal(const Wave& wv, float2* s_sm, float
     __syncthreads();
     float E = 0.0f;
 #pragma unroll
-    for (int w = 0; w < kThreads / 32; ++w) E += red[w];
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) E += red[w];
     __syncthreads();
     return E;
 }
