@@ -497,7 +497,7 @@ def run_optim(args):
                          "algorithmic_flop_per_step": alg_step,
                          "peak_source": f"FP32 FMA peak at {sm_max:.0f} MHz ({src})"},
             "isl_median_start": float(np.median(hist[0])), "isl_median_end": float(np.median(hist[-1])),
-            "cpu_baseline": cpu, "gpu_launches": 4 * STEPS * runs, "clocks": clk.summary()}
+            "cpu_baseline": cpu, "gpu_launches": 5 * STEPS * runs, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
 
