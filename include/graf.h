@@ -3,7 +3,8 @@
  * library: the discrete ambiguity function (AF) of a complex waveform, its
  * fused sidelobe losses and their Wirtinger-calculus gradient.
  *
- * Method (Bara et al., "GRAF: differentiable radar ambiguity functions"):
+ * Method: GRAF, from M. Bara, "Differentiable Radar Ambiguity Functions:
+ * Mathematical Formulation and Computational Implementation" (arXiv 2506.22935):
  *   lag product   R[k,n] = s[n] conj(s[n-k])                        Sec. 4.1, Eq. 8
  *                 aperiodic: s[n] = 0 outside [0,N), k = -(N-1)..N-1 (the
  *                 non-periodic extension listed in Sec. 8.6); the paper's own

@@ -298,7 +298,8 @@ typedef struct {
 
 /* For each delay row k of the window:
  *   G_R[k,n] = sum_m G[k,m] conj(W[(m n) mod M])   (adjoint of Eq. 11: the
- *              unnormalised inverse DFT of Sec. 4.2 "IFFT operation (linear)")
+ *              unnormalised inverse DFT of the linear inverse-transform step
+ *              of Sec. 4.2)
  *   and the product rule on R[k,n] = s[n] conj(s[n-k]) (Eq. 8):
  *   dL/ds*[n]   += G_R[k,n] s[n-k]          (through R*[k,n])
  *   dL/ds*[n-k] += conj(G_R[k,n]) s[n]       (through R[k,n]).

@@ -2,7 +2,8 @@
 // losses, backward with recomputation) as templates over the row length M;
 // graf_af_m*.cu instantiate them, a few M per translation unit.
 //
-// One CTA = 256 threads = 256/TPR row slots; a CTA owns one waveform b and a
+// One CTA = RowPlan<M>::THREADS threads (256; 512 for M = 16384) = THREADS/TPR
+// row slots; a CTA owns one waveform b and a
 // tile of consecutive delay rows k >= 0.  Per row a slot builds the aperiodic
 // lag product (Eq. 8) from the waveform in shared memory, transforms it
 // (Eq. 11) with row_fft, and consumes the result in registers.  Rows k < 0

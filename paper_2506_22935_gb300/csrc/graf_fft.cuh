@@ -3,10 +3,12 @@
 //
 // Computes X[m] = sum_n x[n] exp(-2 pi j m n / M) (paper Eq. 11, the FFT over
 // the time axis of each delay row) and its adjoint sum_m G[m] exp(+2 pi j m n
-// / M) (Sec. 4.2: "IFFT operation (linear)", unnormalised).
+// / M) (the linear inverse-transform step of the backward pass, Sec. 4.2,
+// unnormalised).
 //
-// Layout: a row of length M is owned by TPR = M / VALS threads, VALS = min(M,
-// 64) complex values per thread in registers.  On entry AND on exit thread t
+// Layout: a row of length M is owned by TPR = M / VALS threads, VALS = 32
+// complex values per thread in registers (64 for M = 64, M below; see
+// RowPlan).  On entry AND on exit thread t
 // holds element t + TPR * w in register w ("natural strided" layout), so the
 // lag-product builder, the loss epilogue and the gradient scatter all index
 // the same way and the forward and inverse transforms chain without any
@@ -14,12 +16,12 @@
 //
 // Algorithm: Stockham auto-sort passes (Cooley-Tukey with a self-sorting
 // output index, as in Govindaraju et al., SC'08), radices R_0 = VALS, then
-// M / VALS split into radices dividing 64.  Pass p with radix R and span Ns
+// M / VALS as one radix (M <= 1024) or 16 x (M / 512).  Pass p with radix R and span Ns
 // takes, for butterfly j, inputs x[j + r M/R], multiplies input r by
 // W_(Ns R)^((j mod Ns) r), does an R-point DFT in registers and writes
 // output r to (j / Ns) Ns R + (j mod Ns) + r Ns.  The first pass reads
 // registers, the last keeps its outputs in registers; only the exchanges
-// between passes go through shared memory (one for M <= 4096).  Each
+// between passes go through shared memory (one for M <= 1024, two above).  Each
 // R-point DFT is itself split A x B (A in {2,4,8}) with compile-time
 // twiddles, so W_R^q folds into immediates.
 #pragma once
