@@ -204,6 +204,7 @@ inline int threads_of(int M) { return tpr_of(M) > 256 ? tpr_of(M) : 256; }
 inline int slots_of(int M) { return threads_of(M) / tpr_of(M); }
 
 constexpr size_t kMaxSmem = 232448;  // opt-in dynamic shared memory per CTA (227 KB)
+constexpr size_t kSmemPerSm = 233472;  // shared memory per SM (228 KB)
 constexpr size_t kRedBytes = 1024;   // block-reduction scratch
 
 template <int M>
@@ -227,11 +228,20 @@ constexpr size_t backward_smem(int N, int acc_copies, int real = 0) {
     return smem_signal_bytes<M>(N) + row_buffer_bytes<M>() +
            (((size_t)acc_copies * N * (real ? sizeof(float) : sizeof(float2)) + 255) & ~(size_t)255) + kRedBytes;
 }
-// Largest power-of-two number of gradient accumulators (<= slots) that fits
-// in shared memory; 0 if even one does not.
+// Number of gradient accumulators per CTA (a power of two <= slots; slots
+// sharing one take turns in the scatter): the largest that still lets the
+// registers' number of CTAs share an SM, if that leaves at most two turns,
+// else the largest that fits in shared memory; 0 if even one does not.
 template <int M>
 int backward_acc_copies(int N, int real = 0) {
-    for (int a = RowPlan<M>::THREADS / RowPlan<M>::TPR; a >= 1; a /= 2)
+    constexpr int slots = RowPlan<M>::THREADS / RowPlan<M>::TPR;
+    constexpr int per_sm = RowPlan<M>::MIN_BLOCKS;
+    if (per_sm > 1) {
+        const size_t budget = kSmemPerSm / per_sm - 1024;  // 1 KB per CTA is reserved
+        for (int a = slots; a >= 1 && 2 * a >= slots; a /= 2)
+            if (backward_smem<M>(N, a, real) <= budget) return a;
+    }
+    for (int a = slots; a >= 1; a /= 2)
         if (backward_smem<M>(N, a, real) <= kMaxSmem) return a;
     return 0;
 }
