@@ -336,20 +336,20 @@ static size_t smem_need(int M, int N, int which) {
 
 size_t row_kernel_smem(int M, int N, int which) { return smem_need(M, N, which); }
 
-int acc_copies_for(int M, int N, int real) {
+int acc_copies_for(int M, int N, int real, int per) {
     switch (M) {
-        case 8: return backward_acc_copies<8>(N, real);
-        case 16: return backward_acc_copies<16>(N, real);
-        case 32: return backward_acc_copies<32>(N, real);
-        case 64: return backward_acc_copies<64>(N, real);
-        case 128: return backward_acc_copies<128>(N, real);
-        case 256: return backward_acc_copies<256>(N, real);
-        case 512: return backward_acc_copies<512>(N, real);
-        case 1024: return backward_acc_copies<1024>(N, real);
-        case 2048: return backward_acc_copies<2048>(N, real);
-        case 4096: return backward_acc_copies<4096>(N, real);
-        case 8192: return backward_acc_copies<8192>(N, real);
-        case 16384: return backward_acc_copies<16384>(N, real);
+        case 8: return backward_acc_copies<8>(N, real, per);
+        case 16: return backward_acc_copies<16>(N, real, per);
+        case 32: return backward_acc_copies<32>(N, real, per);
+        case 64: return backward_acc_copies<64>(N, real, per);
+        case 128: return backward_acc_copies<128>(N, real, per);
+        case 256: return backward_acc_copies<256>(N, real, per);
+        case 512: return backward_acc_copies<512>(N, real, per);
+        case 1024: return backward_acc_copies<1024>(N, real, per);
+        case 2048: return backward_acc_copies<2048>(N, real, per);
+        case 4096: return backward_acc_copies<4096>(N, real, per);
+        case 8192: return backward_acc_copies<8192>(N, real, per);
+        case 16384: return backward_acc_copies<16384>(N, real, per);
         default: return 0;
     }
 }

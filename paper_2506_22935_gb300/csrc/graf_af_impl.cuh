@@ -284,10 +284,13 @@ __global__ void __launch_bounds__(RowPlan<M>::THREADS, RowPlan<M>::MIN_BLOCKS) a
 // Slots that share an accumulator (turns > 1) take turns, CTA-wide.
 // CONJ: v holds Y = conj(G_R) (the adjoint computed as conj(DFT(conj(G)))):
 // G_R s = cmulc(s, Y) and conj(G_R) s = Y s.
+// wrap (periodic AF, lag k - N, N = M a power of two): the second index n - k
+// lies in [N - k, 2N - k) and is taken mod N, so one N-length accumulator
+// serves both terms.
 template <int M, bool HALF, bool CONJ = false>
 __device__ __forceinline__ void scatter_row(const float2* v, float2* acc, const float2* s_sm, int N,
                                             int k, int t, bool active, int slot, int turns,
-                                            int my_turn) {
+                                            int my_turn, bool wrap) {
     using P = RowPlan<M>;
     constexpr int WN = HALF ? P::VALS / 2 : P::VALS;
     auto scatter_a = [&]() {
@@ -301,14 +304,18 @@ __device__ __forceinline__ void scatter_row(const float2* v, float2* acc, const 
             }
         });
     };
+    // (N = M, a power of two, for the periodic AF; HALF rows have 2N <= M,
+    // which no periodic row has)
+    const int wrap_mask = (!HALF && wrap) ? N - 1 : -1;
     auto scatter_b = [&]() {
         if (!active) return;
         sfor<0, WN>([&](auto w) {
             const int n = t + P::TPR * decltype(w)::value;
             if ((unsigned)(n - k) < (unsigned)(N - k)) {
-                const float2 a = acc[n - k];
+                const int i = HALF ? n - k : (n - k) & wrap_mask;
+                const float2 a = acc[i];
                 const float2 g = CONJ ? cmul(v[w], s_sm[n]) : cmulc(s_sm[n], v[w]);
-                acc[n - k] = cadd(a, g);
+                acc[i] = cadd(a, g);
             }
         });
     };
@@ -339,7 +346,7 @@ __device__ __forceinline__ void scatter_row(const float2* v, float2* acc, const 
 template <int M, bool HALF>
 __device__ __forceinline__ void scatter_row_real(const float2* v, float* acc, const float2* s_sm, int N,
                                                  int k, int t, bool active, int slot, int turns,
-                                                 int my_turn) {
+                                                 int my_turn, bool wrap) {
     using P = RowPlan<M>;
     constexpr int WN = HALF ? P::VALS / 2 : P::VALS;
     float q[WN];
@@ -358,11 +365,15 @@ __device__ __forceinline__ void scatter_row_real(const float2* v, float* acc, co
             if ((unsigned)(n - k) < (unsigned)(N - k)) acc[n] += q[w];
         });
     };
+    const int wrap_mask = (!HALF && wrap) ? N - 1 : -1;  // periodic: index mod N (N = M)
     auto scatter_b = [&]() {
         if (!active) return;
         sfor<0, WN>([&](auto w) {
             const int n = t + P::TPR * decltype(w)::value;
-            if ((unsigned)(n - k) < (unsigned)(N - k)) acc[n - k] -= q[w];
+            if ((unsigned)(n - k) < (unsigned)(N - k)) {
+                const int i = HALF ? n - k : (n - k) & wrap_mask;
+                acc[i] -= q[w];
+            }
         });
     };
     if (turns == 1) {
@@ -405,18 +416,14 @@ __device__ __forceinline__ void write_grad_partial(const AfParams& p, const Wave
         const float* acc_r = reinterpret_cast<const float*>(acc_all);
         for (int n = tid; n < wv.N; n += P::THREADS) {
             float a = acc_r[n];
-            for (int s = 1; s < p.acc_copies; ++s) a += acc_r[(size_t)s * wv.sN + n];
-            if (wv.periodic)  // fold the second copy: index n + N is n mod N
-                for (int s = 0; s < p.acc_copies; ++s) a += acc_r[(size_t)s * wv.sN + wv.N + n];
+            for (int s = 1; s < p.acc_copies; ++s) a += acc_r[(size_t)s * wv.N + n];
             out[n] = make_float2(a, 0.0f);
         }
         return;
     }
     for (int n = tid; n < wv.N; n += P::THREADS) {
         float2 a = acc_all[n];
-        for (int s = 1; s < p.acc_copies; ++s) a = cadd(a, acc_all[(size_t)s * wv.sN + n]);
-        if (wv.periodic)
-            for (int s = 0; s < p.acc_copies; ++s) a = cadd(a, acc_all[(size_t)s * wv.sN + wv.N + n]);
+        for (int s = 1; s < p.acc_copies; ++s) a = cadd(a, acc_all[(size_t)s * wv.N + n]);
         out[n] = a;
     }
 }
@@ -456,8 +463,8 @@ __device__ __forceinline__ void backward_item(const AfParams& p, int b, int tile
     // slots sharing an accumulator (when shared memory is short) take turns
     const int turns = SLOTS / p.acc_copies;
     const int my_turn = slot / p.acc_copies;
-    float2* acc = acc_all + (size_t)(slot % p.acc_copies) * wv.sN;
-    float* acc_r = reinterpret_cast<float*>(acc_all) + (size_t)(slot % p.acc_copies) * wv.sN;
+    float2* acc = acc_all + (size_t)(slot % p.acc_copies) * wv.N;
+    float* acc_r = reinterpret_cast<float*>(acc_all) + (size_t)(slot % p.acc_copies) * wv.N;
 
     const int row0 = wv.r_lo + tile * wv.rows_per_tile;
     const int row_end = min(row0 + wv.rows_per_tile, wv.r_hi + 1);
@@ -499,9 +506,11 @@ __device__ __forceinline__ void backward_item(const AfParams& p, int b, int tile
             });
         }
         if (p.phase_only)
-            scatter_row_real<M, HALF>(v, acc_r, s_sm, wv.N, wv.periodic ? k - wv.N : k, t, valid, slot, turns, my_turn);
+            scatter_row_real<M, HALF>(v, acc_r, s_sm, wv.N, wv.periodic ? k - wv.N : k, t, valid, slot, turns,
+                                      my_turn, wv.periodic != 0);
         else
-            scatter_row<M, HALF, true>(v, acc, s_sm, wv.N, wv.periodic ? k - wv.N : k, t, valid, slot, turns, my_turn);
+            scatter_row<M, HALF, true>(v, acc, s_sm, wv.N, wv.periodic ? k - wv.N : k, t, valid, slot, turns,
+                                       my_turn, wv.periodic != 0);
     }
     write_grad_partial<M>(p, wv, acc_all, red, csum, tile);
 }
@@ -542,8 +551,8 @@ __device__ __forceinline__ void match_item(const AfParams& p, int b, int tile, u
     const ColMasks cm = col_masks<M>(wv, t);
     const int turns = SLOTS / p.acc_copies;
     const int my_turn = slot / p.acc_copies;
-    float2* acc = acc_all + (size_t)(slot % p.acc_copies) * wv.sN;
-    float* acc_r = reinterpret_cast<float*>(acc_all) + (size_t)(slot % p.acc_copies) * wv.sN;
+    float2* acc = acc_all + (size_t)(slot % p.acc_copies) * wv.N;
+    float* acc_r = reinterpret_cast<float*>(acc_all) + (size_t)(slot % p.acc_copies) * wv.N;
     const int ncols = wv.m_hi - wv.m_lo + 1;
     const float* tgt = p.target + (size_t)b * (wv.k_hi - wv.k_lo + 1) * ncols;
 
@@ -593,10 +602,10 @@ __device__ __forceinline__ void match_item(const AfParams& p, int b, int tile, u
         }
         if (p.phase_only)
             scatter_row_real<M, HALF>(v, acc_r, s_sm, wv.N, wv.periodic ? k - wv.N : k, t, grad_row, slot, turns,
-                                      my_turn);
+                                      my_turn, wv.periodic != 0);
         else
             scatter_row<M, HALF, true>(v, acc, s_sm, wv.N, wv.periodic ? k - wv.N : k, t, grad_row, slot, turns,
-                                       my_turn);
+                                       my_turn, wv.periodic != 0);
     }
     // the tile's loss partial, fixed order
 #pragma unroll
@@ -980,8 +989,8 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
     constexpr unsigned long long full_mask = P::VALS == 64 ? ~0ull : ((1ull << P::VALS) - 1ull);
     const int turns = SLOTS / p.acc_copies;
     const int my_turn = slot / p.acc_copies;
-    float2* acc = acc_all + (size_t)(slot % p.acc_copies) * wv.sN;
-    float* acc_r = reinterpret_cast<float*>(acc_all) + (size_t)(slot % p.acc_copies) * wv.sN;
+    float2* acc = acc_all + (size_t)(slot % p.acc_copies) * wv.N;
+    float* acc_r = reinterpret_cast<float*>(acc_all) + (size_t)(slot % p.acc_copies) * wv.N;
 
     const int row0 = wv.r_lo + tile * wv.rows_per_tile;
     const int row_end = min(row0 + wv.rows_per_tile, wv.r_hi + 1);
@@ -997,127 +1006,137 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
         const int k = row0 + slot + it * SLOTS;
         const bool valid = k < row_end;
         const bool grad_row = valid && k > wv.defer_hi && !(p.phase_only && k == 0);
-        build_lag_row<M, HALF>(v, s_sm, wv.N, wv.periodic ? k - wv.N : k, t, valid);
-        // one transform instance, run twice: the forward DFT, then the adjoint
-        // as conj(DFT(conj(c X))) -- the epilogue writes conj(c X) and the
-        // scatter reads the conjugated result
+        // a warp of several row slots none of which holds a valid row skips
+        // both transforms; it still runs the scatter below, with nothing to
+        // add, so that it joins the CTA's barriers when slots take turns.  Only
+        // the last iteration of a tile can hold such warps.  (A slot of whole
+        // warps already skips the adjoint of an invalid row.)
+        const bool live = P::TPR >= 32 || row0 + (tid >> 5) * (32 / P::TPR) + it * SLOTS < row_end;
+        if (live) {
+            build_lag_row<M, HALF>(v, s_sm, wv.N, wv.periodic ? k - wv.N : k, t, valid);
+            // one transform instance, run twice: the forward DFT, then the adjoint
+            // as conj(DFT(conj(c X))) -- the epilogue writes conj(c X) and the
+            // scatter reads the conjugated result
 #pragma unroll 1
-        for (int ph = 0; ph < 2; ++ph) {
-            row_sync<P::TPR>(slot);
-            row_fft<M, false, false, false>(v, buf, t, slot);
-            if (ph == 1) break;
-            const float invE2 = s_k[0], eps_n = s_k[1], bl2 = s_k[2], cP = s_k[3], cI = s_k[4];
-            const bool psl_mode = wv.w_psl != 0.0f;
-            const float wb = valid ? (float)base_weight(wv, k) : 0.0f;
-            // A row every cell of which carries the same weight (the window
-            // spans all Doppler bins, delay k and/or -k in it, no mainlobe-box
-            // cell) takes the fast path; the test is slot-uniform.
-            const bool in_pos = k >= wv.k_lo && k <= wv.k_hi;
-            const bool in_neg = k > 0 && -k >= wv.k_lo && -k <= wv.k_hi;
-            if (fixed && valid && wv.full_m && k > wv.k_ml && (in_pos || in_neg)) {
-                // accumulate P = sum |X|^2, Z = sum e, Q = sum e |X|^2 and
-                // apply the weight, 1/E^2 and eps once per row; e = exp(beta
-                // (a2 - mx)) from |X|^2 in one FMA; c = Kp (e - e0) + Ki
-                const float wrow = (in_pos && in_neg) ? 2.0f : 1.0f;
-                const float sh = mx * bl2;
-                const float e0 = ex2a(-sh);
-                const float Kp = (grad_row && psl_mode) ? wrow * cP : 0.0f;
-                const float Ki = (grad_row && !psl_mode) ? (wrow - wb) * cI : 0.0f;
-                const float Kc0 = fmaf(-e0, Kp, Ki);
-                const float kexp = s_k[5], kofs = fmaf(eps_n, bl2, -sh);
-                float rP[2] = {0.0f, 0.0f}, rZ[2] = {0.0f, 0.0f}, rQ[2] = {0.0f, 0.0f};
-                float rH[2] = {0.0f, 0.0f};
-                sfor<0, P::VALS>([&](auto w) {
-                    constexpr int h = decltype(w)::value & 1;
-                    const float2 x = v[w];
-                    const float p2 = fmaf(x.x, x.x, x.y * x.y);
-                    const float e = ex2v(fmaf(p2, kexp, kofs));
-                    rH[h] = fmaxf(rH[h], p2);
-                    rP[h] += p2;
-                    rZ[h] += e;
-                    rQ[h] = fmaf(e, p2, rQ[h]);
-                    const float c = fmaf(e, Kp, Kc0);
-                    v[w] = make_float2(c * x.x, -c * x.y);
-                });
-                const float sa2 = fmaf(rP[0] + rP[1], invE2, (float)P::VALS * eps_n);  // sum a2
-                const float Zr = rZ[0] + rZ[1];
-                const float sea2 = fmaf(rQ[0] + rQ[1], invE2, eps_n * Zr);            // sum e a2
-                isl = fmaf(wrow, sa2, isl);
-                zs = fmaf(wrow, Zr, zs);
-                ts = fmaf(wrow, sea2, ts);
-                cs += fmaf(Kp, fmaf(-e0, sa2, sea2), Ki * sa2);
-                hm = fmaxf(hm, fmaf(fmaxf(rH[0], rH[1]), invE2, eps_n));
-            } else {
-                const RowMasks rmk = row_masks(wv, cm, k);
-                const bool uniform = !valid || (rmk.one == full_mask && (rmk.two == 0ull || rmk.two == full_mask));
-                const float wrow = valid ? (rmk.two != 0ull ? 2.0f : (rmk.one != 0ull ? 1.0f : 0.0f)) : 0.0f;
-                // pass 1 (running shift only): largest weighted a2 of the row
-                // (two independent chains)
-                float tmx[2] = {-CUDART_INF_F, -CUDART_INF_F};
-                if (!fixed) {
+            for (int ph = 0; ph < 2; ++ph) {
+                row_sync<P::TPR>(slot);
+                row_fft<M, false, false, false>(v, buf, t, slot);
+                if (ph == 1) break;
+                const float invE2 = s_k[0], eps_n = s_k[1], bl2 = s_k[2], cP = s_k[3], cI = s_k[4];
+                const bool psl_mode = wv.w_psl != 0.0f;
+                const float wb = valid ? (float)base_weight(wv, k) : 0.0f;
+                // A row every cell of which carries the same weight (the window
+                // spans all Doppler bins, delay k and/or -k in it, no mainlobe-box
+                // cell) takes the fast path; the test is slot-uniform.
+                const bool in_pos = k >= wv.k_lo && k <= wv.k_hi;
+                const bool in_neg = k > 0 && -k >= wv.k_lo && -k <= wv.k_hi;
+                if (fixed && valid && wv.full_m && k > wv.k_ml && (in_pos || in_neg)) {
+                    // accumulate P = sum |X|^2, Z = sum e, Q = sum e |X|^2 and
+                    // apply the weight, 1/E^2 and eps once per row; e = exp(beta
+                    // (a2 - mx)) from |X|^2 in one FMA; c = Kp (e - e0) + Ki
+                    const float wrow = (in_pos && in_neg) ? 2.0f : 1.0f;
+                    const float sh = mx * bl2;
+                    const float e0 = ex2a(-sh);
+                    const float Kp = (grad_row && psl_mode) ? wrow * cP : 0.0f;
+                    const float Ki = (grad_row && !psl_mode) ? (wrow - wb) * cI : 0.0f;
+                    const float Kc0 = fmaf(-e0, Kp, Ki);
+                    const float kexp = s_k[5], kofs = fmaf(eps_n, bl2, -sh);
+                    float rP[2] = {0.0f, 0.0f}, rZ[2] = {0.0f, 0.0f}, rQ[2] = {0.0f, 0.0f};
+                    float rH[2] = {0.0f, 0.0f};
                     sfor<0, P::VALS>([&](auto w) {
+                        constexpr int h = decltype(w)::value & 1;
                         const float2 x = v[w];
-                        const float a2 = fmaf(fmaf(x.x, x.x, x.y * x.y), invE2, eps_n);
-                        const float wt = uniform ? wrow : mweight<decltype(w)::value>(rmk);
-                        tmx[w & 1] = fmaxf(tmx[w & 1], wt > 0.0f ? a2 : -CUDART_INF_F);
+                        const float p2 = fmaf(x.x, x.x, x.y * x.y);
+                        const float e = ex2v(fmaf(p2, kexp, kofs));
+                        rH[h] = fmaxf(rH[h], p2);
+                        rP[h] += p2;
+                        rZ[h] += e;
+                        rQ[h] = fmaf(e, p2, rQ[h]);
+                        const float c = fmaf(e, Kp, Kc0);
+                        v[w] = make_float2(c * x.x, -c * x.y);
                     });
-                }
-                const float rmx = fixed ? mx : slot_max<P::TPR>(fmaxf(tmx[0], tmx[1]), red + 32, slot);
-                if (rmx > mx) {  // slot-uniform
-                    const float f = ex2a((mx - rmx) * bl2);  // 0 while mx = -inf
-                    zs *= f;
-                    ts *= f;
-                    if (psl_mode) {
-                        cs *= f;
-                        if (mx > -CUDART_INF_F) {  // the slot owns its accumulator on this path
-                            if (p.phase_only) {
-                                for (int n = t; n < wv.sN; n += P::TPR) acc_r[n] *= f;
-                            } else {
-                                for (int n = t; n < wv.sN; n += P::TPR) {
-                                    const float2 a = acc[n];
-                                    acc[n] = make_float2(a.x * f, a.y * f);
+                    const float sa2 = fmaf(rP[0] + rP[1], invE2, (float)P::VALS * eps_n);  // sum a2
+                    const float Zr = rZ[0] + rZ[1];
+                    const float sea2 = fmaf(rQ[0] + rQ[1], invE2, eps_n * Zr);            // sum e a2
+                    isl = fmaf(wrow, sa2, isl);
+                    zs = fmaf(wrow, Zr, zs);
+                    ts = fmaf(wrow, sea2, ts);
+                    cs += fmaf(Kp, fmaf(-e0, sa2, sea2), Ki * sa2);
+                    hm = fmaxf(hm, fmaf(fmaxf(rH[0], rH[1]), invE2, eps_n));
+                } else {
+                    const RowMasks rmk = row_masks(wv, cm, k);
+                    const bool uniform = !valid || (rmk.one == full_mask && (rmk.two == 0ull || rmk.two == full_mask));
+                    const float wrow = valid ? (rmk.two != 0ull ? 2.0f : (rmk.one != 0ull ? 1.0f : 0.0f)) : 0.0f;
+                    // pass 1 (running shift only): largest weighted a2 of the row
+                    // (two independent chains)
+                    float tmx[2] = {-CUDART_INF_F, -CUDART_INF_F};
+                    if (!fixed) {
+                        sfor<0, P::VALS>([&](auto w) {
+                            const float2 x = v[w];
+                            const float a2 = fmaf(fmaf(x.x, x.x, x.y * x.y), invE2, eps_n);
+                            const float wt = uniform ? wrow : mweight<decltype(w)::value>(rmk);
+                            tmx[w & 1] = fmaxf(tmx[w & 1], wt > 0.0f ? a2 : -CUDART_INF_F);
+                        });
+                    }
+                    const float rmx = fixed ? mx : slot_max<P::TPR>(fmaxf(tmx[0], tmx[1]), red + 32, slot);
+                    if (rmx > mx) {  // slot-uniform
+                        const float f = ex2a((mx - rmx) * bl2);  // 0 while mx = -inf
+                        zs *= f;
+                        ts *= f;
+                        if (psl_mode) {
+                            cs *= f;
+                            if (mx > -CUDART_INF_F) {  // the slot owns its accumulator on this path
+                                if (p.phase_only) {
+                                    for (int n = t; n < wv.N; n += P::TPR) acc_r[n] *= f;
+                                } else {
+                                    for (int n = t; n < wv.N; n += P::TPR) {
+                                        const float2 a = acc[n];
+                                        acc[n] = make_float2(a.x * f, a.y * f);
+                                    }
                                 }
                             }
                         }
+                        mx = rmx;
                     }
-                    mx = rmx;
+                    // pass 2: loss partials and the gradient remainder, v = conj(c X)
+                    const float sh = mx * bl2;
+                    const float e0 = ex2a(-sh);
+                    // row sums in two independent chains each (even / odd registers)
+                    float r_isl[2] = {0.0f, 0.0f}, r_z[2] = {0.0f, 0.0f}, r_t[2] = {0.0f, 0.0f};
+                    float r_c[2] = {0.0f, 0.0f}, r_h[2] = {-CUDART_INF_F, -CUDART_INF_F};
+                    sfor<0, P::VALS>([&](auto w) {
+                        constexpr int h = decltype(w)::value & 1;
+                        const float2 x = v[w];
+                        const float a2 = fmaf(fmaf(x.x, x.x, x.y * x.y), invE2, eps_n);
+                        const float wt = uniform ? wrow : mweight<decltype(w)::value>(rmk);
+                        const float e = wt > 0.0f ? ex2a(fmaf(a2, bl2, -sh)) : 0.0f;
+                        r_h[h] = fmaxf(r_h[h], wt > 0.0f ? a2 : -CUDART_INF_F);
+                        const float we = wt * e;
+                        r_isl[h] = fmaf(wt, a2, r_isl[h]);
+                        r_z[h] += we;
+                        r_t[h] = fmaf(we, a2, r_t[h]);
+                        float c = 0.0f;
+                        if (grad_row) c = psl_mode ? wt * (e - e0) * cP : (wt - wb) * cI;
+                        r_c[h] = fmaf(c, a2, r_c[h]);
+                        v[w] = make_float2(c * x.x, -c * x.y);
+                    });
+                    isl += r_isl[0] + r_isl[1];
+                    zs += r_z[0] + r_z[1];
+                    ts += r_t[0] + r_t[1];
+                    cs += r_c[0] + r_c[1];
+                    hm = fmaxf(hm, fmaxf(r_h[0], r_h[1]));
                 }
-                // pass 2: loss partials and the gradient remainder, v = conj(c X)
-                const float sh = mx * bl2;
-                const float e0 = ex2a(-sh);
-                // row sums in two independent chains each (even / odd registers)
-                float r_isl[2] = {0.0f, 0.0f}, r_z[2] = {0.0f, 0.0f}, r_t[2] = {0.0f, 0.0f};
-                float r_c[2] = {0.0f, 0.0f}, r_h[2] = {-CUDART_INF_F, -CUDART_INF_F};
-                sfor<0, P::VALS>([&](auto w) {
-                    constexpr int h = decltype(w)::value & 1;
-                    const float2 x = v[w];
-                    const float a2 = fmaf(fmaf(x.x, x.x, x.y * x.y), invE2, eps_n);
-                    const float wt = uniform ? wrow : mweight<decltype(w)::value>(rmk);
-                    const float e = wt > 0.0f ? ex2a(fmaf(a2, bl2, -sh)) : 0.0f;
-                    r_h[h] = fmaxf(r_h[h], wt > 0.0f ? a2 : -CUDART_INF_F);
-                    const float we = wt * e;
-                    r_isl[h] = fmaf(wt, a2, r_isl[h]);
-                    r_z[h] += we;
-                    r_t[h] = fmaf(we, a2, r_t[h]);
-                    float c = 0.0f;
-                    if (grad_row) c = psl_mode ? wt * (e - e0) * cP : (wt - wb) * cI;
-                    r_c[h] = fmaf(c, a2, r_c[h]);
-                    v[w] = make_float2(c * x.x, -c * x.y);
-                });
-                isl += r_isl[0] + r_isl[1];
-                zs += r_z[0] + r_z[1];
-                ts += r_t[0] + r_t[1];
-                cs += r_c[0] + r_c[1];
-                hm = fmaxf(hm, fmaxf(r_h[0], r_h[1]));
-            }
-            if constexpr (P::TPR >= 32) {
-                if (!grad_row) break;  // slot-uniform: the slot is one or more whole warps
+                if constexpr (P::TPR >= 32) {
+                    if (!grad_row) break;  // slot-uniform: the slot is one or more whole warps
+                }
             }
         }
         if (p.phase_only)
-            scatter_row_real<M, HALF>(v, acc_r, s_sm, wv.N, wv.periodic ? k - wv.N : k, t, grad_row, slot, turns, my_turn);
+            scatter_row_real<M, HALF>(v, acc_r, s_sm, wv.N, wv.periodic ? k - wv.N : k, t, grad_row, slot, turns,
+                                      my_turn, wv.periodic != 0);
         else
-            scatter_row<M, HALF, true>(v, acc, s_sm, wv.N, wv.periodic ? k - wv.N : k, t, grad_row, slot, turns, my_turn);
+            scatter_row<M, HALF, true>(v, acc, s_sm, wv.N, wv.periodic ? k - wv.N : k, t, grad_row, slot, turns,
+                                       my_turn, wv.periodic != 0);
     }
     // bring every slot to the CTA's largest shift (fixed shift: the CTA's
     // largest weighted a2, the record's hard maximum)
@@ -1136,9 +1155,9 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
     if (wv.w_psl != 0.0f && !fixed) {
         cs *= fs;
         if (p.phase_only) {
-            for (int n = t; n < wv.sN; n += P::TPR) acc_r[n] *= fs;
+            for (int n = t; n < wv.N; n += P::TPR) acc_r[n] *= fs;
         } else {
-            for (int n = t; n < wv.sN; n += P::TPR) {
+            for (int n = t; n < wv.N; n += P::TPR) {
                 const float2 a = acc[n];
                 acc[n] = make_float2(a.x * fs, a.y * fs);
             }
@@ -1210,7 +1229,7 @@ cudaError_t run_loss_m(const AfParams& p, cudaStream_t st) {
 template <int M>
 cudaError_t run_backward_m(const AfParams& p, cudaStream_t st) {
     if (p.acc_copies < 1 || (RowPlan<M>::THREADS / RowPlan<M>::TPR) % p.acc_copies) return cudaErrorInvalidConfiguration;
-    const size_t smem = backward_smem<M>(sig_len(p), p.acc_copies, p.phase_only);
+    const size_t smem = backward_smem<M>(p.N, p.acc_copies, p.phase_only, p.periodic);
     return launch_rows<M>(af_backward_kernel<M, false>, smem, p, st);
 }
 
@@ -1222,7 +1241,7 @@ cudaError_t run_backward_m(const AfParams& p, cudaStream_t st) {
 template <int M>
 cudaError_t run_match_m(const AfParams& p, cudaStream_t st) {
     if (p.acc_copies < 1 || (RowPlan<M>::THREADS / RowPlan<M>::TPR) % p.acc_copies) return cudaErrorInvalidConfiguration;
-    const size_t smem = backward_smem<M>(sig_len(p), p.acc_copies, p.phase_only);
+    const size_t smem = backward_smem<M>(p.N, p.acc_copies, p.phase_only, p.periodic);
     if (2 * p.N <= M && !p.periodic) return launch_rows<M>(af_match_kernel<M, true>, smem, p, st);
     return launch_rows<M>(af_match_kernel<M, false>, smem, p, st);
 }
@@ -1230,7 +1249,7 @@ cudaError_t run_match_m(const AfParams& p, cudaStream_t st) {
 template <int M>
 cudaError_t run_fused_m(const AfParams& p, cudaStream_t st) {
     if (p.acc_copies < 1 || (RowPlan<M>::THREADS / RowPlan<M>::TPR) % p.acc_copies) return cudaErrorInvalidConfiguration;
-    const size_t smem = backward_smem<M>(sig_len(p), p.acc_copies, p.phase_only);
+    const size_t smem = backward_smem<M>(p.N, p.acc_copies, p.phase_only, p.periodic);
     if (2 * p.N <= M) return launch_rows<M>(af_fused_kernel<M, true>, smem, p, st);
     return launch_rows<M>(af_fused_kernel<M, false>, smem, p, st);
 }

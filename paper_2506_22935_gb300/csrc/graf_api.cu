@@ -222,7 +222,7 @@ static graf_status_t af_backward_impl(const Mode& md, const void* x, graf_input_
     p.csum = reinterpret_cast<float*>(ws + gpart_bytes(B, N, T));
     p.usum = reinterpret_cast<double*>(ws + gpart_bytes(B, N, T) + csum_bytes(B, T));
     p.phase_only = (kind == GRAF_IN_PHASE && grad_s == nullptr) ? 1 : 0;
-    p.acc_copies = graf::acc_copies_for(M, store_len(md, N), p.phase_only);
+    p.acc_copies = graf::acc_copies_for(M, N, p.phase_only, md.periodic);
     if (p.acc_copies < 1) return GRAF_ERR_UNSUPPORTED;
     return cuda_status(graf::run_backward(p, dL, reinterpret_cast<float2*>(grad_s), grad_phi,
                                           static_cast<cudaStream_t>(stream)));
@@ -240,7 +240,7 @@ static graf_status_t af_loss_backward_impl(const Mode& md, const void* x, graf_i
     if (!workspace || workspace_bytes < backward_ws_impl(md, B, N, M, w)) return GRAF_ERR_WORKSPACE;
     if (reinterpret_cast<uintptr_t>(workspace) & 255) return GRAF_ERR_WORKSPACE;
     const bool phase_only = kind == GRAF_IN_PHASE && grad_s == nullptr;
-    const int acc = graf::acc_copies_for(M, store_len(md, N), phase_only ? 1 : 0);
+    const int acc = graf::acc_copies_for(M, N, phase_only ? 1 : 0, md.periodic);
     if (acc < 1) return GRAF_ERR_UNSUPPORTED;
     FusedPlan f = fused_plan(B, N, M, w, l.w_psl != 0.0f, phase_only);
     // on the PSL path with a running log-sum-exp shift each row slot needs its
@@ -291,7 +291,7 @@ static graf_status_t af_loss_backward_impl(const Mode& md, const void* x, graf_i
         q.csum = csum2;
         q.scale = nullptr;
         q.phase_only = 0;  // its rows all need their gradient
-        q.acc_copies = graf::acc_copies_for(M, store_len(md, N), 0);  // complex accumulators
+        q.acc_copies = graf::acc_copies_for(M, N, 0, md.periodic);  // complex accumulators
         if (q.acc_copies < 1) return GRAF_ERR_UNSUPPORTED;
         e = graf::run_backward(q, nullptr, nullptr, nullptr, st);
         p.tiles2 = f.T2.tiles;

@@ -110,11 +110,13 @@ cudaError_t run_match(const AfParams& p, float* loss_out, cudaStream_t st);
 template <int M> cudaError_t run_composite_m(const CompParams& q, cudaStream_t st);
 template <int M> cudaError_t run_spectral_m(const SpecParams& q, cudaStream_t st);
 
-// Shared-memory length of the signal and of each gradient accumulator.
+// Shared-memory length of the signal: N, or 2N for the periodic AF (the
+// signal twice, so that s[(n - k) mod N] is one load).
 __host__ __device__ __forceinline__ int sig_len(const AfParams& p) { return p.periodic ? 2 * p.N : p.N; }
-// Bytes of all gradient accumulators of a CTA (256-byte aligned).
+// Bytes of all gradient accumulators of a CTA (N entries each, 256-byte
+// aligned).
 __host__ __device__ __forceinline__ size_t acc_region_bytes(const AfParams& p) {
-    return ((size_t)p.acc_copies * sig_len(p) * (p.phase_only ? sizeof(float) : sizeof(float2)) + 255) &
+    return ((size_t)p.acc_copies * p.N * (p.phase_only ? sizeof(float) : sizeof(float2)) + 255) &
            ~(size_t)255;
 }
 
@@ -127,7 +129,7 @@ struct Wave {
     int k_lo, k_hi, m_lo, m_hi, k_ml, m_ml;
     int r_lo, r_hi, rows_per_tile, tiles, full_m, defer_hi, unscaled;
     int periodic, pconj;
-    int sN;         // shared-memory length of the signal and of each accumulator: N, or 2N periodic
+    int sN;         // shared-memory length of the signal: N, or 2N periodic
     float eps, beta, w_psl, w_isl;
     // Fixed log-sum-exp shift (in units of Ahat^2), 0 = none.  For phase
     // input E = N and every cell has a2 = |X|^2/E^2 + eps/E^2 <= 1 + eps/N^2
@@ -223,9 +225,10 @@ constexpr size_t forward_smem(int N) {
 }
 // Gradient accumulators: complex (float2) in general, real (float) when only
 // the phase gradient is wanted (see scatter_row_real).
+// per: periodic AF (the signal is stored twice; accumulators keep N entries).
 template <int M>
-constexpr size_t backward_smem(int N, int acc_copies, int real = 0) {
-    return smem_signal_bytes<M>(N) + row_buffer_bytes<M>() +
+constexpr size_t backward_smem(int N, int acc_copies, int real = 0, int per = 0) {
+    return smem_signal_bytes<M>(per ? 2 * N : N) + row_buffer_bytes<M>() +
            (((size_t)acc_copies * N * (real ? sizeof(float) : sizeof(float2)) + 255) & ~(size_t)255) + kRedBytes;
 }
 // Number of gradient accumulators per CTA (a power of two <= slots; slots
@@ -233,23 +236,23 @@ constexpr size_t backward_smem(int N, int acc_copies, int real = 0) {
 // registers' number of CTAs share an SM, if that leaves at most two turns,
 // else the largest that fits in shared memory; 0 if even one does not.
 template <int M>
-int backward_acc_copies(int N, int real = 0) {
+int backward_acc_copies(int N, int real = 0, int per = 0) {
     constexpr int slots = RowPlan<M>::THREADS / RowPlan<M>::TPR;
     constexpr int per_sm = RowPlan<M>::MIN_BLOCKS;
     if (per_sm > 1) {
         const size_t budget = kSmemPerSm / per_sm - 1024;  // 1 KB per CTA is reserved
         for (int a = slots; a >= 1 && 2 * a >= slots; a /= 2)
-            if (backward_smem<M>(N, a, real) <= budget) return a;
+            if (backward_smem<M>(N, a, real, per) <= budget) return a;
     }
     for (int a = slots; a >= 1; a /= 2)
-        if (backward_smem<M>(N, a, real) <= kMaxSmem) return a;
+        if (backward_smem<M>(N, a, real, per) <= kMaxSmem) return a;
     return 0;
 }
 
 size_t row_kernel_smem(int M, int N, int which);  // which: 0 forward/loss, 2 backward
 cudaError_t run_loss_rows(const AfParams& p, cudaStream_t st);      // loss row kernel only
 cudaError_t run_backward_rows(const AfParams& p, cudaStream_t st);  // backward row kernel only
-int acc_copies_for(int M, int N, int real = 0);    // backward accumulators, 0 = unsupported
+int acc_copies_for(int M, int N, int real = 0, int per = 0);  // backward accumulators, 0 = unsupported
 template <int M> cudaError_t run_forward_m(const AfParams& p, cudaStream_t st);
 template <int M> cudaError_t run_loss_m(const AfParams& p, cudaStream_t st);
 template <int M> cudaError_t run_backward_m(const AfParams& p, cudaStream_t st);
