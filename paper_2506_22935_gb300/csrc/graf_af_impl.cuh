@@ -946,8 +946,9 @@ cudaError_t run_composite_m(const CompParams& q, cudaStream_t st) {
 // not uniform) contribute loss partials only; af_backward_kernel adds their
 // gradient once PSL_soft is known.  On the PSL path every slot owns its
 // accumulator (acc_copies == slot count).
-template <int M, bool HALF>
+template <int M, bool HALF, bool RO>
 __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, unsigned char* smem) {
+    const bool phase_only = RO || p.phase_only;  // RO: only dL/dphi is wanted, known at compile time
     using P = RowPlan<M>;
     constexpr int SLOTS = P::THREADS / P::TPR;
     constexpr int NW = P::THREADS / 32;
@@ -1005,7 +1006,7 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
     for (int it = 0; it < iters; ++it) {
         const int k = row0 + slot + it * SLOTS;
         const bool valid = k < row_end;
-        const bool grad_row = valid && k > wv.defer_hi && !(p.phase_only && k == 0);
+        const bool grad_row = valid && k > wv.defer_hi && !(phase_only && k == 0);
         // a warp of several row slots none of which holds a valid row skips
         // both transforms; it still runs the scatter below, with nothing to
         // add, so that it joins the CTA's barriers when slots take turns.  Only
@@ -1086,7 +1087,7 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
                         if (psl_mode) {
                             cs *= f;
                             if (mx > -CUDART_INF_F) {  // the slot owns its accumulator on this path
-                                if (p.phase_only) {
+                                if (phase_only) {
                                     for (int n = t; n < wv.N; n += P::TPR) acc_r[n] *= f;
                                 } else {
                                     for (int n = t; n < wv.N; n += P::TPR) {
@@ -1131,12 +1132,13 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
                 }
             }
         }
-        if (p.phase_only)
+        if (phase_only) {
             scatter_row_real<M, HALF>(v, acc_r, s_sm, wv.N, wv.periodic ? k - wv.N : k, t, grad_row, slot, turns,
                                       my_turn, wv.periodic != 0);
-        else
+        } else if constexpr (!RO) {
             scatter_row<M, HALF, true>(v, acc, s_sm, wv.N, wv.periodic ? k - wv.N : k, t, grad_row, slot, turns,
                                        my_turn, wv.periodic != 0);
+        }
     }
     // bring every slot to the CTA's largest shift (fixed shift: the CTA's
     // largest weighted a2, the record's hard maximum)
@@ -1154,7 +1156,7 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
     ts *= fs;
     if (wv.w_psl != 0.0f && !fixed) {
         cs *= fs;
-        if (p.phase_only) {
+        if (phase_only) {
             for (int n = t; n < wv.N; n += P::TPR) acc_r[n] *= fs;
         } else {
             for (int n = t; n < wv.N; n += P::TPR) {
@@ -1185,10 +1187,10 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
     write_grad_partial<M>(p, wv, acc_all, red, cs, tile);
 }
 
-template <int M, bool HALF>
+template <int M, bool HALF, bool RO>
 __global__ void __launch_bounds__(RowPlan<M>::THREADS, RowPlan<M>::MIN_BLOCKS) af_fused_kernel(AfParams p) {
     extern __shared__ __align__(256) unsigned char smem[];
-    for_each_item(p, [&](int b, int tile) { fused_item<M, HALF>(p, b, tile, smem); });
+    for_each_item(p, [&](int b, int tile) { fused_item<M, HALF, RO>(p, b, tile, smem); });
 }
 
 // ---------------------------------------------------------- host launchers
@@ -1250,8 +1252,10 @@ template <int M>
 cudaError_t run_fused_m(const AfParams& p, cudaStream_t st) {
     if (p.acc_copies < 1 || (RowPlan<M>::THREADS / RowPlan<M>::TPR) % p.acc_copies) return cudaErrorInvalidConfiguration;
     const size_t smem = backward_smem<M>(p.N, p.acc_copies, p.phase_only, p.periodic);
-    if (2 * p.N <= M) return launch_rows<M>(af_fused_kernel<M, true>, smem, p, st);
-    return launch_rows<M>(af_fused_kernel<M, false>, smem, p, st);
+    // the phase-gradient-only kernel carries no complex scatter
+    if (2 * p.N <= M && p.phase_only) return launch_rows<M>(af_fused_kernel<M, true, true>, smem, p, st);
+    if (2 * p.N <= M) return launch_rows<M>(af_fused_kernel<M, true, false>, smem, p, st);
+    return launch_rows<M>(af_fused_kernel<M, false, false>, smem, p, st);
 }
 
 }  // namespace graf
