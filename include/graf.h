@@ -10,7 +10,7 @@
  *                 non-periodic extension listed in Sec. 8.6); the paper's own
  *                 circular form is the graf_paf_* family at the end
  *   row DFT       X[k,m] = sum_n R[k,n] exp(-2 pi j m n / M)          Sec. 4.1, Eq. 11
- *                 M-point (zero padded), m in [-M/2, M/2-1]         Algorithm 1 step 5
+ *                 M-point (zero padded), m in [-M/2, M/2-1]         (fftshift, Algorithm 1)
  *   magnitude     Ahat[k,m] = sqrt(|X[k,m]|^2 + eps) / E,           Eq. 12, Eq. 17
  *                 E = sum_n |s[n]|^2 (= max |X| = |X[0,0]|)
  *   losses on the sidelobe region Omega (Eqs. 18, 19, 22):
@@ -76,8 +76,8 @@ typedef struct {
 
 /* Delay/Doppler window (inclusive bounds, Doppler in fftshift order) and the
  * mainlobe box |k| <= k_ml && |m| <= m_ml that the losses exclude; the
- * sidelobe region is Omega = window minus box (Eq. 18: "the sidelobe region
- * excluding the mainlobe").  A box size of -1 excludes nothing. */
+ * sidelobe region of Eq. 18 is Omega = window minus box.  A box size of -1
+ * excludes nothing. */
 typedef struct {
     int32_t k_lo, k_hi;
     int32_t m_lo, m_hi;
@@ -97,6 +97,29 @@ GRAF_API const char* graf_status_string(graf_status_t status);
 
 /* GRAF_VERSION of the loaded library. */
 GRAF_API int32_t graf_version(void);
+
+/* Bits of the device error word.  The calls return before their kernels run,
+ * so conditions only the device sees are recorded there, per device, by the
+ * loss finalisation of every loss call (graf_af_loss, graf_af_loss_backward,
+ * graf_paf_*, the batch plans) and of graf_af_match. */
+#define GRAF_DEVERR_ENERGY 1u    /* a waveform's energy E = sum |s|^2 was 0 or not finite */
+#define GRAF_DEVERR_NONFINITE 2u /* a loss scalar came out not finite (NaN or Inf in the input) */
+
+/*
+ * graf_get_device_error_word - takes the current device's error word in
+ * stream order (read and cleared in one atomic exchange after the work queued
+ * on `stream`), waits for it and returns it in *word (0 = nothing raised).
+ * The word collects bits from every stream of the device since it was last
+ * taken.
+ * GRAF_ERR_INVALID_ARG if word is NULL, GRAF_ERR_CUDA if a CUDA call fails.
+ */
+GRAF_API graf_status_t graf_get_device_error_word(uint32_t* word, void* stream);
+
+/*
+ * graf_get_device_error - as graf_get_device_error_word without the bits:
+ * GRAF_OK if the word was 0, else GRAF_ERR_DEVICE_FLAG (the word is cleared).
+ */
+GRAF_API graf_status_t graf_get_device_error(void* stream);
 
 /*
  * graf_af_forward - the energy-normalised AF over a window (Algorithm 1 with
@@ -346,8 +369,8 @@ GRAF_API graf_status_t graf_af_loss_backward_noalloc(const void* x, graf_input_t
  * Periodic AF: the paper's own discrete definition (Sec. 3.1 Eq. 2, Sec. 4.1
  * Eqs. 7-12, Algorithm 1):
  *   X[k,m] = sum_{n=0}^{N-1} s[n] conj(s[(n-k) mod N]) exp(sign 2 pi j m n / N)
- *   chi[k,m] = |X[k,m]|^2,  k, m in [-N/2, N/2-1] (fftshift order, Algorithm 1
- *   step 5),  sign = +1 as in Eq. 7 or -1 as the FFT of Algorithm 1 step 3.
+ *   chi[k,m] = |X[k,m]|^2,  k, m in [-N/2, N/2-1] (fftshift order, as in
+ *   Algorithm 1),  sign = +1 as in Eq. 7 or -1 as the forward FFT of Algorithm 1.
  * Constraints as above with M = N: N a power of two in [GRAF_M_MIN,
  * GRAF_M_MAX]; windows inside k, m in [-N/2, N/2-1]; sign = +1 or -1, else
  * GRAF_ERR_INVALID_ARG.  The losses are those of the aperiodic calls with

@@ -263,7 +263,7 @@ def paf_complex(s, sign=1, k_lo=None, k_hi=None, m_lo=None, m_hi=None) -> np.nda
 
 def paf_chi(s, sign=1, normalise=True) -> np.ndarray:
     """chi = |X|^2 (Eq. 12), divided by E^2 = chi[0,0] = max chi if normalise
-    (Eq. 17); [N][N], fftshift order (Algorithm 1 steps 4-5)."""
+    (Eq. 17); [N][N], fftshift order (as in Algorithm 1)."""
     X = paf_complex(s, sign)
     chi = np.abs(X) ** 2
     if normalise:

@@ -9,10 +9,10 @@
  * Definitions followed (paper section / equation):
  *   - lag product R[k,n] = s[n] * conj(s[n-k])                 (Sec. 4.1, Eq. 8)
  *     taken aperiodically: s[n] = 0 outside [0, N), delays k = -(N-1)..N-1
- *     (the non-periodic extension named in Sec. 8.6 "Limitations").
+ *     (the non-periodic extension that Sec. 8.6 lists among the limitations).
  *   - row DFT X[k,m] = sum_n R[k,n] exp(-j 2 pi m n / M)        (Sec. 4.1, Eq. 11)
  *     with an M-point (zero padded) transform, m in [-M/2, M/2-1] (fftshift
- *     order, Algorithm 1 step 5).
+ *     order, as in Algorithm 1).
  *   - eps-stabilised, energy-normalised magnitude
  *     Ahat = sqrt(|X|^2 + eps) / E, E = sum |s|^2             (Eq. 12, Eq. 17;
  *     E equals max |X| = |X[0,0]| by Cauchy-Schwarz).
@@ -454,9 +454,9 @@ int orc_fd_grad_s(const double* s, int64_t N, int64_t M, const int64_t win6[6], 
 /* ============================================================ periodic AF */
 /* The paper's literal discrete AF (Sec. 3.1 Eq. 2, Sec. 4.1 Eqs. 7-12):
  *   X[k,m] = sum_{n=0}^{N-1} s[n] conj(s[(n-k) mod N]) exp(sign j 2 pi m n / N)
- * with sign = +1 (Eq. 7) or -1 (the FFT of Algorithm 1 step 3), chi = |X|^2,
+ * with sign = +1 (Eq. 7) or -1 (the forward FFT of Algorithm 1), chi = |X|^2,
  * delays and Doppler bins both in fftshift order k, m in [-N/2, N/2-1]
- * (Algorithm 1 step 5).  The losses use Ahat^2 = (|X|^2 + eps) / E^2 exactly
+ * (as in Algorithm 1).  The losses use Ahat^2 = (|X|^2 + eps) / E^2 exactly
  * as for the aperiodic AF; with eps = 0 that is chi / chi[0,0] = chi / max chi
  * (Eq. 17: |X| <= E by Cauchy-Schwarz, with equality at the origin). */
 

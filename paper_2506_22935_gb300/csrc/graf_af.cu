@@ -2,9 +2,18 @@
 // gradient reduction) and the dispatch over the row length M.
 #include <math_constants.h>
 
+#include "graf.h"
 #include "graf_kernels.cuh"
 
 namespace graf {
+
+// The device error word of this device (GRAF_DEVERR_* bits), raised by the
+// finalisation kernels and taken (read and cleared in one atomic exchange) by
+// graf_get_device_error_word.
+__device__ unsigned int g_device_error;
+__device__ unsigned int g_device_error_taken;
+
+__global__ void take_device_error_kernel() { g_device_error_taken = atomicExch(&g_device_error, 0u); }
 
 // |Omega| = |window| - |window intersect mainlobe box|, exact in int64.
 __device__ __forceinline__ long long omega_count(const Wave& p) {
@@ -81,6 +90,12 @@ __global__ void loss_finalize_kernel(AfParams p, float* out8) {
         }
         o[5] = (float)cnt;
         o[7] = 0.0f;
+        // E was written by the row kernels earlier on this stream
+        const float E = o[4];
+        unsigned int bits = 0;
+        if (!(E > 0.0f) || !isfinite(E)) bits |= GRAF_DEVERR_ENERGY;
+        if (!isfinite(o[0]) || !isfinite(o[1]) || !isfinite(o[2]) || !isfinite(o[3])) bits |= GRAF_DEVERR_NONFINITE;
+        if (bits) atomicOr(&g_device_error, bits);
     }
     // fused loss + gradient: per-CTA factor that turns a partial accumulated
     // with the CTA's shift mx_cta into the true remainder, exp(beta (mx_cta -
@@ -289,6 +304,7 @@ __global__ void match_finalize_kernel(AfParams p, float* loss_out) {
     for (int i = 0; i < wv.tiles; ++i) s += p.mpart[wv.rec_off + i];
     if (loss_out) loss_out[b] = (float)s;
     if (p.out8) p.out8[(size_t)b * 8] += (float)((double)p.match_w * s);
+    if (!isfinite(s)) atomicOr(&g_device_error, GRAF_DEVERR_NONFINITE);
 }
 
 #define GRAF_DISPATCH_M(FN, M, ...)                      \
@@ -443,3 +459,28 @@ cudaError_t run_finalize(const AfParams& p, cudaStream_t st) {
 }
 
 }  // namespace graf
+
+extern "C" {
+
+graf_status_t graf_get_device_error_word(uint32_t* word, void* stream) {
+    if (!word) return GRAF_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned int h = 0;
+    graf::take_device_error_kernel<<<1, 1, 0, st>>>();
+    if (cudaGetLastError() != cudaSuccess) return GRAF_ERR_CUDA;
+    if (cudaMemcpyFromSymbolAsync(&h, graf::g_device_error_taken, sizeof h, 0, cudaMemcpyDeviceToHost, st) !=
+        cudaSuccess)
+        return GRAF_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return GRAF_ERR_CUDA;
+    *word = h;
+    return GRAF_OK;
+}
+
+graf_status_t graf_get_device_error(void* stream) {
+    uint32_t w = 0;
+    const graf_status_t s = graf_get_device_error_word(&w, stream);
+    if (s != GRAF_OK) return s;
+    return w ? GRAF_ERR_DEVICE_FLAG : GRAF_OK;
+}
+
+}  // extern "C"

@@ -64,7 +64,7 @@ __device__ __forceinline__ void for_each_item(const AfParams& p, F&& body) {
 
 // ---------------------------------------------------------- forward (store)
 // Ahat = sqrt(|X|^2 + eps) / E (Eq. 12, Eq. 17) -- or chi = |X|^2 (Eq. 12,
-// Algorithm 1 step 4), optionally over chi[0,0] = E^2 = max chi (Eq. 17) --
+// Algorithm 1), optionally over chi[0,0] = E^2 = max chi (Eq. 17) --
 // for every window cell of rows k and -k.  Stores are coalesced along m (consecutive threads hold
 // consecutive Doppler bins) and streaming (written once, never re-read here).
 template <int M, bool HALF>

@@ -24,6 +24,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgraf.so")
 
 GRAF_OK = 0
+GRAF_ERR_DEVICE_FLAG = 6
 GRAF_IN_COMPLEX = 0
 GRAF_IN_PHASE = 1
 GRAF_LOSS_OUT = 8
@@ -64,6 +65,8 @@ _sz = ctypes.c_size_t
 _SIGS = {
     "graf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "graf_version": (_i32, []),
+    "graf_get_device_error_word": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32), _vp]),
+    "graf_get_device_error": (ctypes.c_int, [_vp]),
     "graf_af_forward": (ctypes.c_int, [_vp, ctypes.c_int, _i32, _i32, _i32, graf_window_t, ctypes.c_float,
                                        _vp, _vp]),
     "graf_af_loss_workspace_bytes": (_sz, [_i32, _i32, _i32, graf_window_t]),
@@ -136,6 +139,24 @@ def graf_status_string(status: int) -> str:
 
 def graf_version() -> int:
     return load().graf_version()
+
+
+GRAF_DEVERR_ENERGY = 1
+GRAF_DEVERR_NONFINITE = 2
+
+
+def graf_get_device_error(stream) -> int:
+    return load().graf_get_device_error(stream)
+
+
+def device_error_word(device=None) -> int:
+    """Takes (reads and clears) the device error word after the work queued
+    on the current stream: GRAF_DEVERR_* bits, 0 if nothing was raised."""
+    torch = _torch()
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    w = ctypes.c_uint32(0)
+    _check(load().graf_get_device_error_word(ctypes.byref(w), _stream(dev)), "graf_get_device_error_word")
+    return int(w.value)
 
 
 def graf_af_forward(x, kind, B, N, M, w, eps, af_out, stream) -> int:
