@@ -68,7 +68,8 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
         return r.stdout + r.stderr
 
     # the largest translation units first, so the parallel build ends sooner
-    prio = ["graf_af_m16384", "graf_af_m8192", "graf_af_m4096", "graf_af_m2048", "graf_af_m1024"]
+    prio = ["graf_af_m64", "graf_af_m16384", "graf_af_m8192", "graf_af_m4096", "graf_af_m2048", "graf_af_m1024",
+            "graf_af_m32", "graf_af_m512", "graf_af_m256", "graf_af_m128"]
 
     def rank(so):
         name = os.path.basename(so[0])[:-3]
