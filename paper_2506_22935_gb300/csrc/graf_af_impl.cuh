@@ -1252,10 +1252,10 @@ template <int M>
 cudaError_t run_fused_m(const AfParams& p, cudaStream_t st) {
     if (p.acc_copies < 1 || (RowPlan<M>::THREADS / RowPlan<M>::TPR) % p.acc_copies) return cudaErrorInvalidConfiguration;
     const size_t smem = backward_smem<M>(p.N, p.acc_copies, p.phase_only, p.periodic);
-    // the phase-gradient-only kernels carry no complex scatter
+    // the phase-gradient-only kernel carries no complex scatter (for N > M/2,
+    // the periodic AF among them, it measured slower and is not used)
     if (2 * p.N <= M && p.phase_only) return launch_rows<M>(af_fused_kernel<M, true, true>, smem, p, st);
     if (2 * p.N <= M) return launch_rows<M>(af_fused_kernel<M, true, false>, smem, p, st);
-    if (p.phase_only) return launch_rows<M>(af_fused_kernel<M, false, true>, smem, p, st);
     return launch_rows<M>(af_fused_kernel<M, false, false>, smem, p, st);
 }
 
