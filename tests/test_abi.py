@@ -100,6 +100,8 @@ def test_invalid_arguments_rejected_before_launch(lib):
     assert g.graf_af_backward(FAKE, 1, 1, 64, 128, w, l, FAKE, None, None, None, FAKE, 1 << 20, None) == INV
     assert g.graf_af_backward(FAKE, 1, 1, 64, 128, w, l, None, None, None, FAKE, FAKE, 1 << 20, None) == INV
     assert g.graf_af_loss_backward(FAKE, 1, 1, 64, 128, w, l, FAKE, None, None, FAKE, FAKE, 16, None) == WS
+    # the device error query needs somewhere to put the word
+    assert lib.graf_get_device_error_word(None, None) == INV
 
 
 def test_binding_refuses_missing_library(tmp_path):
