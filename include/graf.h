@@ -35,6 +35,9 @@
  *     m in [-M/2, M/2-1] with lo <= hi, mainlobe box sizes >= -1, eps >= 0,
  *     beta > 0.  A violated constraint returns GRAF_ERR_INVALID_ARG before
  *     anything is enqueued.  A kernel launch error returns GRAF_ERR_CUDA.
+ *     What only the device can see (a zero or non-finite energy, a
+ *     non-finite loss) is recorded in the device error word, read with
+ *     graf_get_device_error.
  *   - Results are deterministic: every reduction runs in a fixed order.
  */
 #ifndef GRAF_H
