@@ -112,3 +112,17 @@ def test_binding_refuses_missing_library(tmp_path):
             g.load(str(tmp_path / "nope.so"))
         finally:
             g._lib = g._lib_saved
+
+
+def test_product_path_refuses_host_tensors():
+    """No CPU fallback: the torch conveniences refuse host tensors before any
+    call into the library."""
+    torch = pytest.importorskip("torch")
+    phi = torch.zeros(2, 64, dtype=torch.float32)
+    w, loss = W.full(64, 128), g.Loss()
+    with pytest.raises(ValueError, match="CUDA"):
+        g.af_forward(phi, 128, w)
+    with pytest.raises(ValueError, match="CUDA"):
+        g.af_loss_backward(phi, 128, w, loss)
+    with pytest.raises(ValueError, match="CUDA"):
+        g.af_loss(phi.to(torch.complex64), 128, w, loss)
