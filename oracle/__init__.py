@@ -6,6 +6,9 @@ legs of ``bench.py`` may import this package.  It loads ``graf_oracle.c``
 first use, and shares no code with the CUDA library.
 
 Conventions (paper Sec. 4.1, Eqs. 8, 11, 12, 17-19, 22):
+  * ``beta = inf`` selects the hard PSL of Eq. 18, max over Omega of Ahat^2
+    (the beta -> infinity limit of the log-sum-exp PSL), whose subgradient
+    goes through one arg-max cell: the first in row-major window order.
   * ``s`` is complex128 of length N; ``phi`` float64 phases, s = exp(j phi).
   * windows are ``(k_lo, k_hi, m_lo, m_hi, k_ml, m_ml)``: delay and Doppler
     ranges (inclusive, Doppler in fftshift order [-M/2, M/2-1]) and the
@@ -75,9 +78,14 @@ def _load():
             lib.orc_pgrad.argtypes = [_dp, _i64, _c, _ip, _d, _d, _d, _d, _dp, _dp, _dp]
             lib.orc_pfd_grad_phi.argtypes = [_dp, _i64, _c, _ip, _d, _d, _d, _d, _d, _dp]
             lib.orc_match.argtypes = [_dp, _i64, _i64, _ip, _dp, _d, _d, _dp, _dp, _dp, _c]
+            lib.orc_peak_cell.argtypes = [_dp, _i64, _i64, _ip, _d, _ip, _c]
+            lib.orc_cell_grad.argtypes = [_dp, _i64, _i64, _i64, _i64, _d, _dp, _dp]
+            lib.orc_ppeak_cell.argtypes = [_dp, _i64, _c, _ip, _d, _ip]
+            lib.orc_pcell_grad.argtypes = [_dp, _i64, _c, _i64, _i64, _d, _dp, _dp]
             for f in ("orc_af_complex", "orc_af_ahat", "orc_af_cells", "orc_loss", "orc_grad",
                       "orc_fd_grad_phi", "orc_fd_grad_s", "orc_paf_complex", "orc_ploss", "orc_pgrad",
-                      "orc_pfd_grad_phi", "orc_match"):
+                      "orc_pfd_grad_phi", "orc_match", "orc_peak_cell", "orc_cell_grad", "orc_ppeak_cell",
+                      "orc_pcell_grad"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -183,6 +191,27 @@ def grad(s, M, window, w_psl=1.0, w_isl=1.0, beta=50.0, eps=1e-12, nthreads=None
                           _ptr(gs.view(np.float64)), _ptr(gp), _ptr(out), _threads(nthreads))
     _check(st, "grad")
     return gs, gp, out
+
+
+def peak_cell(s, M, window, eps=1e-12, nthreads=None):
+    """(k, m) of the arg-max of Ahat^2 over Omega that the hard PSL uses."""
+    s, sv = _s_buf(s)
+    w = _win(window)
+    pk = np.zeros(2, dtype=np.int64)
+    _check(_load().orc_peak_cell(_ptr(sv), s.shape[0], M, w.ctypes.data_as(_ip), eps, pk.ctypes.data_as(_ip),
+                                 _threads(nthreads)), "peak_cell")
+    return int(pk[0]), int(pk[1])
+
+
+def cell_grad(s, M, k, m, eps=1e-12):
+    """(grad_s, grad_phi) of one cell's Ahat^2[k, m] (conventions as grad)."""
+    s, sv = _s_buf(s)
+    N = s.shape[0]
+    gs = np.zeros(N, dtype=np.complex128)
+    gp = np.zeros(N, dtype=np.float64)
+    _check(_load().orc_cell_grad(_ptr(sv), N, M, int(k), int(m), eps, _ptr(gs.view(np.float64)), _ptr(gp)),
+           "cell_grad")
+    return gs, gp
 
 
 def fd_grad_phi(phi, M, window, w_psl=1.0, w_isl=1.0, beta=50.0, eps=1e-12, h=1e-6,
@@ -291,6 +320,27 @@ def pgrad(s, window, w_psl=1.0, w_isl=1.0, beta=50.0, eps=1e-12, sign=1):
     _check(_load().orc_pgrad(_ptr(sv), N, int(sign), w.ctypes.data_as(_ip), w_psl, w_isl, beta, eps,
                              _ptr(gs.view(np.float64)), _ptr(gp), _ptr(out)), "pgrad")
     return gs, gp, out
+
+
+def ppeak_cell(s, window, eps=1e-12, sign=1):
+    """(k, m) of the arg-max of the periodic AF's Ahat^2 over Omega."""
+    s, sv = _s_buf(s)
+    w = _win(window)
+    pk = np.zeros(2, dtype=np.int64)
+    _check(_load().orc_ppeak_cell(_ptr(sv), s.shape[0], int(sign), w.ctypes.data_as(_ip), eps,
+                                  pk.ctypes.data_as(_ip)), "ppeak_cell")
+    return int(pk[0]), int(pk[1])
+
+
+def pcell_grad(s, k, m, eps=1e-12, sign=1):
+    """(grad_s, grad_phi) of one periodic cell's Ahat^2[k, m]."""
+    s, sv = _s_buf(s)
+    N = s.shape[0]
+    gs = np.zeros(N, dtype=np.complex128)
+    gp = np.zeros(N, dtype=np.float64)
+    _check(_load().orc_pcell_grad(_ptr(sv), N, int(sign), int(k), int(m), eps, _ptr(gs.view(np.float64)),
+                                  _ptr(gp)), "pcell_grad")
+    return gs, gp
 
 
 def pfd_grad_phi(phi, window, w_psl=1.0, w_isl=1.0, beta=50.0, eps=1e-12, sign=1, h=3e-5):

@@ -20,7 +20,10 @@
  *       ISL      = sum_Omega Ahat^2
  *       PSL_soft = (1/beta) log sum_Omega exp(beta Ahat^2)
  *       PSL_hard = max_Omega Ahat^2
- *       L        = w_psl PSL_soft + w_isl ISL
+ *       L        = w_psl PSL_soft + w_isl ISL   (beta finite)
+ *       L        = w_psl PSL_hard + w_isl ISL   (beta = +infinity: the
+ *                  hard maximum of Eq. 18, the beta -> infinity limit of
+ *                  PSL_soft, with the subgradient through one arg-max cell)
  *   - Wirtinger adjoint (Sec. 3.3 Eq. 6, Sec. 4.2 Eqs. 13-15): the gradient
  *     exported is 2 dL/ds* = dL/dRe(s) + j dL/dIm(s), and for phase input
  *     s = exp(j phi), dL/dphi = 2 Im(dL/ds* . conj(s)).
@@ -224,11 +227,20 @@ int orc_af_cells(const double* s, int64_t N, int64_t M, int64_t ncells, const in
  *   out[6] sum_Omega p Ahat^2 with p = exp(beta (Ahat^2 - PSL_soft)), the
  *          softmax-weighted mean that the dL/dE term needs
  *   out[7] 0
- * The log-sum-exp is taken in two passes (max, then shifted sum). */
+ * The log-sum-exp is taken in two passes (max, then shifted sum).
+ * beta = +infinity (hard PSL): out[1] = out[3] = out[6] = max Ahat^2 (the
+ * limits of PSL_soft and of the softmax-weighted mean as beta grows) and
+ * L = w_psl max + w_isl ISL.
+ * peak (nullable): the arg-max cell (k, m), the first in row-major window
+ * order (k ascending, then m ascending) among the cells of Omega whose Ahat^2
+ * is within a relative 1e-12 of the maximum (cells equal in exact arithmetic
+ * differ by FP64 rounding; this keeps the choice among them to the order
+ * alone); (0, 0) with an empty Omega. */
 static int loss_from_X(const double* X, const orc_window* w, double E, double eps,
-                       double w_psl, double w_isl, double beta, double out[8]) {
+                       double w_psl, double w_isl, double beta, double out[8], int64_t peak[2]) {
     int64_t ncols = w->m_hi - w->m_lo + 1;
     double isl = 0.0, amax = -INFINITY, count = 0.0;
+    int64_t pk = 0, pm = 0;
     for (int64_t k = w->k_lo; k <= w->k_hi; ++k)
         for (int64_t m = w->m_lo; m <= w->m_hi; ++m) {
             if (!in_omega(w, k, m)) continue;
@@ -238,9 +250,32 @@ static int loss_from_X(const double* X, const orc_window* w, double E, double ep
             if (a2 > amax) amax = a2;
             count += 1.0;
         }
+    if (count > 0.0) {
+        const double thr = amax - 1e-12 * fabs(amax);
+        int found = 0;
+        for (int64_t k = w->k_lo; k <= w->k_hi && !found; ++k)
+            for (int64_t m = w->m_lo; m <= w->m_hi; ++m) {
+                if (!in_omega(w, k, m)) continue;
+                const double* x = X + 2 * ((k - w->k_lo) * ncols + (m - w->m_lo));
+                double a2 = (x[0] * x[0] + x[1] * x[1] + eps) / (E * E);
+                if (a2 >= thr) { pk = k; pm = m; found = 1; break; }
+            }
+    }
+    if (peak) { peak[0] = pk; peak[1] = pm; }
     if (count == 0.0) {
         memset(out, 0, sizeof(double) * 8);
         out[4] = E;
+        return ORC_OK;
+    }
+    if (isinf(beta)) {
+        out[0] = w_psl * amax + w_isl * isl;
+        out[1] = amax;
+        out[2] = isl;
+        out[3] = amax;
+        out[4] = E;
+        out[5] = count;
+        out[6] = amax;
+        out[7] = 0.0;
         return ORC_OK;
     }
     double z = 0.0;
@@ -279,7 +314,7 @@ int orc_loss(const double* s, int64_t N, int64_t M, const int64_t win6[6], doubl
     double* X = (double*)malloc(sizeof(double) * 2 * (size_t)cells);
     if (!X) return ORC_ENOMEM;
     int st = orc_af_complex(s, N, M, w.k_lo, w.k_hi, w.m_lo, w.m_hi, X, nthreads);
-    if (!st) st = loss_from_X(X, &w, orc_energy(s, N), eps, w_psl, w_isl, beta, out);
+    if (!st) st = loss_from_X(X, &w, orc_energy(s, N), eps, w_psl, w_isl, beta, out, NULL);
     free(X);
     return st;
 }
@@ -341,6 +376,8 @@ static void* adj_worker(void* p) {
 /* Gradient of the loss of orc_loss.
  * Cell adjoint (Eqs. 13-14 applied to Ahat^2 = (|X|^2+eps)/E^2):
  *   dL/dAhat^2 = w_isl + w_psl p,  p = exp(beta (Ahat^2 - PSL_soft))
+ *   (beta = +infinity: p = 1 at the arg-max cell of loss_from_X, 0 elsewhere:
+ *   the subgradient of the hard maximum through that one cell)
  *   G[k,m] = dL/dX*[k,m] = (dL/dAhat^2) X[k,m] / E^2   on Omega, 0 elsewhere.
  * Energy term: dAhat^2/dE = -2 Ahat^2 / E, dE/ds* = s, so
  *   dL/ds* += dLdE * s,  dLdE = -(2/E) (w_isl ISL + w_psl sum_Omega p Ahat^2).
@@ -357,16 +394,20 @@ int orc_grad(const double* s, int64_t N, int64_t M, const int64_t win6[6], doubl
     if (!X || !W) { free(X); free(W); return ORC_ENOMEM; }
     int st = orc_af_complex(s, N, M, w.k_lo, w.k_hi, w.m_lo, w.m_hi, X, nthreads);
     double E = orc_energy(s, N);
-    if (!st) st = loss_from_X(X, &w, E, eps, w_psl, w_isl, beta, out);
+    int64_t peak[2];
+    if (!st) st = loss_from_X(X, &w, E, eps, w_psl, w_isl, beta, out, peak);
     if (st) { free(X); free(W); return st; }
     double psl_soft = out[1];
     /* X becomes G in place */
     for (int64_t r = 0; r < rows; ++r)
         for (int64_t c = 0; c < ncols; ++c) {
             double* x = X + 2 * (r * ncols + c);
-            if (!in_omega(&w, w.k_lo + r, w.m_lo + c)) { x[0] = x[1] = 0.0; continue; }
+            int64_t k = w.k_lo + r, m = w.m_lo + c;
+            if (!in_omega(&w, k, m)) { x[0] = x[1] = 0.0; continue; }
             double a2 = (x[0] * x[0] + x[1] * x[1] + eps) / (E * E);
-            double dl_da2 = w_isl + w_psl * exp(beta * (a2 - psl_soft));
+            double p = isinf(beta) ? ((k == peak[0] && m == peak[1]) ? 1.0 : 0.0)
+                                   : exp(beta * (a2 - psl_soft));
+            double dl_da2 = w_isl + w_psl * p;
             x[0] *= dl_da2 / (E * E);
             x[1] *= dl_da2 / (E * E);
         }
@@ -398,6 +439,53 @@ int orc_grad(const double* s, int64_t N, int64_t M, const int64_t win6[6], doubl
     free(gparts);
     free(X);
     free(W);
+    return ORC_OK;
+}
+
+/* The arg-max cell of Ahat^2 over Omega that the hard PSL (beta = +infinity)
+ * differentiates through: the first in row-major window order among the
+ * cells whose Ahat^2 equals the maximum (see loss_from_X). */
+int orc_peak_cell(const double* s, int64_t N, int64_t M, const int64_t win6[6], double eps,
+                  int64_t peak[2], int nthreads) {
+    orc_window w = {win6[0], win6[1], win6[2], win6[3], win6[4], win6[5]};
+    if (check_window(N, M, &w) || eps < 0.0) return ORC_EINVAL;
+    int64_t cells = (w.k_hi - w.k_lo + 1) * (w.m_hi - w.m_lo + 1);
+    double* X = (double*)malloc(sizeof(double) * 2 * (size_t)cells);
+    if (!X) return ORC_ENOMEM;
+    double out[8];
+    int st = orc_af_complex(s, N, M, w.k_lo, w.k_hi, w.m_lo, w.m_hi, X, nthreads);
+    if (!st) st = loss_from_X(X, &w, orc_energy(s, N), eps, 1.0, 0.0, INFINITY, out, peak);
+    free(X);
+    return st;
+}
+
+/* Gradient of one cell's Ahat^2[k,m] = (|X[k,m]|^2 + eps) / E^2 (the term
+ * the hard PSL adds, times w_psl): the cell adjoint G = X[k,m] / E^2 at that
+ * cell alone, the row adjoint and the two product-rule scatters of adj_worker,
+ * and the energy term -(2/E) Ahat^2[k,m] s.  Exported as orc_grad's. */
+int orc_cell_grad(const double* s, int64_t N, int64_t M, int64_t k, int64_t m, double eps,
+                  double* grad_s, double* grad_phi) {
+    orc_window w = {k, k, m, m, -1, -1};
+    if (check_window(N, M, &w) || eps < 0.0) return ORC_EINVAL;
+    double* W = make_w_table(M);
+    double* g = (double*)calloc(2 * (size_t)N, sizeof(double));
+    if (!W || !g) { free(W); free(g); return ORC_ENOMEM; }
+    double G[2];
+    af_cell(s, N, M, W, k, m, &G[0], &G[1]);
+    double E = orc_energy(s, N);
+    double a2 = (G[0] * G[0] + G[1] * G[1] + eps) / (E * E);
+    G[0] /= E * E;
+    G[1] /= E * E;
+    adj_job job = {s, N, M, W, w, G, 0, 1, g};
+    adj_worker(&job);
+    double dlde = -(2.0 / E) * a2;
+    for (int64_t n = 0; n < N; ++n) {
+        double gr = g[2 * n] + dlde * s[2 * n], gi = g[2 * n + 1] + dlde * s[2 * n + 1];
+        if (grad_s) { grad_s[2 * n] = 2.0 * gr; grad_s[2 * n + 1] = 2.0 * gi; }
+        if (grad_phi) grad_phi[n] = 2.0 * (gi * s[2 * n] - gr * s[2 * n + 1]);
+    }
+    free(W);
+    free(g);
     return ORC_OK;
 }
 
@@ -525,7 +613,7 @@ int orc_ploss(const double* s, int64_t N, int sign, const int64_t win6[6], doubl
     double* X = (double*)malloc(sizeof(double) * 2 * (size_t)cells);
     if (!X) return ORC_ENOMEM;
     int st = orc_paf_complex(s, N, sign, w.k_lo, w.k_hi, w.m_lo, w.m_hi, X);
-    if (!st) st = loss_from_X(X, &w, orc_energy(s, N), eps, w_psl, w_isl, beta, out);
+    if (!st) st = loss_from_X(X, &w, orc_energy(s, N), eps, w_psl, w_isl, beta, out, NULL);
     free(X);
     return st;
 }
@@ -547,15 +635,19 @@ int orc_pgrad(const double* s, int64_t N, int sign, const int64_t win6[6], doubl
     if (!X || !W || !g) { free(X); free(W); free(g); return ORC_ENOMEM; }
     int st = orc_paf_complex(s, N, sign, w.k_lo, w.k_hi, w.m_lo, w.m_hi, X);
     double E = orc_energy(s, N);
-    if (!st) st = loss_from_X(X, &w, E, eps, w_psl, w_isl, beta, out);
+    int64_t peak[2];
+    if (!st) st = loss_from_X(X, &w, E, eps, w_psl, w_isl, beta, out, peak);
     if (st) { free(X); free(W); free(g); return st; }
     double psl_soft = out[1];
     for (int64_t r = 0; r < rows; ++r)
         for (int64_t c = 0; c < ncols; ++c) {
             double* x = X + 2 * (r * ncols + c);
-            if (!in_omega(&w, w.k_lo + r, w.m_lo + c)) { x[0] = x[1] = 0.0; continue; }
+            int64_t k = w.k_lo + r, m = w.m_lo + c;
+            if (!in_omega(&w, k, m)) { x[0] = x[1] = 0.0; continue; }
             double a2 = (x[0] * x[0] + x[1] * x[1] + eps) / (E * E);
-            double dl_da2 = w_isl + w_psl * exp(beta * (a2 - psl_soft));
+            double p = isinf(beta) ? ((k == peak[0] && m == peak[1]) ? 1.0 : 0.0)
+                                   : exp(beta * (a2 - psl_soft));
+            double dl_da2 = w_isl + w_psl * p;
             x[0] *= dl_da2 / (E * E);
             x[1] *= dl_da2 / (E * E);
         }
@@ -587,6 +679,60 @@ int orc_pgrad(const double* s, int64_t N, int sign, const int64_t win6[6], doubl
         if (grad_phi) grad_phi[n] = 2.0 * (gi * s[2 * n] - gr * s[2 * n + 1]);
     }
     free(X);
+    free(W);
+    free(g);
+    return ORC_OK;
+}
+
+/* The arg-max cell of the periodic AF's Ahat^2 over Omega (as orc_peak_cell). */
+int orc_ppeak_cell(const double* s, int64_t N, int sign, const int64_t win6[6], double eps, int64_t peak[2]) {
+    orc_window w = {win6[0], win6[1], win6[2], win6[3], win6[4], win6[5]};
+    if (check_pwindow(N, &w) || eps < 0.0) return ORC_EINVAL;
+    int64_t cells = (w.k_hi - w.k_lo + 1) * (w.m_hi - w.m_lo + 1);
+    double* X = (double*)malloc(sizeof(double) * 2 * (size_t)cells);
+    if (!X) return ORC_ENOMEM;
+    double out[8];
+    int st = orc_paf_complex(s, N, sign, w.k_lo, w.k_hi, w.m_lo, w.m_hi, X);
+    if (!st) st = loss_from_X(X, &w, orc_energy(s, N), eps, 1.0, 0.0, INFINITY, out, peak);
+    free(X);
+    return st;
+}
+
+/* Gradient of one periodic cell's Ahat^2[k,m] = (|X[k,m]|^2 + eps) / E^2:
+ * G = X[k,m] / E^2 at that cell, G_R[n] = G conj(exp(sign j 2 pi m n / N)),
+ * the product rule on R[k,n] = s[n] conj(s[(n-k) mod N]) as in orc_pgrad, and
+ * the energy term -(2/E) Ahat^2 s. */
+int orc_pcell_grad(const double* s, int64_t N, int sign, int64_t k, int64_t m, double eps, double* grad_s,
+                   double* grad_phi) {
+    orc_window w = {k, k, m, m, -1, -1};
+    if (check_pwindow(N, &w) || (sign != 1 && sign != -1) || eps < 0.0) return ORC_EINVAL;
+    double* W = make_pw_table(N, sign);
+    double* g = (double*)calloc(2 * (size_t)N, sizeof(double));
+    if (!W || !g) { free(W); free(g); return ORC_ENOMEM; }
+    double G[2];
+    paf_cell(s, N, W, k, m, &G[0], &G[1]);
+    double E = orc_energy(s, N);
+    double a2 = (G[0] * G[0] + G[1] * G[1] + eps) / (E * E);
+    G[0] /= E * E;
+    G[1] /= E * E;
+    for (int64_t n = 0; n < N; ++n) {
+        int64_t q = (mod_i64(m, N) * n) % N;
+        double wr = W[2 * q], wi = -W[2 * q + 1]; /* conj */
+        double gr = G[0] * wr - G[1] * wi, gi = G[0] * wi + G[1] * wr;
+        int64_t j = mod_i64(n - k, N);
+        double ar = s[2 * j], ai = s[2 * j + 1];
+        g[2 * n] += gr * ar - gi * ai;
+        g[2 * n + 1] += gr * ai + gi * ar;
+        double br = s[2 * n], bi = s[2 * n + 1];
+        g[2 * j] += gr * br + gi * bi;
+        g[2 * j + 1] += gr * bi - gi * br;
+    }
+    double dlde = -(2.0 / E) * a2;
+    for (int64_t n = 0; n < N; ++n) {
+        double gr = g[2 * n] + dlde * s[2 * n], gi = g[2 * n + 1] + dlde * s[2 * n + 1];
+        if (grad_s) { grad_s[2 * n] = 2.0 * gr; grad_s[2 * n + 1] = 2.0 * gi; }
+        if (grad_phi) grad_phi[n] = 2.0 * (gi * s[2 * n] - gr * s[2 * n + 1]);
+    }
     free(W);
     free(g);
     return ORC_OK;
