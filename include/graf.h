@@ -355,9 +355,11 @@ GRAF_API graf_status_t graf_mlp_backward(int32_t rows, const float* master, cons
  *   exits.  A shape whose graf_af_backward_workspace_bytes() exceeds it
  *   returns GRAF_ERR_WORKSPACE; invalid arguments return
  *   GRAF_ERR_INVALID_ARG.  Nothing is allocated or freed.
- *   The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before any stream capture.
+ *   Every call looks up the array's device address (cudaGetSymbolAddress)
+ *   in the context current at the call, so it stays right after a device
+ *   reset and under a caller-created context; the first call in a context
+ *   also loads the library's module there, so make that first call before
+ *   any stream capture.
  *   All calls share the one array and it keeps the last call's contents:
  *   calls that can overlap on the GPU (different streams, or several host
  *   threads) race on it and must be serialised by the caller.

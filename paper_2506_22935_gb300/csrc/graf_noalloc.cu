@@ -11,10 +11,11 @@
 //
 // The array is reached from host code only through cudaGetSymbolAddress: on
 // the host, the name `g_noalloc_scratch` is a stand-in object, not a device
-// address, and must never be passed to a kernel.
+// address, and must never be passed to a kernel.  The address is looked up on
+// every call, in the context current at that call: a device reset or a
+// caller-created (non-primary) context gives the array a new address, so no
+// address is kept from one call to the next.
 #include <cuda_runtime.h>
-
-#include <mutex>
 
 #include "graf.h"
 
@@ -22,24 +23,6 @@ namespace {
 
 // GRAF_NOALLOC_SCRATCH_BYTES of device memory, 256-byte aligned.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[GRAF_NOALLOC_SCRATCH_BYTES];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device, resolved on the
-// first call for that device.  Returns nullptr on a CUDA error.
-void* scratch_on_current_device() {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return nullptr;
-        g_scratch_ptr[dev] = p;
-    }
-    return g_scratch_ptr[dev];
-}
 
 }  // namespace
 
@@ -51,8 +34,10 @@ extern "C" graf_status_t graf_af_loss_backward_noalloc(const void* x, graf_input
     const size_t need = graf_af_backward_workspace_bytes(B, N, M, w);
     if (need == 0) return GRAF_ERR_INVALID_ARG;
     if (need > (size_t)GRAF_NOALLOC_SCRATCH_BYTES) return GRAF_ERR_WORKSPACE;
-    void* scratch = scratch_on_current_device();
-    if (!scratch) return GRAF_ERR_CUDA;
+    // the array's address in the current context (the first call in a context
+    // loads the module there)
+    void* scratch = nullptr;
+    if (cudaGetSymbolAddress(&scratch, g_noalloc_scratch) != cudaSuccess || !scratch) return GRAF_ERR_CUDA;
     // every scratch byte the kernels read is written earlier in the same call
     // (per-CTA records and partial gradients), so nothing needs clearing
     return graf_af_loss_backward(x, kind, B, N, M, w, l, out8, dL, grad_s, grad_phi, scratch,

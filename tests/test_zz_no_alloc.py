@@ -6,6 +6,11 @@ workspace, on consecutive calls that reuse its fixed scratch array.
 
 This file is collected last on purpose, so a stop-at-first-failure run has
 already run every other test if this one fails."""
+import json
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
 
@@ -85,3 +90,16 @@ def test_no_alloc_rejects_shapes_beyond_its_scratch():
                                          out8.data_ptr(), None, None, out8.data_ptr(),
                                          torch.cuda.current_stream().cuda_stream)
     assert st == 7  # GRAF_ERR_WORKSPACE
+
+
+def test_no_alloc_in_a_caller_created_context():
+    """The scratch array's address is looked up in the context current at
+    each call: calls in the primary context, in a context the caller creates
+    with the driver API, and in the primary context again all match the
+    workspace path (run in a child process that never loads torch)."""
+    _build.build()
+    child = os.path.join(os.path.dirname(os.path.abspath(__file__)), "noalloc_context_child.py")
+    r = subprocess.run([sys.executable, child], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    rep = json.loads(r.stdout.strip().splitlines()[-1])
+    assert rep["ok"], rep
