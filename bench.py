@@ -36,7 +36,7 @@ UNIT = "Gcells/s"
 WORKLOAD = ("256 random polyphase codes, N=1024, M=2048, all 2047 delays x 2048 Doppler bins, "
             "PSL(log-sum-exp beta=50)+ISL, forward + Wirtinger backward w.r.t. phases")
 FLOP_PER_ROW = 5.0 * M * math.log2(M)  # nominal radix-2 count of one M-point FFT
-SMS, FP32_LANES = 152, 128
+FP32_LANES = 128  # FP32 FMA lanes per SM (Blackwell: 4 partitions x 32)
 
 
 def _env_rank():
@@ -71,6 +71,19 @@ def _measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def _fp32_peak(dev):
+    """FP32 FMA peak of `dev` in TFLOP/s: the SM count read from the device
+    (cudaDevAttrMultiProcessorCount through torch) x 128 lanes x 2 flop x the
+    maximum SM clock of MEASURED_PEAKS.json; and how it was formed."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks, src = _measured_peaks()
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = sms * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    return peak, (f"FP32 FMA peak = {sms} SMs (read from the device) x {FP32_LANES} lanes x 2 x {mhz:.0f} MHz "
+                  f"(sm_max_mhz from MEASURED_PEAKS.json, {src})")
+
+
 # the sources af_fused_kernel<2048> is compiled from
 _FUSED_SOURCES = ("graf_af_impl.cuh", "graf_fft.cuh", "graf_kernels.cuh", "graf_af_m2048.cu", "gen_twiddles.py")
 
@@ -99,59 +112,85 @@ def _traffic_record():
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle sampling while the GPU is under load."""
-    FIELDS = ("clocks.sm,clocks.max.sm,utilization.gpu,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    """SM clock, power and clock-event reasons sampled in-process through
+    NVML (read-only queries, libnvidia-ml via ctypes) every `period` seconds
+    on a background thread while the `with` block runs.  Samples whose
+    reasons include "GPU idle" are not counted as under load."""
+    # NVML clock-event reason bits (nvml.h: nvmlClocksEventReason*)
+    IDLE, SW_POWER_CAP, HW_SLOWDOWN, SW_THERMAL, HW_THERMAL, HW_POWER_BRAKE = 0x1, 0x4, 0x8, 0x20, 0x40, 0x80
+    NAMES = ((SW_POWER_CAP, "sw_power_cap"), (HW_SLOWDOWN, "hw_slowdown"), (SW_THERMAL, "sw_thermal_slowdown"),
+             (HW_THERMAL, "hw_thermal_slowdown"), (HW_POWER_BRAKE, "hw_power_brake_slowdown"))
 
-    def __init__(self, index: int):
-        self.index = index
-        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
-        self.proc = None
+    def __init__(self, device, period: float = 0.01):
+        self.device, self.period = device, period
+        self.samples, self.error = [], None
+        self._stop = None
+        self._thread = None
+        self._nvml = self._handle = None
+
+    def _open(self):
+        import ctypes
+        import torch
+        nv = ctypes.CDLL("libnvidia-ml.so.1")
+        if nv.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit_v2 failed")
+        h = ctypes.c_void_p()
+        uuid = getattr(torch.cuda.get_device_properties(self.device), "uuid", None)
+        ok = False
+        if uuid is not None:
+            u = str(uuid)
+            u = u if u.startswith("GPU-") else "GPU-" + u
+            ok = nv.nvmlDeviceGetHandleByUUID(u.encode(), ctypes.byref(h)) == 0
+        if not ok:
+            idx = self.device.index if self.device.index is not None else 0
+            if nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(idx), ctypes.byref(h)) != 0:
+                raise OSError("no NVML handle for the device")
+        self._nvml, self._handle = nv, h
+        reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None)
+        self._reasons = reasons if reasons is not None else nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = ctypes.c_uint()
+        nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx))  # NVML_CLOCK_SM = 1
+        self.max_mhz = float(mx.value)
+
+    def _run(self):
+        import ctypes
+        nv, h = self._nvml, self._handle
+        clk, pw, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self._stop.is_set():
+            if nv.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(clk)) == 0 and \
+                    self._reasons(h, ctypes.byref(rs)) == 0:
+                p = float(pw.value) / 1e3 if nv.nvmlDeviceGetPowerUsage(h, ctypes.byref(pw)) == 0 else None
+                self.samples.append((float(clk.value), int(rs.value), p))
+            self._stop.wait(self.period)
 
     def __enter__(self):
+        import threading
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
-                 "-i", str(self.index)], stdout=self.file, stderr=subprocess.DEVNULL)
-        except OSError:
-            self.proc = None
-        time.sleep(0.3)
+            self._open()
+        except Exception as e:  # no NVML on this host: the line says so
+            self.error = f"{type(e).__name__}: {e}"
+            return self
+        self._stop = threading.Event()
+        self._thread = threading.Thread(target=self._run, daemon=True)
+        self._thread.start()
         return self
 
     def __exit__(self, *a):
-        if self.proc is not None:
-            time.sleep(0.25)
-            self.proc.terminate()
-            try:
-                self.proc.wait(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.proc.kill()
+        if self._thread is not None:
+            self._stop.set()
+            self._thread.join(timeout=5)
 
     def summary(self):
-        self.file.flush()
-        self.file.seek(0)
-        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
-        os.unlink(self.file.name)
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
-            r = [c.strip() for c in r]
-            if len(r) < 9:
-                continue
-            try:
-                clk, cmax, util = float(r[0]), float(r[1]), float(r[2])
-            except ValueError:
-                continue
-            mx = cmax
-            if util < 50:
-                continue
-            sm.append(clk)
-            for nm, v in zip(names, r[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples_under_load": len(sm)}
+        if self.error is not None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples_under_load": 0,
+                    "source": "NVML unavailable: " + self.error}
+        load = [x for x in self.samples if not (x[1] & self.IDLE)]
+        reasons = sorted({nm for _, r, _ in load for bit, nm in self.NAMES if r & bit})
+        pw = [p for _, _, p in load if p is not None]
+        return {"sm_mhz": statistics.median([c for c, _, _ in load]) if load else None,
+                "sm_max_mhz": self.max_mhz, "reasons": reasons, "samples_under_load": len(load),
+                "samples": len(self.samples), "power_w_max": max(pw) if pw else None,
+                "source": f"NVML in-process, every {self.period * 1e3:.0f} ms across warm-up and timed steps"}
 
 
 def _oracle_cols(cols, nthreads=None, want_grad=False):
@@ -248,23 +287,23 @@ def run_graf(args):
 
     launches_per_step = 3  # fused rows, loss finalisation, gradient reduction
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
-    with ClockSampler(dev.index) as clk:
-        for _ in range(args.warmup):
-            step_call(x.data_ptr(), out8.data_ptr(), grad.data_ptr())
-        torch.cuda.synchronize(dev)
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-        for i in range(args.steps):
-            flush.zero_()
-            e0, e1 = ev[i]
-            e0.record(stream)
-            step_call(x.data_ptr(), out8.data_ptr(), grad.data_ptr())
-            e1.record(stream)
-        torch.cuda.synchronize(dev)
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
+    clk = ClockSampler(dev).__enter__()  # sampled through the timed and the end-to-end steps
+    for _ in range(args.warmup):
+        step_call(x.data_ptr(), out8.data_ptr(), grad.data_ptr())
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    for i in range(args.steps):
+        flush.zero_()
+        e0, e1 = ev[i]
+        e0.record(stream)
+        step_call(x.data_ptr(), out8.data_ptr(), grad.data_ptr())
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
     step_ms = reduce_max_ms(sum(e0.elapsed_time(e1) for e0, e1 in ev), dist, dev)
     ms_per_step = step_ms / args.steps
     value = weak_value(world, cells, args.steps, step_ms)
@@ -293,6 +332,7 @@ def run_graf(args):
         b.record(stream)
         b.synchronize()
         e2e_ms += a.elapsed_time(b)
+    clk.__exit__(None, None, None)
     e2e_value = weak_value(world, cells, args.steps, reduce_max_ms(e2e_ms, dist, dev))
 
     if rank != 0:
@@ -318,9 +358,7 @@ def run_graf(args):
         del lc_, gc_
         torch.cuda.empty_cache()
 
-    peaks, src = _measured_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tflops = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    peak_tflops, peak_src = _fp32_peak(dev)
     # algorithmic work of one call: the forward DFT and its adjoint for every
     # one of the 2N-1 delay rows; executed: both transforms for the N rows
     # k >= 0 (rows -k are mirrors), minus the adjoint of row 0
@@ -330,8 +368,7 @@ def run_graf(args):
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": _traffic_record(),
                 "kernel": "af_fused_kernel<2048> (+ loss finalisation and gradient reduction in the same timing)",
-                "peak_source": f"FP32 FMA peak = {SMS} SMs x {FP32_LANES} lanes x 2 x {sm_max:.0f} MHz "
-                               f"(sm_max_mhz from MEASURED_PEAKS.json, {src})",
+                "peak_source": peak_src,
                 "algorithmic_flop_per_launch": alg,
                 "executed_flop_per_launch": executed,
                 "executed_frac": executed / (ms_per_step / 1e3) / 1e12 / peak_tflops}
@@ -463,16 +500,14 @@ def run_optim(args):
         opt.reset(phi0)
         opt.run(STEPS, graph=True)
 
-    with ClockSampler(0) as clk:
+    with ClockSampler(torch.device('cuda', 0)) as clk:
         ms_graph = _timed_events(graph_run, runs, 1, stream)
     hist = opt.history.cpu().numpy()
     ms_eager = _timed_events(lambda: (opt.reset(phi0), opt.run(STEPS, graph=False)), 1, 1, stream)
     rows = 2 * K3 + 1
     alg_step = B3 * 2 * rows * 5.0 * M3 * math.log2(M3)
     exe_step = B3 * 2 * (K3 + 1) * 5.0 * M3 * math.log2(M3)   # both transforms of the rows k >= 0
-    peaks, src = _measured_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    peak, peak_src = _fp32_peak(dev)
     achieved = alg_step * STEPS / (ms_graph / 1e3) / 1e12
     cpu = None
     if not args.no_cpu_baseline:
@@ -497,7 +532,7 @@ def run_optim(args):
                          "frac": achieved / peak, "traffic": None,
                          "algorithmic_flop_per_step": alg_step, "executed_flop_per_step": exe_step,
                          "executed_frac": achieved * exe_step / alg_step / peak,
-                         "peak_source": f"FP32 FMA peak at {sm_max:.0f} MHz ({src})"},
+                         "peak_source": peak_src},
             "isl_median_start": float(np.median(hist[0])), "isl_median_end": float(np.median(hist[-1])),
             "cpu_baseline": cpu, "gpu_launches": 5 * STEPS * runs, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
@@ -541,7 +576,7 @@ def run_ragged(args):
     say(f"untuned plan {ms_default:.2f} ms/step")
     cache = os.path.join(tempfile.gettempdir(), "graf_autotune_ragged.txt")
     plan.autotune(x, cache_path=cache)
-    with ClockSampler(0) as clk:
+    with ClockSampler(torch.device('cuda', 0)) as clk:
         ms_tuned = _timed_events(plan_step, steps, 3, stream, flush)
     info = plan.info()
     torch.cuda.synchronize()
@@ -608,9 +643,7 @@ def run_ragged(args):
         del res, parts
         torch.cuda.empty_cache()
     plan.close()
-    peaks, src = _measured_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    peak, peak_src = _fp32_peak(dev)
     achieved = alg / (ms_tuned / 1e3) / 1e12
     line = {"metric": "ragged-batch AF fwd+bwd Gcells/s", "value": cells / (ms_tuned / 1e3) / 1e9,
             "unit": UNIT, "higher_is_better": True, "n_gpus": 1, "steps": steps, "warmup": 3,
@@ -624,7 +657,7 @@ def run_ragged(args):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None, "algorithmic_flop_per_step": alg,
                          "executed_flop_per_step": exe, "executed_frac": achieved * exe / alg / peak,
-                         "peak_source": f"FP32 FMA peak at {sm_max:.0f} MHz ({src})"},
+                         "peak_source": peak_src},
             "cufft_pipeline": cmp, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
@@ -658,14 +691,12 @@ def run_periodic(args):
         assert st == 0, g.graf_status_string(st)
 
     steps = max(3, min(args.steps, 100))
-    with ClockSampler(0) as clk:
+    with ClockSampler(torch.device('cuda', 0)) as clk:
         ms = _timed_events(step, steps, 5, stream, flush)
     cells = Bp * Np * Np
     alg = Bp * 2 * Np * 5.0 * Np * math.log2(Np)   # forward + adjoint DFT of every delay row
     exe = Bp * 2 * (Np // 2 + 1) * 5.0 * Np * math.log2(Np)   # rows 0..N/2 (row N - k mirrors row k)
-    peaks, src = _measured_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    peak, peak_src = _fp32_peak(dev)
     achieved = alg / (ms / 1e3) / 1e12
     chi = g.paf_forward(x[:64], 1, normalise=True)
     torch.cuda.synchronize()
@@ -679,7 +710,7 @@ def run_periodic(args):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None, "algorithmic_flop_per_step": alg,
                          "executed_flop_per_step": exe, "executed_frac": achieved * exe / alg / peak,
-                         "peak_source": f"FP32 FMA peak at {sm_max:.0f} MHz ({src})"},
+                         "peak_source": peak_src},
             "mean_psl_hard": float(out8[:, 3].mean()), "mean_chi_max": float(chi.amax(dim=(1, 2)).mean()),
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
@@ -706,7 +737,7 @@ def run_lpi(args):
     phi0 = torch.from_numpy(inputs.random_phases(seed, Bl, Nl)).to(dev)
     win = g.Window.periodic(Nl)
     res = {}
-    with ClockSampler(0) as clk:
+    with ClockSampler(torch.device('cuda', 0)) as clk:
         for lam in (0.0, 0.5, 1.0, 2.0):
             phi = phi0.clone()
             opt = PhaseOptimizer(phi, window=win, loss=g.Loss(1.0, 0.0, BETA_L, EPS), adam=Adam(lr=1e-2),

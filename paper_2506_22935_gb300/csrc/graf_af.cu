@@ -15,6 +15,15 @@ __device__ unsigned int g_device_error_taken;
 
 __global__ void take_device_error_kernel() { g_device_error_taken = atomicExch(&g_device_error, 0u); }
 
+int device_sm_count() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+        return sms;
+    cudaGetLastError();  // no device: clear the error the failed query recorded
+    return 152;
+}
+
 // |Omega| = |window| - |window intersect mainlobe box|, exact in int64.
 __device__ __forceinline__ long long omega_count(const Wave& p) {
     const long long nk = p.k_hi - p.k_lo + 1, nm = p.m_hi - p.m_lo + 1;

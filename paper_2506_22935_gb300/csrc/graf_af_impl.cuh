@@ -1202,8 +1202,8 @@ static cudaError_t launch_rows(K kernel, size_t smem, const AfParams& p, cudaStr
     if (e != cudaSuccess) return e;
     long long grid = (long long)p.B * p.tiles;
     if (p.items) {  // persistent: as many CTAs as fit on the SMs at once
-        int dev = 0, sms = kSmsTarget, per_sm = 1;
-        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int sms = device_sm_count();
+        int per_sm = 1;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, P::THREADS, smem) != cudaSuccess ||
             per_sm < 1)
             per_sm = 1;

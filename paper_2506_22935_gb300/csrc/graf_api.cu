@@ -95,7 +95,7 @@ struct FusedPlan {
 FusedPlan fused_plan(int32_t B, int32_t N, int32_t M, const graf_window_t& w, bool psl, bool phase_only) {
     FusedPlan f{};
     const bool full_m = (w.m_lo == -(M / 2) && w.m_hi == M / 2 - 1);
-    f.T1 = graf::make_tiling(B, M, w.k_lo, w.k_hi);
+    f.T1 = graf::make_tiling(B, M, w.k_lo, w.k_hi, graf::device_sm_count());
     f.fused = !psl || full_m;
     f.defer_hi = -1;
     f.deferred_launch = false;
@@ -104,7 +104,7 @@ FusedPlan fused_plan(int32_t B, int32_t N, int32_t M, const graf_window_t& w, bo
         const int lo = (phase_only && f.T1.r_lo == 0) ? 1 : f.T1.r_lo;  // row 0: no phase gradient
         if (lo <= f.defer_hi) {
             f.deferred_launch = true;
-            f.T2 = graf::make_tiling_rows(B, M, lo, f.defer_hi);
+            f.T2 = graf::make_tiling_rows(B, M, lo, f.defer_hi, graf::device_sm_count());
         }
     }
     (void)N;
@@ -156,7 +156,7 @@ static graf_status_t af_forward_impl(const Mode& md, const void* x, graf_input_t
     if (s != GRAF_OK) return s;
     if (!af_out || !(eps >= 0.0f) || eps > 1e30f) return GRAF_ERR_INVALID_ARG;
     if (graf::row_kernel_smem(M, store_len(md, N), 0) > graf::kMaxSmem) return GRAF_ERR_UNSUPPORTED;
-    const Tiling T = graf::make_tiling(B, M, w.k_lo, w.k_hi);
+    const Tiling T = graf::make_tiling(B, M, w.k_lo, w.k_hi, graf::device_sm_count());
     AfParams p = base_params(x, kind, B, N, M, w, T, md);
     p.eps = eps;
     p.chi_out = chi_out;
@@ -166,7 +166,7 @@ static graf_status_t af_forward_impl(const Mode& md, const void* x, graf_input_t
 
 static size_t loss_ws_impl(const Mode& md, int32_t B, int32_t N, int32_t M, graf_window_t w) {
     if (check_shape(B, N, M) != GRAF_OK || check_window(N, M, w, md) != GRAF_OK) return 0;
-    return loss_ws(B, graf::make_tiling(B, M, w.k_lo, w.k_hi));
+    return loss_ws(B, graf::make_tiling(B, M, w.k_lo, w.k_hi, graf::device_sm_count()));
 }
 
 static graf_status_t af_loss_impl(const Mode& md, const void* x, graf_input_t kind, int32_t B, int32_t N,
@@ -177,7 +177,7 @@ static graf_status_t af_loss_impl(const Mode& md, const void* x, graf_input_t ki
     if ((s = check_loss(l)) != GRAF_OK) return s;
     if (!out8) return GRAF_ERR_INVALID_ARG;
     if (graf::row_kernel_smem(M, store_len(md, N), 0) > graf::kMaxSmem) return GRAF_ERR_UNSUPPORTED;
-    const Tiling T = graf::make_tiling(B, M, w.k_lo, w.k_hi);
+    const Tiling T = graf::make_tiling(B, M, w.k_lo, w.k_hi, graf::device_sm_count());
     if (!workspace || workspace_bytes < loss_ws(B, T)) return GRAF_ERR_WORKSPACE;
     if (reinterpret_cast<uintptr_t>(workspace) & 255) return GRAF_ERR_WORKSPACE;
     AfParams p = base_params(x, kind, B, N, M, w, T, md);
@@ -189,7 +189,7 @@ static graf_status_t af_loss_impl(const Mode& md, const void* x, graf_input_t ki
 
 static size_t backward_ws_impl(const Mode& md, int32_t B, int32_t N, int32_t M, graf_window_t w) {
     if (check_shape(B, N, M) != GRAF_OK || check_window(N, M, w, md) != GRAF_OK) return 0;
-    const Tiling T = graf::make_tiling(B, M, w.k_lo, w.k_hi);
+    const Tiling T = graf::make_tiling(B, M, w.k_lo, w.k_hi, graf::device_sm_count());
     size_t s = loss_ws(B, T);
     const size_t b = backward_ws(B, N, T);
     if (b > s) s = b;
@@ -211,7 +211,7 @@ static graf_status_t af_backward_impl(const Mode& md, const void* x, graf_input_
     if ((s = check_loss(l)) != GRAF_OK) return s;
     if (!saved8 || (!grad_s && !grad_phi)) return GRAF_ERR_INVALID_ARG;
     if (grad_phi && kind != GRAF_IN_PHASE) return GRAF_ERR_INVALID_ARG;
-    const Tiling T = graf::make_tiling(B, M, w.k_lo, w.k_hi);
+    const Tiling T = graf::make_tiling(B, M, w.k_lo, w.k_hi, graf::device_sm_count());
     if (!workspace || workspace_bytes < backward_ws(B, N, T)) return GRAF_ERR_WORKSPACE;
     if (reinterpret_cast<uintptr_t>(workspace) & 255) return GRAF_ERR_WORKSPACE;
     AfParams p = base_params(x, kind, B, N, M, w, T, md);
@@ -391,7 +391,7 @@ graf_status_t graf_composite_terms(const void* x, graf_input_t kind, int32_t B, 
 // ------------------------------------------------------------ match term
 size_t graf_af_match_workspace_bytes(int32_t B, int32_t N, int32_t M, graf_window_t w) {
     if (check_shape(B, N, M) != GRAF_OK || check_window(N, M, w) != GRAF_OK) return 0;
-    const Tiling T = graf::make_tiling(B, M, w.k_lo, w.k_hi);
+    const Tiling T = graf::make_tiling(B, M, w.k_lo, w.k_hi, graf::device_sm_count());
     return backward_ws(B, N, T) + csum_bytes(B, T);
 }
 
@@ -403,7 +403,7 @@ graf_status_t graf_af_match(const void* x, graf_input_t kind, int32_t B, int32_t
     if (s != GRAF_OK) return s;
     if (!target || !(weight == weight) || !(eps >= 0.0f) || eps > 1e30f) return GRAF_ERR_INVALID_ARG;
     if (grad_phi && kind != GRAF_IN_PHASE) return GRAF_ERR_INVALID_ARG;
-    const Tiling T = graf::make_tiling(B, M, w.k_lo, w.k_hi);
+    const Tiling T = graf::make_tiling(B, M, w.k_lo, w.k_hi, graf::device_sm_count());
     if (!workspace || workspace_bytes < graf_af_match_workspace_bytes(B, N, M, w)) return GRAF_ERR_WORKSPACE;
     if (reinterpret_cast<uintptr_t>(workspace) & 255) return GRAF_ERR_WORKSPACE;
     const int phase_only = (kind == GRAF_IN_PHASE && grad_s == nullptr) ? 1 : 0;

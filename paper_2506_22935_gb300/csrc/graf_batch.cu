@@ -289,7 +289,7 @@ static graf_status_t create_plan(int32_t B, const int32_t* N_host, const int32_t
         d.N = N;
         d.M = M;
         d.k_lo = w.k_lo; d.k_hi = w.k_hi; d.m_lo = w.m_lo; d.m_hi = w.m_hi; d.k_ml = w.k_ml; d.m_ml = w.m_ml;
-        const graf::Tiling T = graf::make_tiling(1, M, w.k_lo, w.k_hi);
+        const graf::Tiling T = graf::make_tiling(1, M, w.k_lo, w.k_hi, 1);
         d.r_lo = T.r_lo;
         d.r_hi = T.r_hi;
         d.eps = l.eps; d.beta = l.beta; d.w_psl = l.w_psl; d.w_isl = l.w_isl;

@@ -11,7 +11,11 @@
 namespace graf {
 
 constexpr int kThreads = 256;     // threads per CTA of the row kernels (RowPlan<M>::THREADS for the largest M)
-constexpr int kSmsTarget = 152;   // GB300 SM count, used to size tiles
+
+// Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount),
+// read at every call; 152 (a GB300) only when no CUDA device is visible, so that
+// workspace sizes can still be queried on a host without a GPU.
+int device_sm_count();
 
 // Per-waveform parameters of a batch of unequal waveforms (device table, one
 // entry per waveform).  Offsets are in elements of the arrays they index.
@@ -75,6 +79,11 @@ struct AfParams {
     const int2* items;     // (waveform, tile) of this launch's work items, longest first
     int n_items;
     unsigned int* counter; // zeroed before the launch
+    // hard PSL (beta = +inf): per waveform {transformed row k >= 0 of the
+    // arg-max cell (-1: Omega empty), its cell code (bin q >= 0, or -1 - t: one
+    // of the bins of thread t of the row), float bits of max Ahat^2, 0},
+    // written by the loss finalisation (nullable)
+    int4* peak;
 };
 
 // Spectral variance of the normalised power spectrum (the LPI term of the
@@ -131,6 +140,12 @@ struct Wave {
     int periodic, pconj;
     int sN;         // shared-memory length of the signal: N, or 2N periodic
     float eps, beta, w_psl, w_isl;
+    // Hard PSL (the loss's beta = +inf): L = w_peak max_Omega Ahat^2 + w_isl ISL.
+    // The view then carries beta = 0 and w_psl = 0, so that the kernels' soft
+    // log-sum-exp term vanishes and they compute ISL and the maximum; the
+    // maximum's gradient is added through its arg-max cell (peak_grad_kernel).
+    int hard;
+    float w_peak;
     // Fixed log-sum-exp shift (in units of Ahat^2), 0 = none.  For phase
     // input E = N and every cell has a2 = |X|^2/E^2 + eps/E^2 <= 1 + eps/N^2
     // (|X[k,m]| <= E by Cauchy-Schwarz), so with m = (1 + eps/N^2)/2 the terms
@@ -139,6 +154,9 @@ struct Wave {
     // relative to this shift when it is set, else relative to their maximum.
     float lse_fix;
 };
+
+// beta = +inf selects the hard PSL (larger than any finite float).
+__host__ __device__ __forceinline__ bool is_hard_beta(float beta) { return beta > 3.4028234e38f; }
 
 // The fixed log-sum-exp shift of a waveform (see Wave::lse_fix), 0 = none.
 // Host code uses it too: with a fixed shift no accumulator is ever rescaled,
@@ -182,6 +200,12 @@ __host__ __device__ __forceinline__ Wave wave_of(const AfParams& p, int b) {
     }
     w.sN = w.periodic ? 2 * w.N : w.N;
     w.full_m = (w.m_lo == -(w.M / 2) && w.m_hi == w.M / 2 - 1) ? 1 : 0;
+    w.hard = is_hard_beta(w.beta) ? 1 : 0;
+    w.w_peak = w.hard ? w.w_psl : 0.0f;
+    if (w.hard) {
+        w.beta = 0.0f;
+        w.w_psl = 0.0f;
+    }
     w.lse_fix = lse_fixed_shift(w.kind, w.eps, w.beta, w.N);
     return w;
 }
@@ -259,6 +283,10 @@ template <int M> cudaError_t run_backward_m(const AfParams& p, cudaStream_t st);
 template <int M> cudaError_t run_fused_m(const AfParams& p, cudaStream_t st);
 cudaError_t run_fused(const AfParams& p, cudaStream_t st);
 cudaError_t run_finalize(const AfParams& p, cudaStream_t st);
+// Hard PSL: add (accumulate != 0) or write dL w_peak dAhat^2[peak]/d(s or phi)
+// for every waveform from the peak records of the finalisation.
+cudaError_t run_peak_grad(const AfParams& p, const float* dL, float2* grad_s, float* grad_phi, int accumulate,
+                          cudaStream_t st);
 cudaError_t run_grad_reduce(const AfParams& p, const float* dL, float2* grad_s, float* grad_phi,
                             cudaStream_t st);
 cudaError_t run_forward(const AfParams& p, cudaStream_t st);
@@ -267,8 +295,9 @@ cudaError_t run_backward(const AfParams& p, const float* dL, float2* grad_s, flo
                          cudaStream_t st);
 
 // Tiles of transformed rows [r_lo, r_hi] for B waveforms: rows per CTA a
-// multiple of the slot count, at least 4 CTAs per SM where the batch allows.
-inline Tiling make_tiling_rows(int B, int M, int r_lo, int r_hi) {
+// multiple of the slot count, at least 4 CTAs per SM (of `sms` SMs) where the
+// batch allows.
+inline Tiling make_tiling_rows(int B, int M, int r_lo, int r_hi, int sms) {
     Tiling T;
     T.r_lo = r_lo;
     T.r_hi = r_hi;
@@ -279,7 +308,7 @@ inline Tiling make_tiling_rows(int B, int M, int r_lo, int r_hi) {
     int rps = M >= 128 ? 16 : 8;
     while (rps > 1) {
         long long tiles = (T.nrows + (long long)T.slots * rps - 1) / ((long long)T.slots * rps);
-        if ((long long)B * tiles >= 4LL * kSmsTarget) break;
+        if ((long long)B * tiles >= 4LL * sms) break;
         rps /= 2;
     }
     T.rows_per_tile = T.slots * rps;
@@ -289,10 +318,10 @@ inline Tiling make_tiling_rows(int B, int M, int r_lo, int r_hi) {
 
 // Rows k >= 0 whose transform serves the window: row k gives delay k and,
 // by |X[-k,m]| = |X[k,-m]|, delay -k.
-inline Tiling make_tiling(int B, int M, int k_lo, int k_hi) {
-    if (k_lo >= 0) return make_tiling_rows(B, M, k_lo, k_hi);
-    if (k_hi <= 0) return make_tiling_rows(B, M, -k_hi, -k_lo);
-    return make_tiling_rows(B, M, 0, (-k_lo > k_hi) ? -k_lo : k_hi);
+inline Tiling make_tiling(int B, int M, int k_lo, int k_hi, int sms) {
+    if (k_lo >= 0) return make_tiling_rows(B, M, k_lo, k_hi, sms);
+    if (k_hi <= 0) return make_tiling_rows(B, M, -k_hi, -k_lo, sms);
+    return make_tiling_rows(B, M, 0, (-k_lo > k_hi) ? -k_lo : k_hi, sms);
 }
 
 // ex2.approx (PTX): 2^x with relative error below 2^-22, +0 at -inf.

@@ -7,6 +7,10 @@
 
 #include "graf.h"
 
+namespace graf {
+int device_sm_count();  // graf_af.cu
+}
+
 namespace {
 
 // One Adam update (Kingma & Ba): t = *step + 1,
@@ -60,7 +64,8 @@ graf_status_t graf_adam_step(float* x, float* m, float* v, const float* grad, in
         !(hp.eps > 0.0f))
         return GRAF_ERR_INVALID_ARG;
     long long blocks = (count + 255) / 256;
-    if (blocks > 4 * 152) blocks = 4 * 152;
+    const long long cap = 4LL * graf::device_sm_count();
+    if (blocks > cap) blocks = cap;
     adam_kernel<<<(unsigned)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
         x, m, v, grad, count, hp, step, static_cast<unsigned int*>(state));
     return cudaGetLastError() == cudaSuccess ? GRAF_OK : GRAF_ERR_CUDA;

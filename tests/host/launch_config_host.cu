@@ -12,6 +12,8 @@
 
 using namespace graf;
 
+constexpr int kSms = 152;  // the SM count the tiling is checked with (a GB300)
+
 template <int M>
 void one() {
     using P = RowPlan<M>;
@@ -35,14 +37,14 @@ void one() {
         const int his[] = {0, 1, M / 2, M - 1};
         for (int hi : his) {
             if (hi < 0) continue;
-            const Tiling T = make_tiling_rows(B, M, 0, hi);
+            const Tiling T = make_tiling_rows(B, M, 0, hi, kSms);
             std::printf("tile %d %d %d %d %d %d %d\n", B, M, 0, hi, T.slots, T.rows_per_tile, T.tiles);
         }
     }
 }
 
 int main() {
-    std::printf("const %zu %zu %d\n", kMaxSmem, kSmemPerSm, kSmsTarget);
+    std::printf("const %zu %zu %d\n", kMaxSmem, kSmemPerSm, kSms);
     one<8>(); one<16>(); one<32>(); one<64>(); one<128>(); one<256>(); one<512>();
     one<1024>(); one<2048>(); one<4096>(); one<8192>(); one<16384>();
     return 0;
