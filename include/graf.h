@@ -16,7 +16,9 @@
  *   losses on the sidelobe region Omega (Eqs. 18, 19, 22):
  *                 ISL = sum_Omega Ahat^2,  PSL_hard = max_Omega Ahat^2,
  *                 PSL_soft = (1/beta) log sum_Omega exp(beta Ahat^2),
- *                 L = w_psl PSL_soft + w_isl ISL
+ *                 L = w_psl PSL_soft + w_isl ISL  (beta finite), or
+ *                 L = w_psl PSL_hard + w_isl ISL  (beta = +infinity: the hard
+ *                 maximum of Eq. 18, differentiated through one arg-max cell)
  *   gradient      Wirtinger calculus, Sec. 3.3 Eq. 6 and Sec. 4.2 Eqs. 13-15:
  *                 grad_s = 2 dL/ds* = dL/dRe(s) + j dL/dIm(s) (PyTorch's
  *                 convention) and, for s = exp(j phi), grad_phi = dL/dphi.
@@ -88,7 +90,12 @@ typedef struct {
 } graf_window_t;
 
 /* Composite loss weights (Eq. 22, lambda_2 = w_psl, lambda_3 = w_isl), the
- * soft-max temperature beta of PSL_soft and the magnitude stabiliser eps. */
+ * soft-max temperature beta of PSL_soft and the magnitude stabiliser eps.
+ * beta = +INFINITY selects the hard PSL of Eq. 18 (the beta -> infinity limit
+ * of PSL_soft): the PSL term is max_Omega Ahat^2 and its gradient is that of
+ * one arg-max cell's Ahat^2 (a subgradient; cells equal within FP32 rounding
+ * are all valid choices, and mirror cells (k, m), (-k, -m) are one function
+ * of s, so they give the same gradient).  Batch plans take finite beta only. */
 typedef struct {
     float w_psl, w_isl, beta, eps;
 } graf_loss_t;
@@ -150,8 +157,9 @@ GRAF_API size_t graf_af_loss_workspace_bytes(int32_t B, int32_t N, int32_t M, gr
  *   out8  float [B][GRAF_LOSS_OUT]: per waveform
  *         {L, PSL_soft, ISL, PSL_hard, E, |Omega|, S_p, 0}
  *         where S_p = sum_Omega p Ahat^2, p = exp(beta (Ahat^2 - PSL_soft)),
- *         the softmax-weighted term the energy gradient needs.  If Omega is
- *         empty, L = PSL_soft = ISL = PSL_hard = S_p = 0.
+ *         the softmax-weighted term the energy gradient needs.  With beta =
+ *         +infinity, PSL_soft and S_p are PSL_hard (their limits).  If Omega
+ *         is empty, L = PSL_soft = ISL = PSL_hard = S_p = 0.
  *   workspace  caller-owned scratch of graf_af_loss_workspace_bytes();
  *         too small -> GRAF_ERR_WORKSPACE.  Its contents are overwritten.
  */
@@ -170,7 +178,9 @@ GRAF_API size_t graf_af_backward_workspace_bytes(int32_t B, int32_t N, int32_t M
  * for both factors, and the energy term dL/dE * s.  The AF rows are
  * recomputed, never stored.
  *   saved8   [B][GRAF_LOSS_OUT] from graf_af_loss on the SAME x, window and
- *            loss (PSL_soft, ISL and S_p are used)
+ *            loss (PSL_soft, ISL and S_p are used).  With beta = +infinity
+ *            the call locates the arg-max cell itself (one more pass over
+ *            the rows) and does not read saved8.
  *   dL       float [B] upstream gradient dOut/dL per waveform, or NULL for 1
  *   grad_s   graf_c32 [B][N] = dL * (dL/dRe s + j dL/dIm s), or NULL
  *   grad_phi float [B][N] = dL * dL/dphi, or NULL; requires GRAF_IN_PHASE
@@ -230,16 +240,21 @@ GRAF_API graf_status_t graf_record_loss(const float* out8, int32_t B, float* his
  * waveform's delay rows into tiles, and orders the (waveform, tile) work
  * items longest first; each M then runs as one persistent launch whose CTAs
  * claim items from an atomic counter.  Plans own device memory (created and
- * freed here, never in the compute calls).  Phase input (GRAF_IN_PHASE) and
- * the phase gradient only.
+ * freed here, never in the compute calls).  A plan is made for one input
+ * kind: phase codes (GRAF_IN_PHASE, gradient dL/dphi through
+ * graf_batch_loss_backward) or complex signals (GRAF_IN_COMPLEX, gradient
+ * dL/dRe s + j dL/dIm s through graf_batch_loss_backward_complex); finite
+ * beta only (GRAF_ERR_UNSUPPORTED for +inf).
  *   N_host   host int32[B], 1 <= N_b
  *   M_host   host int32[B] (power of two, N_b <= M_b <= GRAF_M_MAX) or NULL
  *            for the next power of two >= 2 N_b
  *   w_host   host graf_window_t[B], or NULL for every delay and Doppler bin
  *            minus the zero-delay mainlobe box |m| < M_b / N_b
  *   l_host   host graf_loss_t[B] if losses_per_waveform, else [1] for all
+ *   kind     GRAF_IN_PHASE or GRAF_IN_COMPLEX (else GRAF_ERR_INVALID_ARG)
  * Packed layout: waveform b occupies elements [off_b, off_b + N_b) of the
- * input phases and of the gradient, off_b = N_0 + ... + N_{b-1}.
+ * input (float phases or graf_c32 samples) and of the gradient (likewise),
+ * off_b = N_0 + ... + N_{b-1}.
  */
 typedef struct graf_batch_plan_s* graf_batch_plan_t;
 
@@ -282,12 +297,46 @@ GRAF_API graf_status_t graf_batch_plan_info(graf_batch_plan_t plan, int32_t* n_b
 /*
  * graf_batch_loss_backward - loss scalars (out8 [B][GRAF_LOSS_OUT], as
  * graf_af_loss) and grad_phi (packed, dL_b * dL/dphi) for every waveform of
- * the plan.  dL: device float[B] or NULL for ones.  Enqueues on `stream`,
- * allocates nothing.
+ * a phase plan (a complex plan: GRAF_ERR_INVALID_ARG).  dL: device float[B]
+ * or NULL for ones.  Enqueues on `stream`, allocates nothing.
  */
 GRAF_API graf_status_t graf_batch_loss_backward(graf_batch_plan_t plan, const float* phi, float* out8,
                                                 const float* dL, float* grad_phi, void* workspace,
                                                 size_t workspace_bytes, void* stream);
+
+/*
+ * graf_batch_loss_backward_complex - the same for a complex plan (Sec. 4.3:
+ * batched s in C^{B x N}, here ragged): s packed graf_c32, grad_s packed
+ * graf_c32 = dL_b (dL/dRe s + j dL/dIm s), the Wirtinger gradient of
+ * Sec. 4.2 with the energy term of E = sum |s|^2 (a phase plan:
+ * GRAF_ERR_INVALID_ARG).
+ */
+GRAF_API graf_status_t graf_batch_loss_backward_complex(graf_batch_plan_t plan, const graf_c32* s, float* out8,
+                                                        const float* dL, graf_c32* grad_s, void* workspace,
+                                                        size_t workspace_bytes, void* stream);
+
+/*
+ * graf_batch_loss - the loss scalars alone (out8 [B][GRAF_LOSS_OUT], as
+ * graf_af_loss; Eqs. 18, 19, 22) for every waveform of the plan, x packed as
+ * the plan's input kind; the AF is not written.  Same workspace as the
+ * gradient calls.
+ */
+GRAF_API graf_status_t graf_batch_loss(graf_batch_plan_t plan, const void* x, float* out8, void* workspace,
+                                       size_t workspace_bytes, void* stream);
+
+/*
+ * graf_batch_af_offsets - host int64[B + 1]: waveform b's window occupies
+ * floats [off_b, off_{b+1}) of graf_batch_forward's output (off_B = total).
+ */
+GRAF_API graf_status_t graf_batch_af_offsets(graf_batch_plan_t plan, int64_t* af_off_host);
+
+/*
+ * graf_batch_forward - Ahat = sqrt(|X|^2 + eps) / E (Algorithm 1 with the
+ * aperiodic lag; Eqs. 8, 11, 12, 17) over every waveform's window, eps of its
+ * plan loss: waveform b's window at af_out + off_b (graf_batch_af_offsets),
+ * row-major [k_hi-k_lo+1][m_hi-m_lo+1] as graf_af_forward.  No workspace.
+ */
+GRAF_API graf_status_t graf_batch_forward(graf_batch_plan_t plan, const void* x, float* af_out, void* stream);
 
 /*
  * graf_batch_autotune - for every M of the plan, time the row kernel with

@@ -1,5 +1,7 @@
 // graf_af.cu - reductions that follow the row kernels (loss finalisation,
 // gradient reduction) and the dispatch over the row length M.
+#include <climits>
+
 #include <math_constants.h>
 
 #include "graf.h"
@@ -37,12 +39,72 @@ __device__ __forceinline__ long long omega_count(const Wave& p) {
     return nk * nm - bk * bm;
 }
 
+// Hard PSL (beta = +inf): merge the tile records {ISL, max, row, code} --
+// ISL in a fixed order, the arg-max by the larger value, then the smaller row,
+// then the smaller code -- into out8 = {w_peak max + w_isl ISL, max, ISL, max,
+// E, |Omega|, max, 0} (max is PSL_hard, and the limit of PSL_soft and of the
+// softmax-weighted mean S_p) and the waveform's peak record.
+__device__ void finalize_hard(const AfParams& p, const Wave& wv, int b, int lane, float* out8) {
+    double isl = 0.0;
+    float bv = -CUDART_INF_F;
+    int brow = INT_MAX, bcode = INT_MAX;
+    auto better = [](float v, int r, int c, float v2, int r2, int c2) {
+        return v > v2 || (v == v2 && (r < r2 || (r == r2 && c < c2)));
+    };
+    for (int i = lane; i < wv.tiles; i += 32) {
+        const float4 r = p.rec[wv.rec_off + i];
+        isl += r.x;
+        const int rr = __float_as_int(r.z), rc = __float_as_int(r.w);
+        if (r.y > -CUDART_INF_F && better(r.y, rr, rc, bv, brow, bcode)) {
+            bv = r.y;
+            brow = rr;
+            bcode = rc;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        isl += __shfl_xor_sync(0xffffffffu, isl, o);
+        const float v2 = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int r2 = __shfl_xor_sync(0xffffffffu, brow, o), c2 = __shfl_xor_sync(0xffffffffu, bcode, o);
+        if (better(v2, r2, c2, bv, brow, bcode)) {
+            bv = v2;
+            brow = r2;
+            bcode = c2;
+        }
+    }
+    if (lane == 0) {
+        float* o = out8 + (size_t)b * 8;
+        const bool any = bv > -CUDART_INF_F;
+        const float h = any ? bv : 0.0f;
+        o[0] = any ? (float)((double)wv.w_peak * h + (double)wv.w_isl * isl) : 0.0f;
+        o[1] = h;
+        o[2] = any ? (float)isl : 0.0f;
+        o[3] = h;
+        o[5] = (float)omega_count(wv);
+        o[6] = h;
+        o[7] = 0.0f;
+        const float E = o[4];
+        unsigned int bits = 0;
+        if (!(E > 0.0f) || !isfinite(E)) bits |= GRAF_DEVERR_ENERGY;
+        if (!isfinite(o[0]) || !isfinite(o[2]) || !isfinite(o[3])) bits |= GRAF_DEVERR_NONFINITE;
+        if (bits) atomicOr(&g_device_error, bits);
+        if (p.peak) p.peak[b] = make_int4(any ? brow : -1, any ? bcode : 0, __float_as_int(h), 0);
+    }
+    // every partial of the fused kernel is final (its soft PSL weight is 0)
+    if (p.scale)
+        for (int i = lane; i < wv.tiles; i += 32) p.scale[wv.rec_off + i] = 1.0f;
+}
+
 // One warp per waveform: merge the tile records in a fixed order (double).
 __global__ void loss_finalize_kernel(AfParams p, float* out8) {
     const int b = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     const int lane = threadIdx.x & 31;
     if (b >= p.B) return;
     const Wave wv = wave_of(p, b);
+    if (wv.hard) {
+        finalize_hard(p, wv, b, lane, out8);
+        return;
+    }
     const double beta = wv.beta;
     const bool fixed = wv.lse_fix > 0.0f;
     double isl = 0.0, mx = -CUDART_INF, z = 0.0, T = 0.0, hard = -CUDART_INF;
@@ -304,6 +366,116 @@ __global__ void grad_s_kernel(AfParams p, const float* dL, float2* grad_s, float
     }
 }
 
+// e^{-2 pi j q n / M} for M a power of two: the exponent reduced exactly in
+// integers, then sincospi of a value in [0, 2).
+__device__ __forceinline__ float2 twiddle_qn(int q, int n, int M) {
+    const int r = (int)(((unsigned)q * (unsigned)n) & (unsigned)(M - 1));
+    float sn, cs;
+    sincospif(2.0f * (float)r / (float)M, &sn, &cs);
+    return make_float2(cs, -sn);
+}
+
+// X[k, q] = sum_n u[n] conj(u[n - k]) e^{-2 pi j q n / M} of transformed row
+// k >= 0 (lag k - N over the doubled signal for the periodic AF), summed by
+// the CTA in a fixed order; every thread gets the result.  `red` holds 2
+// floats per warp.
+__device__ float2 row_bin(const Wave& wv, const float2* u, int k, int q, float* red) {
+    float2 acc = make_float2(0.0f, 0.0f);
+    const int n0 = wv.periodic ? 0 : k;
+    for (int n = n0 + (int)threadIdx.x; n < wv.N; n += (int)blockDim.x) {
+        const int j = wv.periodic ? ((n - k) & (wv.N - 1)) : n - k;
+        const float2 r = cmulc(u[n], u[j]);
+        const float2 w = twiddle_qn(q, n, wv.M);
+        acc = make_float2(fmaf(r.x, w.x, fmaf(-r.y, w.y, acc.x)), fmaf(r.x, w.y, fmaf(r.y, w.x, acc.y)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        red[2 * (threadIdx.x >> 5)] = acc.x;
+        red[2 * (threadIdx.x >> 5) + 1] = acc.y;
+    }
+    __syncthreads();
+    float2 x = make_float2(0.0f, 0.0f);
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x = make_float2(x.x + red[2 * w], x.y + red[2 * w + 1]);
+    return x;
+}
+
+// Hard PSL gradient: per waveform, w_peak dAhat^2/du* at the arg-max cell
+// (k, q) of its peak record -- one delay row, in closed form (the product rule
+// on the one sum X = sum_n u[n] conj(u[n-k]) W^(q n), W = e^{-2 pi j / M}):
+//   dAhat^2/du*[p] = (X u[p-k] conj(W^(q p)) + conj(X) u[p+k] W^(q (p+k))) / E^2
+//                    - 2 Ahat^2 u[p] / E,
+// a term absent where p - k or p + k leaves [0, N) (taken mod N for the
+// periodic AF).  u = s, or conj(s) for the +j periodic AF (mapped back as in
+// grad_s_kernel).
+__global__ void peak_grad_kernel(AfParams p, const float* dL, float2* grad_s, float* grad_phi, int accumulate) {
+    extern __shared__ float2 u_sm[];
+    __shared__ float red[64];
+    __shared__ double dred[32];
+    const int b = blockIdx.x;
+    const Wave wv = wave_of(p, b);
+    const int N = wv.N, M = wv.M;
+    double e = 0.0;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        const float2 v = signal_at(wv, n);
+        u_sm[n] = v;
+        e += (double)v.x * v.x + (double)v.y * v.y;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if ((threadIdx.x & 31) == 0) dred[threadIdx.x >> 5] = e;
+    __syncthreads();
+    double E = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) E += dred[w];
+    const int4 pk = p.peak[b];
+    const int k = pk.x, q = pk.y;
+    // nothing to add: Omega empty, no weight, or row 0 of a unit-modulus
+    // phase code (|s[n]|^2 = 1 whatever the phases)
+    const bool none = k < 0 || q < 0 || wv.w_peak == 0.0f || (wv.kind == 1 && k == 0);
+    float2 X = make_float2(0.0f, 0.0f);
+    if (!none) X = row_bin(wv, u_sm, k, q, red);
+    const double invE2 = 1.0 / (E * E);
+    const double a2 = ((double)X.x * X.x + (double)X.y * X.y + (double)wv.eps) * invE2;
+    const float scale = 2.0f * wv.w_peak * (dL ? dL[b] : 1.0f);
+    const float cj = wv.pconj ? -1.0f : 1.0f;
+    const bool add = !none;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        float2 g = make_float2(0.0f, 0.0f);
+        if (add) {
+            const float2 un = u_sm[n];
+            const int jm = wv.periodic ? ((n - k) & (N - 1)) : n - k;  // p - k
+            const int jp = wv.periodic ? ((n + k) & (N - 1)) : n + k;  // p + k
+            float2 d = make_float2(0.0f, 0.0f);
+            if (jm >= 0) {  // X u[p-k] conj(W^(q p))
+                const float2 w = twiddle_qn(q, n, M);
+                d = cadd(d, cmulc(cmul(X, u_sm[jm]), w));
+            }
+            if (jp < N) {  // conj(X) u[p+k] W^(q (p+k))
+                const float2 w = twiddle_qn(q, wv.periodic ? jp : n + k, M);
+                d = cadd(d, cmul(cmulc(u_sm[jp], X), w));
+            }
+            const float c1 = (float)invE2, c2 = (float)(2.0 * a2 / E);
+            g = make_float2(fmaf(c1, d.x, -c2 * un.x), fmaf(c1, d.y, -c2 * un.y));  // dAhat^2/du*
+            if (grad_phi) {
+                const float pv = cj * scale * (g.y * un.x - g.x * un.y);
+                grad_phi[wv.out_off + n] = accumulate ? grad_phi[wv.out_off + n] + pv : pv;
+            }
+            if (grad_s) {
+                float2 gv = make_float2(scale * g.x, cj * scale * g.y);
+                if (accumulate) gv = cadd(gv, grad_s[wv.out_off + n]);
+                grad_s[wv.out_off + n] = gv;
+            }
+        } else if (!accumulate) {
+            if (grad_phi) grad_phi[wv.out_off + n] = 0.0f;
+            if (grad_s) grad_s[wv.out_off + n] = make_float2(0.0f, 0.0f);
+        }
+    }
+}
+
 // Per-waveform match loss: the tile partials summed in order.
 __global__ void match_finalize_kernel(AfParams p, float* loss_out) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -458,6 +630,17 @@ cudaError_t run_match(const AfParams& p, float* loss_out, cudaStream_t st) {
     cudaError_t e = run_match_rows(p, st);
     if (e != cudaSuccess) return e;
     match_finalize_kernel<<<(p.B + 127) / 128, 128, 0, st>>>(p, loss_out);
+    return cudaGetLastError();
+}
+
+cudaError_t run_peak_grad(const AfParams& p, const float* dL, float2* grad_s, float* grad_phi, int accumulate,
+                          cudaStream_t st) {
+    const size_t sm = (size_t)p.N * sizeof(float2);
+    if (sm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(peak_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    peak_grad_kernel<<<p.B, 256, sm, st>>>(p, dL, grad_s, grad_phi, accumulate);
     return cudaGetLastError();
 }
 

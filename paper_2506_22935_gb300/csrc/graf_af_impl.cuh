@@ -11,6 +11,8 @@
 // -k with the Doppler axis mirrored (the loss weight of a transformed cell
 // counts both cells, and its adjoint adds both).
 #pragma once
+#include <climits>
+
 #include <math_constants.h>
 
 #include "graf_kernels.cuh"
@@ -62,33 +64,28 @@ __device__ __forceinline__ void for_each_item(const AfParams& p, F&& body) {
     }
 }
 
-// ---------------------------------------------------------- forward (store)
-// Ahat = sqrt(|X|^2 + eps) / E (Eq. 12, Eq. 17) -- or chi = |X|^2 (Eq. 12,
-// Algorithm 1), optionally over chi[0,0] = E^2 = max chi (Eq. 17) --
-// for every window cell of rows k and -k.  Stores are coalesced along m (consecutive threads hold
-// consecutive Doppler bins) and streaming (written once, never re-read here).
 template <int M, bool HALF>
-__global__ void __launch_bounds__(RowPlan<M>::THREADS, RowPlan<M>::MIN_BLOCKS) af_forward_kernel(AfParams p) {
+__device__ __forceinline__ void forward_item(const AfParams& p, int b, int tile, unsigned char* smem) {
     using P = RowPlan<M>;
-    extern __shared__ __align__(256) unsigned char smem[];
+    __shared__ Wave s_wave;
+    if (threadIdx.x == 0) s_wave = wave_of(p, b);
+    __syncthreads();
+    const Wave& wv = s_wave;
     float2* s_sm = reinterpret_cast<float2*>(smem);
     float2* bufs = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(sig_len(p)));
     float* red = reinterpret_cast<float*>(smem + smem_signal_bytes<M>(sig_len(p)) + row_buffer_bytes<M>());
 
     const int tid = threadIdx.x, slot = tid / P::TPR, t = tid % P::TPR;
-    const int b = blockIdx.x / p.tiles, tile = blockIdx.x % p.tiles;
-    const Wave wv = wave_of(p, b);
     const float E = load_signal(wv, s_sm, red);
     const float invE = 1.0f / E;
     const float sc = p.chi_out == 1 ? invE * invE : 1.0f;  // chi output: |X|^2 / E^2 or |X|^2
     float2* buf = bufs + (size_t)slot * (P::SPLIT ? P::SMEM_ROW / 2 : P::SMEM_ROW);
     const ColMasks cm = col_masks<M>(wv, t);
 
-    const int ncols = p.m_hi - p.m_lo + 1;
-    const size_t rows_out = (size_t)(p.k_hi - p.k_lo + 1);
-    float* out_b = p.af_out + (size_t)b * rows_out * ncols;
-    const int row0 = p.r_lo + tile * p.rows_per_tile;
-    const int row_end = min(row0 + p.rows_per_tile, p.r_hi + 1);
+    const int ncols = wv.m_hi - wv.m_lo + 1;
+    float* out_b = p.af_out + wv.af_off;
+    const int row0 = wv.r_lo + tile * wv.rows_per_tile;
+    const int row_end = min(row0 + wv.rows_per_tile, wv.r_hi + 1);
     // iterations for the rows this tile actually holds (CTA-uniform)
     const int iters = max(0, row_end - row0 + (P::THREADS / P::TPR) - 1) / (P::THREADS / P::TPR);
 
@@ -96,20 +93,20 @@ __global__ void __launch_bounds__(RowPlan<M>::THREADS, RowPlan<M>::MIN_BLOCKS) a
     for (int it = 0; it < iters; ++it) {
         const int k = row0 + slot + it * (P::THREADS / P::TPR);
         const bool valid = k < row_end;
-        build_lag_row<M, HALF>(v, s_sm, p.N, p.periodic ? k - p.N : k, t, valid);
+        build_lag_row<M, HALF>(v, s_sm, wv.N, wv.periodic ? k - wv.N : k, t, valid);
         row_sync<P::TPR>(slot);
         row_fft<M, false, HALF, false>(v, buf, t, slot);
         if (valid) {
             const RowMasks rmk = row_masks(wv, cm, k);
             const bool in_pos = rmk.pos != 0ull, in_neg = rmk.neg != 0ull;
             // row k at rp[m], row -k at rn[m'] (m' = -m, and -M/2 maps to itself)
-            float* rp = out_b + (in_pos ? (size_t)(k - p.k_lo) * ncols : 0) - p.m_lo + t;
-            float* rn = out_b + (in_neg ? (size_t)(-k - p.k_lo) * ncols : 0) - p.m_lo - t;
+            float* rp = out_b + (in_pos ? (size_t)(k - wv.k_lo) * ncols : 0) - wv.m_lo + t;
+            float* rn = out_b + (in_neg ? (size_t)(-k - wv.k_lo) * ncols : 0) - wv.m_lo - t;
             sfor<0, P::VALS>([&](auto w) {
                 constexpr int W = decltype(w)::value;
                 constexpr int off = P::TPR * W - (W >= P::VALS / 2 ? M : 0);  // m - t
                 const float2 x = v[w];
-                const float a = p.chi_out == 0 ? sqrtf(fmaf(x.x, x.x, fmaf(x.y, x.y, p.eps))) * invE
+                const float a = p.chi_out == 0 ? sqrtf(fmaf(x.x, x.x, fmaf(x.y, x.y, wv.eps))) * invE
                                                : fmaf(x.x, x.x, x.y * x.y) * sc;
                 if (mbit<W>(rmk.pos)) __stcs(rp + off, a);
                 if (mbit<W>(rmk.neg)) {
@@ -122,6 +119,19 @@ __global__ void __launch_bounds__(RowPlan<M>::THREADS, RowPlan<M>::MIN_BLOCKS) a
             });
         }
     }
+}
+
+// ---------------------------------------------------------- forward (store)
+// Ahat = sqrt(|X|^2 + eps) / E (Eq. 12, Eq. 17) -- or chi = |X|^2 (Eq. 12,
+// Algorithm 1), optionally over chi[0,0] = E^2 = max chi (Eq. 17) --
+// for every window cell of rows k and -k.  Stores are coalesced along m
+// (consecutive threads hold consecutive Doppler bins) and streaming (written
+// once, never re-read here).  Uniform batches and batch plans alike (the
+// window of waveform b starts at its af_off).
+template <int M, bool HALF>
+__global__ void __launch_bounds__(RowPlan<M>::THREADS, RowPlan<M>::MIN_BLOCKS) af_forward_kernel(AfParams p) {
+    extern __shared__ __align__(256) unsigned char smem[];
+    for_each_item(p, [&](int b, int tile) { forward_item<M, HALF>(p, b, tile, smem); });
 }
 
 // ---------------------------------------------------------- fused loss
@@ -154,6 +164,50 @@ __device__ __forceinline__ void lse_merge(float& isl, float& mx, float& sum, flo
     }
 }
 
+// Hard PSL: a candidate arg-max cell (value, transformed row, cell code) and
+// the order that picks one: the larger value, then the smaller row, then the
+// smaller code.  Every reduction below applies it, so the choice depends on
+// the values alone.
+struct PeakKey {
+    float v;
+    int row, code;
+};
+
+__device__ __forceinline__ bool peak_better(const PeakKey& a, const PeakKey& b) {
+    return a.v > b.v || (a.v == b.v && (a.row < b.row || (a.row == b.row && a.code < b.code)));
+}
+
+__device__ __forceinline__ PeakKey warp_best(PeakKey k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const PeakKey c{__shfl_xor_sync(0xffffffffu, k.v, o), __shfl_xor_sync(0xffffffffu, k.row, o),
+                        __shfl_xor_sync(0xffffffffu, k.code, o)};
+        if (peak_better(c, k)) k = c;
+    }
+    return k;
+}
+
+// The CTA's best key, returned to every thread; `scratch` holds 3 words per
+// warp.  Starts and ends with a barrier.
+__device__ __forceinline__ PeakKey block_best(PeakKey k, float* scratch) {
+    __syncthreads();
+    k = warp_best(k);
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    if (lane == 0) {
+        scratch[3 * wi] = k.v;
+        scratch[3 * wi + 1] = __int_as_float(k.row);
+        scratch[3 * wi + 2] = __int_as_float(k.code);
+    }
+    __syncthreads();
+    PeakKey best{scratch[0], __float_as_int(scratch[1]), __float_as_int(scratch[2])};
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+        const PeakKey c{scratch[3 * w], __float_as_int(scratch[3 * w + 1]), __float_as_int(scratch[3 * w + 2])};
+        if (peak_better(c, best)) best = c;
+    }
+    __syncthreads();
+    return best;
+}
+
 template <int M, bool HALF>
 __device__ __forceinline__ void loss_item(const AfParams& p, int b, int tile, unsigned char* smem) {
     using P = RowPlan<M>;
@@ -184,6 +238,10 @@ __device__ __forceinline__ void loss_item(const AfParams& p, int b, int tile, un
     const int iters = max(0, row_end - row0 + SLOTS - 1) / SLOTS;
 
     float isl = 0.0f, mx = -CUDART_INF_F, sum = 0.0f, T = 0.0f;
+    // hard PSL: this thread's largest weighted a2, its row and bin (the first
+    // bin of the first row that reached it)
+    float hbest = -CUDART_INF_F;
+    int hrow = INT_MAX, hq = INT_MAX;
     float2 v[P::VALS];
     for (int it = 0; it < iters; ++it) {
         const int k = row0 + slot + it * SLOTS;
@@ -210,6 +268,17 @@ __device__ __forceinline__ void loss_item(const AfParams& p, int b, int tile, un
         });
         if (rmx == -CUDART_INF_F) continue;
         isl += risl;
+        if (wv.hard) {  // the maximum only; no log-sum-exp
+            if (rmx > hbest) {
+                hbest = rmx;
+                hrow = k;
+                hq = INT_MAX;
+                sfor<0, P::VALS>([&](auto w) {
+                    if (hq == INT_MAX && v[w].y > 0.0f && v[w].x == rmx) hq = t + P::TPR * decltype(w)::value;
+                });
+            }
+            continue;
+        }
         lse_rescale(mx, sum, T, rmx, bl2);
         const float sh = mx * bl2;
         sfor<0, P::VALS>([&](auto w) {
@@ -242,7 +311,13 @@ __device__ __forceinline__ void loss_item(const AfParams& p, int b, int tile, un
             a.z *= f;
             a.w *= f;
         }
-        p.rec[wv.rec_off + tile] = a;
+        if (!wv.hard) p.rec[wv.rec_off + tile] = a;
+        else red[120] = a.x;
+    }
+    if (wv.hard) {  // record {ISL, max, row, bin} of the CTA's arg-max cell
+        const PeakKey pk = block_best(PeakKey{hbest, hrow, hq}, red + 64);
+        if (tid == 0)
+            p.rec[wv.rec_off + tile] = make_float4(red[120], pk.v, __int_as_float(pk.row), __int_as_float(pk.code));
     }
 }
 

@@ -42,10 +42,11 @@ graf_status_t check_window(int32_t N, int32_t M, const graf_window_t& w, const M
     return GRAF_OK;
 }
 
+// beta > 0 finite (soft PSL) or +infinity (hard PSL), eps >= 0 finite.
 graf_status_t check_loss(const graf_loss_t& l) {
     if (!(l.beta > 0.0f) || !(l.eps >= 0.0f)) return GRAF_ERR_INVALID_ARG;
     if (!(l.w_psl == l.w_psl) || !(l.w_isl == l.w_isl)) return GRAF_ERR_INVALID_ARG;
-    if (l.beta > 1e30f || l.eps > 1e30f) return GRAF_ERR_INVALID_ARG;
+    if ((l.beta > 1e30f && !graf::is_hard_beta(l.beta)) || l.eps > 1e30f) return GRAF_ERR_INVALID_ARG;
     return GRAF_OK;
 }
 
@@ -111,10 +112,15 @@ FusedPlan fused_plan(int32_t B, int32_t N, int32_t M, const graf_window_t& w, bo
     return f;
 }
 
+// hard PSL: per-waveform peak records, and the loss scalars graf_af_backward
+// recomputes for itself
+size_t peak_bytes(int32_t B) { return align256((size_t)B * sizeof(int4)); }
+size_t out8_bytes(int32_t B) { return align256((size_t)B * GRAF_LOSS_OUT * sizeof(float)); }
+
 size_t fused_ws(int32_t B, int32_t N, const FusedPlan& f) {
     size_t s = loss_ws(B, f.T1) + csum_bytes(B, f.T1) /* scale */ + csum_bytes(B, f.T1) + gpart_bytes(B, N, f.T1);
     if (f.deferred_launch) s += gpart_bytes(B, N, f.T2) + csum_bytes(B, f.T2);
-    return s + align256((size_t)2 * B * sizeof(double));
+    return s + align256((size_t)2 * B * sizeof(double)) + peak_bytes(B);
 }
 
 graf_status_t check_common(const void* x, graf_input_t kind, int32_t B, int32_t N, int32_t M,
@@ -199,8 +205,14 @@ static size_t backward_ws_impl(const Mode& md, int32_t B, int32_t N, int32_t M, 
             const size_t f = fused_ws(B, N, fused_plan(B, N, M, w, psl != 0, po != 0));
             if (f > s) s = f;
         }
-    return s;
+    // graf_af_backward with the hard PSL runs the fused step on its own loss scalars
+    return s + out8_bytes(B);
 }
+
+static graf_status_t af_loss_backward_impl(const Mode& md, const void* x, graf_input_t kind, int32_t B,
+                                           int32_t N, int32_t M, graf_window_t w, graf_loss_t l, float* out8,
+                                           const float* dL, graf_c32* grad_s, float* grad_phi,
+                                           void* workspace, size_t workspace_bytes, void* stream);
 
 static graf_status_t af_backward_impl(const Mode& md, const void* x, graf_input_t kind, int32_t B, int32_t N,
                                       int32_t M, graf_window_t w, graf_loss_t l, const float* saved8,
@@ -211,6 +223,16 @@ static graf_status_t af_backward_impl(const Mode& md, const void* x, graf_input_
     if ((s = check_loss(l)) != GRAF_OK) return s;
     if (!saved8 || (!grad_s && !grad_phi)) return GRAF_ERR_INVALID_ARG;
     if (grad_phi && kind != GRAF_IN_PHASE) return GRAF_ERR_INVALID_ARG;
+    if (graf::is_hard_beta(l.beta)) {
+        // the hard maximum's gradient needs its arg-max cell: run the fused
+        // step, with its loss scalars at the end of the workspace
+        const size_t need = backward_ws_impl(md, B, N, M, w);
+        if (!workspace || workspace_bytes < need) return GRAF_ERR_WORKSPACE;
+        if (reinterpret_cast<uintptr_t>(workspace) & 255) return GRAF_ERR_WORKSPACE;
+        float* own8 = reinterpret_cast<float*>(static_cast<unsigned char*>(workspace) + need - out8_bytes(B));
+        return af_loss_backward_impl(md, x, kind, B, N, M, w, l, own8, dL, grad_s, grad_phi, workspace,
+                                     need - out8_bytes(B), stream);
+    }
     const Tiling T = graf::make_tiling(B, M, w.k_lo, w.k_hi, graf::device_sm_count());
     if (!workspace || workspace_bytes < backward_ws(B, N, T)) return GRAF_ERR_WORKSPACE;
     if (reinterpret_cast<uintptr_t>(workspace) & 255) return GRAF_ERR_WORKSPACE;
@@ -237,23 +259,40 @@ static graf_status_t af_loss_backward_impl(const Mode& md, const void* x, graf_i
     if ((s = check_loss(l)) != GRAF_OK) return s;
     if (!out8 || (!grad_s && !grad_phi)) return GRAF_ERR_INVALID_ARG;
     if (grad_phi && kind != GRAF_IN_PHASE) return GRAF_ERR_INVALID_ARG;
-    if (!workspace || workspace_bytes < backward_ws_impl(md, B, N, M, w)) return GRAF_ERR_WORKSPACE;
+    if (!workspace || workspace_bytes < backward_ws_impl(md, B, N, M, w) - out8_bytes(B)) return GRAF_ERR_WORKSPACE;
     if (reinterpret_cast<uintptr_t>(workspace) & 255) return GRAF_ERR_WORKSPACE;
     const bool phase_only = kind == GRAF_IN_PHASE && grad_s == nullptr;
     const int acc = graf::acc_copies_for(M, N, phase_only ? 1 : 0, md.periodic);
     if (acc < 1) return GRAF_ERR_UNSUPPORTED;
-    FusedPlan f = fused_plan(B, N, M, w, l.w_psl != 0.0f, phase_only);
+    const bool hard = graf::is_hard_beta(l.beta);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (hard && l.w_isl == 0.0f) {
+        // the hard maximum alone: forward transforms with the arg-max cell
+        // (loss kernel), the finalisation, then that cell's gradient
+        const Tiling T = graf::make_tiling(B, M, w.k_lo, w.k_hi, graf::device_sm_count());
+        AfParams p = base_params(x, kind, B, N, M, w, T, md);
+        p.eps = l.eps; p.beta = l.beta; p.w_psl = l.w_psl; p.w_isl = l.w_isl;
+        p.rec = static_cast<float4*>(workspace);
+        p.peak = reinterpret_cast<int4*>(static_cast<unsigned char*>(workspace) + loss_ws(B, T));
+        p.out8 = out8;
+        cudaError_t e = graf::run_loss(p, st);
+        if (e == cudaSuccess)
+            e = graf::run_peak_grad(p, dL, reinterpret_cast<float2*>(grad_s), grad_phi, 0, st);
+        return cuda_status(e);
+    }
+    // (hard PSL with ISL: the soft-PSL machinery is off, ISL runs fused, and
+    // a loss pass locates the arg-max cell)
+    FusedPlan f = fused_plan(B, N, M, w, l.w_psl != 0.0f && !hard, phase_only);
     // on the PSL path with a running log-sum-exp shift each row slot needs its
     // own gradient accumulator (it rescales it); a fixed shift rescales nothing
     const bool fixed = graf::lse_fixed_shift(kind == GRAF_IN_PHASE ? 1 : 0, l.eps, l.beta, N) > 0.0f;
-    if (l.w_psl != 0.0f && !fixed && acc < graf::slots_of(M)) f.fused = false;
+    if (l.w_psl != 0.0f && !hard && !fixed && acc < graf::slots_of(M)) f.fused = false;
     if (!f.fused) {
         s = af_loss_impl(md, x, kind, B, N, M, w, l, out8, workspace, workspace_bytes, stream);
         if (s != GRAF_OK) return s;
         return af_backward_impl(md, x, kind, B, N, M, w, l, out8, dL, grad_s, grad_phi, workspace,
                                 workspace_bytes, stream);
     }
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     unsigned char* ws = static_cast<unsigned char*>(workspace);
     AfParams p = base_params(x, kind, B, N, M, w, f.T1, md);
     p.eps = l.eps; p.beta = l.beta; p.w_psl = l.w_psl; p.w_isl = l.w_isl;
@@ -279,8 +318,12 @@ static graf_status_t af_loss_backward_impl(const Mode& md, const void* x, graf_i
         ws += csum_bytes(B, f.T2);
     }
     p.usum = reinterpret_cast<double*>(ws);
+    ws += align256((size_t)2 * B * sizeof(double));
+    if (hard) p.peak = reinterpret_cast<int4*>(ws);
     cudaError_t e = graf::run_fused(p, st);
-    if (e == cudaSuccess) e = graf::run_finalize(p, st);
+    // hard PSL: the loss kernel's records (same tiles) carry the arg-max cell;
+    // they replace the fused kernel's before the finalisation
+    if (e == cudaSuccess) e = hard ? graf::run_loss(p, st) : graf::run_finalize(p, st);
     if (e == cudaSuccess && f.deferred_launch) {
         AfParams q = p;
         q.r_lo = f.T2.r_lo;
@@ -300,6 +343,8 @@ static graf_status_t af_loss_backward_impl(const Mode& md, const void* x, graf_i
     }
     if (e == cudaSuccess)
         e = graf::run_grad_reduce(p, dL, reinterpret_cast<float2*>(grad_s), grad_phi, st);
+    if (e == cudaSuccess && hard)
+        e = graf::run_peak_grad(p, dL, reinterpret_cast<float2*>(grad_s), grad_phi, 1, st);
     return cuda_status(e);
 }
 

@@ -63,7 +63,9 @@ struct graf_batch_plan_s {
     int* d_src_entries = nullptr;     // entries grouped by source, ascending
     int* d_src_first = nullptr;       // [B_src + 1] CSR into d_src_entries
     long long* d_src_off = nullptr;   // [B_src + 1]
-    size_t ws_scratch = 0;            // float per entry sample
+    size_t ws_scratch = 0;            // float (phase) or float2 (complex) per entry sample
+    long long total_af = 0;           // floats of the packed forward output
+    std::vector<long long> af_off;    // [B + 1] offsets of the waveforms' windows in it
 };
 
 namespace {
@@ -111,7 +113,9 @@ graf_status_t layout(graf_batch_plan_s* P) {
     P->ws_csum = align256((size_t)rec * sizeof(float));
     P->ws_gpart = align256((size_t)gp * sizeof(float2));
     P->ws_usum = align256((size_t)2 * P->B * sizeof(double));
-    P->ws_scratch = P->scenarios ? align256((size_t)P->total_x * sizeof(float)) : 0;
+    P->ws_scratch = P->scenarios ? align256((size_t)P->total_x * (P->kind == GRAF_IN_PHASE ? sizeof(float)
+                                                                                           : sizeof(float2)))
+                                 : 0;
     // device copies
     cudaError_t e = cudaMemcpy(P->d_waves, P->waves.data(), sizeof(WaveDesc) * P->B, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return GRAF_ERR_CUDA;
@@ -138,15 +142,17 @@ AfParams bucket_params(const graf_batch_plan_s* P, const Bucket& bk, int bi, con
     p.items = bk.d_items;
     p.n_items = (int)bk.items.size();
     p.counter = P->d_counters + bi;
-    unsigned char* w = static_cast<unsigned char*>(ws);
-    p.rec = reinterpret_cast<float4*>(w);
-    p.scale = reinterpret_cast<float*>(w + P->ws_rec);
-    p.csum = reinterpret_cast<float*>(w + P->ws_rec + P->ws_scale);
-    p.gpart = reinterpret_cast<float2*>(w + P->ws_rec + P->ws_scale + P->ws_csum);
-    p.usum = reinterpret_cast<double*>(w + P->ws_rec + P->ws_scale + P->ws_csum + P->ws_gpart);
+    if (ws) {  // (the forward call has no workspace)
+        unsigned char* w = static_cast<unsigned char*>(ws);
+        p.rec = reinterpret_cast<float4*>(w);
+        p.scale = reinterpret_cast<float*>(w + P->ws_rec);
+        p.csum = reinterpret_cast<float*>(w + P->ws_rec + P->ws_scale);
+        p.gpart = reinterpret_cast<float2*>(w + P->ws_rec + P->ws_scale + P->ws_csum);
+        p.usum = reinterpret_cast<double*>(w + P->ws_rec + P->ws_scale + P->ws_csum + P->ws_gpart);
+    }
     p.out8 = out8;
     p.saved8 = out8;
-    p.phase_only = 1;
+    p.phase_only = P->kind == GRAF_IN_PHASE ? 1 : 0;
     p.acc_copies = bk.acc_copies;
     p.defer_hi = -1;
     return p;
@@ -164,11 +170,15 @@ graf_status_t run_rows(const graf_batch_plan_s* P, const Bucket& bk, int bi, con
 
 // Multi-scenario sum (Eq. 24): grad[j][n] = sum over the entries b of source
 // j, in ascending order, of the entry gradient at waves[b].out_off + n (each
-// already scaled by its weight dL[b] = lambda_b).  One thread per sample.
+// already scaled by its weight dL[b] = lambda_b).  One thread per float of
+// the gradient: `width` floats per sample (1 phase, 2 complex).
 __global__ void scenario_sum_kernel(const WaveDesc* waves, const int* entries, const int* first,
-                                    const long long* src_off, int B_src, const float* scratch, float* grad) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= src_off[B_src]) return;
+                                    const long long* src_off, int B_src, int width, const float* scratch,
+                                    float* grad) {
+    const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= src_off[B_src] * width) return;
+    const long long i = f / width;
+    const int c = (int)(f - i * width);
     int lo = 0, hi = B_src - 1;  // source j with src_off[j] <= i < src_off[j+1]
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -177,20 +187,21 @@ __global__ void scenario_sum_kernel(const WaveDesc* waves, const int* entries, c
     }
     const long long n = i - src_off[lo];
     float s = 0.0f;
-    for (int e = first[lo]; e < first[lo + 1]; ++e) s += scratch[waves[entries[e]].out_off + n];
-    grad[i] = s;
+    for (int e = first[lo]; e < first[lo + 1]; ++e) s += scratch[(waves[entries[e]].out_off + n) * width + c];
+    grad[f] = s;
 }
 
-// The whole step for all buckets on one stream.
-graf_status_t batch_step(const graf_batch_plan_s* P, const float* x, float* out8, const float* dL,
-                         float* grad_phi, void* ws, cudaStream_t st) {
+// The loss rows of every bucket (loss kernel or fused kernel), then the
+// finalisation.
+graf_status_t batch_loss_rows(const graf_batch_plan_s* P, const void* x, float* out8, void* ws, bool fused_ok,
+                              bool* any_two_pass, cudaStream_t st) {
     graf_status_t s;
-    bool any_two_pass = false;
+    *any_two_pass = false;
     for (size_t i = 0; i < P->buckets.size(); ++i) {
         const Bucket& bk = P->buckets[i];
-        if (bk.fused) s = run_rows(P, bk, (int)i, x, ws, out8, 0, st);
+        if (bk.fused && fused_ok) s = run_rows(P, bk, (int)i, x, ws, out8, 0, st);
         else {
-            any_two_pass = true;
+            *any_two_pass = *any_two_pass || fused_ok;
             s = run_rows(P, bk, (int)i, x, ws, out8, 1, st);
         }
         if (s != GRAF_OK) return s;
@@ -198,21 +209,37 @@ graf_status_t batch_step(const graf_batch_plan_s* P, const float* x, float* out8
     AfParams q = bucket_params(P, P->buckets[0], 0, x, ws, out8);
     q.N = P->max_N;
     if (graf::run_finalize(q, st) != cudaSuccess) return GRAF_ERR_CUDA;
+    return GRAF_OK;
+}
+
+// The whole step for all buckets on one stream: loss scalars, then the
+// gradient (grad_phi for phase plans, grad_s for complex ones).
+graf_status_t batch_step(const graf_batch_plan_s* P, const void* x, float* out8, const float* dL, float2* grad_s,
+                         float* grad_phi, void* ws, cudaStream_t st) {
+    bool any_two_pass = false;
+    graf_status_t s = batch_loss_rows(P, x, out8, ws, true, &any_two_pass, st);
+    if (s != GRAF_OK) return s;
     if (any_two_pass)
         for (size_t i = 0; i < P->buckets.size(); ++i)
             if (!P->buckets[i].fused && (s = run_rows(P, P->buckets[i], (int)i, x, ws, out8, 2, st)) != GRAF_OK)
                 return s;
+    AfParams q = bucket_params(P, P->buckets[0], 0, x, ws, out8);
+    q.N = P->max_N;
     if (!P->scenarios) {
-        if (graf::run_grad_reduce(q, dL, nullptr, grad_phi, st) != cudaSuccess) return GRAF_ERR_CUDA;
+        if (graf::run_grad_reduce(q, dL, grad_s, grad_phi, st) != cudaSuccess) return GRAF_ERR_CUDA;
         return GRAF_OK;
     }
     float* scratch = reinterpret_cast<float*>(static_cast<unsigned char*>(ws) + P->ws_rec + P->ws_scale +
                                               P->ws_csum + P->ws_gpart + P->ws_usum);
-    if (graf::run_grad_reduce(q, dL, nullptr, scratch, st) != cudaSuccess) return GRAF_ERR_CUDA;
-    const long long n_src = P->src_off[P->B_src];
+    const int width = grad_s ? 2 : 1;
+    if (graf::run_grad_reduce(q, dL, grad_s ? reinterpret_cast<float2*>(scratch) : nullptr,
+                              grad_s ? nullptr : scratch, st) != cudaSuccess)
+        return GRAF_ERR_CUDA;
+    const long long n_src = P->src_off[P->B_src] * width;
     const unsigned grid = (unsigned)((n_src + 255) / 256);
     scenario_sum_kernel<<<grid, 256, 0, st>>>(P->d_waves, P->d_src_entries, P->d_src_first, P->d_src_off,
-                                              P->B_src, scratch, grad_phi);
+                                              P->B_src, width, scratch,
+                                              grad_s ? reinterpret_cast<float*>(grad_s) : grad_phi);
     return cudaGetLastError() == cudaSuccess ? GRAF_OK : GRAF_ERR_CUDA;
 }
 
@@ -239,7 +266,7 @@ static graf_status_t create_plan(int32_t B, const int32_t* N_host, const int32_t
     *plan = nullptr;
     if (B < 1 || B > (1 << 20) || !l_host) return GRAF_ERR_INVALID_ARG;
     if (src_host ? (!N_src_host || B_src < 1 || B_src > (1 << 20)) : !N_host) return GRAF_ERR_INVALID_ARG;
-    if (kind != GRAF_IN_PHASE) return GRAF_ERR_UNSUPPORTED;
+    if (kind != GRAF_IN_PHASE && kind != GRAF_IN_COMPLEX) return GRAF_ERR_INVALID_ARG;
     graf_batch_plan_s* P = new (std::nothrow) graf_batch_plan_s();
     if (!P) return GRAF_ERR_NOMEM;
     P->B = B;
@@ -274,6 +301,10 @@ static graf_status_t create_plan(int32_t B, const int32_t* N_host, const int32_t
             delete P;
             return GRAF_ERR_INVALID_ARG;
         }
+        if (graf::is_hard_beta(l.beta)) {  // the hard PSL runs through the single-shape calls only
+            delete P;
+            return GRAF_ERR_UNSUPPORTED;
+        }
         graf_window_t w;
         if (w_host) w = w_host[b];
         else w = graf_window_t{-(N - 1), N - 1, -(M / 2), M / 2 - 1, 0, std::max(M / N - 1, 0)};
@@ -294,10 +325,14 @@ static graf_status_t create_plan(int32_t B, const int32_t* N_host, const int32_t
         d.r_hi = T.r_hi;
         d.eps = l.eps; d.beta = l.beta; d.w_psl = l.w_psl; d.w_isl = l.w_isl;
         d.defer_hi = -1;
+        d.af_off = P->total_af;
+        P->af_off.push_back(P->total_af);
+        P->total_af += (long long)(w.k_hi - w.k_lo + 1) * (w.m_hi - w.m_lo + 1);
         P->max_N = std::max(P->max_N, N);
         if (std::find(Ms.begin(), Ms.end(), M) == Ms.end()) Ms.push_back(M);
     }
     P->total_x = off;
+    P->af_off.push_back(P->total_af);
     std::sort(Ms.begin(), Ms.end(), [](int a, int c) { return a > c; });  // largest rows first
     for (int M : Ms) {
         std::vector<int> all;
@@ -307,7 +342,8 @@ static graf_status_t create_plan(int32_t B, const int32_t* N_host, const int32_t
                 all.push_back(b);
                 max_N = std::max(max_N, P->waves[b].N);
             }
-        const int acc = graf::acc_copies_for(M, max_N, 1);
+        const int real = P->kind == GRAF_IN_PHASE ? 1 : 0;  // phase gradients use real accumulators
+        const int acc = graf::acc_copies_for(M, max_N, real);
         if (acc < 1 || graf::row_kernel_smem(M, max_N, 0) > graf::kMaxSmem) {
             delete P;
             return GRAF_ERR_UNSUPPORTED;
@@ -327,7 +363,14 @@ static graf_status_t create_plan(int32_t B, const int32_t* N_host, const int32_t
             bool ok = true;
             if (d.w_psl != 0.0f) {
                 if (!full_m || d.k_ml >= 1 || (!fixed && acc < slots)) ok = false;
-                else if (d.k_ml == 0 && d.m_ml >= 0 && d.r_lo == 0) d.defer_hi = 0;
+                // a box on row 0: its cells' weights are not uniform, so the
+                // fused kernel leaves row 0's gradient out; that is exact for
+                // phase codes (row 0 does not depend on the phases), and a
+                // complex waveform takes the two-pass path instead
+                else if (d.k_ml == 0 && d.m_ml >= 0 && d.r_lo == 0) {
+                    if (real) d.defer_hi = 0;
+                    else ok = false;
+                }
             }
             (ok ? fused : two_pass).push_back(b);
         }
@@ -340,7 +383,7 @@ static graf_status_t create_plan(int32_t B, const int32_t* N_host, const int32_t
             bk.fused = pass == 0;
             bk.waves = ws;
             for (int b : ws) bk.max_N = std::max(bk.max_N, P->waves[b].N);
-            bk.acc_copies = graf::acc_copies_for(M, bk.max_N, 1);
+            bk.acc_copies = graf::acc_copies_for(M, bk.max_N, real);
             for (int b : ws) {
                 P->waves[b].unscaled = bk.fused ? 0 : 1;
                 if (!bk.fused) P->waves[b].defer_hi = -1;
@@ -434,13 +477,60 @@ graf_status_t graf_batch_plan_info(graf_batch_plan_t P, int32_t* n_buckets, int3
     return GRAF_OK;
 }
 
+static graf_status_t check_ws(graf_batch_plan_t P, void* workspace, size_t workspace_bytes) {
+    if (!workspace || workspace_bytes < graf_batch_workspace_bytes(P)) return GRAF_ERR_WORKSPACE;
+    if (reinterpret_cast<uintptr_t>(workspace) & 255) return GRAF_ERR_WORKSPACE;
+    return GRAF_OK;
+}
+
 graf_status_t graf_batch_loss_backward(graf_batch_plan_t P, const float* phi, float* out8, const float* dL,
                                        float* grad_phi, void* workspace, size_t workspace_bytes,
                                        void* stream) {
     if (!P || !phi || !out8 || !grad_phi) return GRAF_ERR_INVALID_ARG;
-    if (!workspace || workspace_bytes < graf_batch_workspace_bytes(P)) return GRAF_ERR_WORKSPACE;
-    if (reinterpret_cast<uintptr_t>(workspace) & 255) return GRAF_ERR_WORKSPACE;
-    return batch_step(P, phi, out8, dL, grad_phi, workspace, static_cast<cudaStream_t>(stream));
+    if (P->kind != GRAF_IN_PHASE) return GRAF_ERR_INVALID_ARG;
+    const graf_status_t s = check_ws(P, workspace, workspace_bytes);
+    if (s != GRAF_OK) return s;
+    return batch_step(P, phi, out8, dL, nullptr, grad_phi, workspace, static_cast<cudaStream_t>(stream));
+}
+
+graf_status_t graf_batch_loss_backward_complex(graf_batch_plan_t P, const graf_c32* s_in, float* out8,
+                                               const float* dL, graf_c32* grad_s, void* workspace,
+                                               size_t workspace_bytes, void* stream) {
+    if (!P || !s_in || !out8 || !grad_s) return GRAF_ERR_INVALID_ARG;
+    if (P->kind != GRAF_IN_COMPLEX) return GRAF_ERR_INVALID_ARG;
+    const graf_status_t s = check_ws(P, workspace, workspace_bytes);
+    if (s != GRAF_OK) return s;
+    return batch_step(P, s_in, out8, dL, reinterpret_cast<float2*>(grad_s), nullptr, workspace,
+                      static_cast<cudaStream_t>(stream));
+}
+
+graf_status_t graf_batch_loss(graf_batch_plan_t P, const void* x, float* out8, void* workspace,
+                              size_t workspace_bytes, void* stream) {
+    if (!P || !x || !out8) return GRAF_ERR_INVALID_ARG;
+    graf_status_t s = check_ws(P, workspace, workspace_bytes);
+    if (s != GRAF_OK) return s;
+    bool two = false;
+    return batch_loss_rows(P, x, out8, workspace, false, &two, static_cast<cudaStream_t>(stream));
+}
+
+graf_status_t graf_batch_af_offsets(graf_batch_plan_t P, int64_t* af_off_host) {
+    if (!P || !af_off_host) return GRAF_ERR_INVALID_ARG;
+    for (size_t i = 0; i < P->af_off.size(); ++i) af_off_host[i] = P->af_off[i];
+    return GRAF_OK;
+}
+
+graf_status_t graf_batch_forward(graf_batch_plan_t P, const void* x, float* af_out, void* stream) {
+    if (!P || !x || !af_out) return GRAF_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (size_t i = 0; i < P->buckets.size(); ++i) {
+        const Bucket& bk = P->buckets[i];
+        AfParams p = bucket_params(P, bk, (int)i, x, nullptr, nullptr);
+        p.af_out = af_out;
+        p.chi_out = 0;
+        if (cudaMemsetAsync(p.counter, 0, sizeof(unsigned int), st) != cudaSuccess) return GRAF_ERR_CUDA;
+        if (graf::run_forward(p, st) != cudaSuccess) return GRAF_ERR_CUDA;
+    }
+    return GRAF_OK;
 }
 
 graf_status_t graf_batch_autotune(graf_batch_plan_t P, const float* phi, float* out8, float* grad_phi,

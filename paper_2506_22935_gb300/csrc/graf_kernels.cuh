@@ -22,6 +22,7 @@ int device_sm_count();
 struct WaveDesc {
     long long x_off;      // first element of waveform b in the packed input
     long long out_off;    // first element of its gradient in the packed output
+    long long af_off;     // first float of its window in the packed forward output
     long long gpart_off;  // first float2 of its per-CTA gradient partials (tiles x N)
     int rec_off;          // index of its first per-CTA record / scale / sum
     int N, M;
@@ -80,9 +81,8 @@ struct AfParams {
     int n_items;
     unsigned int* counter; // zeroed before the launch
     // hard PSL (beta = +inf): per waveform {transformed row k >= 0 of the
-    // arg-max cell (-1: Omega empty), its cell code (bin q >= 0, or -1 - t: one
-    // of the bins of thread t of the row), float bits of max Ahat^2, 0},
-    // written by the loss finalisation (nullable)
+    // arg-max cell (-1: Omega empty), its DFT bin q in [0, M), float bits of
+    // max Ahat^2, 0}, written by the loss finalisation (nullable)
     int4* peak;
 };
 
@@ -133,6 +133,7 @@ __host__ __device__ __forceinline__ size_t acc_region_bytes(const AfParams& p) {
 struct Wave {
     const void* x;  // this waveform's input
     long long out_off, gpart_off;
+    long long af_off;  // first float of its window in the forward output
     int rec_off;
     int kind, N, M;
     int k_lo, k_hi, m_lo, m_hi, k_ml, m_ml;
@@ -175,6 +176,7 @@ __host__ __device__ __forceinline__ Wave wave_of(const AfParams& p, int b) {
         w.x = static_cast<const char*>(p.x) + d.x_off * (p.kind == 1 ? 4 : 8);
         w.out_off = d.out_off;
         w.gpart_off = d.gpart_off;
+        w.af_off = d.af_off;
         w.rec_off = d.rec_off;
         w.N = d.N; w.M = d.M;
         w.k_lo = d.k_lo; w.k_hi = d.k_hi; w.m_lo = d.m_lo; w.m_hi = d.m_hi; w.k_ml = d.k_ml; w.m_ml = d.m_ml;
@@ -188,6 +190,7 @@ __host__ __device__ __forceinline__ Wave wave_of(const AfParams& p, int b) {
         w.x = static_cast<const char*>(p.x) + (long long)b * p.N * (p.kind == 1 ? 4 : 8);
         w.out_off = (long long)b * p.N;
         w.gpart_off = (long long)b * p.tiles * p.N;
+        w.af_off = (long long)b * (p.k_hi - p.k_lo + 1) * (p.m_hi - p.m_lo + 1);
         w.rec_off = b * p.tiles;
         w.N = p.N; w.M = p.M;
         w.k_lo = p.k_lo; w.k_hi = p.k_hi; w.m_lo = p.m_lo; w.m_hi = p.m_hi; w.k_ml = p.k_ml; w.m_ml = p.m_ml;

@@ -98,6 +98,10 @@ _SIGS = {
     "graf_batch_workspace_bytes": (_sz, [_vp]),
     "graf_batch_plan_info": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _i32]),
     "graf_batch_loss_backward": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "graf_batch_loss_backward_complex": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "graf_batch_loss": (ctypes.c_int, [_vp, _vp, _vp, _vp, _sz, _vp]),
+    "graf_batch_af_offsets": (ctypes.c_int, [_vp, _vp]),
+    "graf_batch_forward": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "graf_batch_autotune": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _sz, _vp, ctypes.c_char_p]),
     "graf_mlp_param_count": (_sz, []),
     "graf_mlp_activation_bytes": (_sz, [_i32]),
@@ -303,6 +307,22 @@ def graf_batch_loss_backward(plan, phi, out8, dL, grad_phi, workspace, workspace
     return load().graf_batch_loss_backward(plan, phi, out8, dL, grad_phi, workspace, workspace_bytes, stream)
 
 
+def graf_batch_loss_backward_complex(plan, s, out8, dL, grad_s, workspace, workspace_bytes, stream) -> int:
+    return load().graf_batch_loss_backward_complex(plan, s, out8, dL, grad_s, workspace, workspace_bytes, stream)
+
+
+def graf_batch_loss(plan, x, out8, workspace, workspace_bytes, stream) -> int:
+    return load().graf_batch_loss(plan, x, out8, workspace, workspace_bytes, stream)
+
+
+def graf_batch_af_offsets(plan, af_off_host) -> int:
+    return load().graf_batch_af_offsets(plan, af_off_host)
+
+
+def graf_batch_forward(plan, x, af_out, stream) -> int:
+    return load().graf_batch_forward(plan, x, af_out, stream)
+
+
 def graf_batch_autotune(plan, phi, out8, grad_phi, workspace, workspace_bytes, stream, cache_path) -> int:
     return load().graf_batch_autotune(plan, phi, out8, grad_phi, workspace, workspace_bytes, stream, cache_path)
 
@@ -386,11 +406,17 @@ class Window:
 
 @dataclass(frozen=True)
 class Loss:
-    """L = w_psl PSL_soft + w_isl ISL with soft-max temperature beta."""
+    """L = w_psl PSL_soft + w_isl ISL with soft-max temperature beta; with
+    beta = math.inf, L = w_psl PSL_hard + w_isl ISL (the hard maximum of
+    Eq. 18, differentiated through its arg-max cell)."""
     w_psl: float = 1.0
     w_isl: float = 1.0
     beta: float = 50.0
     eps: float = 1e-12
+
+    @staticmethod
+    def hard(w_psl: float = 1.0, w_isl: float = 0.0, eps: float = 1e-12) -> "Loss":
+        return Loss(w_psl, w_isl, float("inf"), eps)
 
     def c(self) -> graf_loss_t:
         return graf_loss_t(self.w_psl, self.w_isl, self.beta, self.eps)
@@ -546,9 +572,10 @@ class BatchPlan:
     next power of two >= 2 N[b]), window windows[b] (default: all bins minus
     the zero-delay mainlobe) and loss losses[b] (or one loss for all)."""
 
-    def __init__(self, N, M=None, windows=None, losses=None, device=None):
+    def __init__(self, N, M=None, windows=None, losses=None, device=None, kind: int = GRAF_IN_PHASE):
         torch = _torch()
         import numpy as np
+        self.kind = kind
         self.N = np.asarray(N, dtype=np.int32)
         self.B = len(self.N)
         Nc = np.ascontiguousarray(self.N)
@@ -563,7 +590,7 @@ class BatchPlan:
         h = ctypes.c_void_p()
         st = graf_batch_plan_create(self.B, Nc.ctypes.data, None if Mc is None else Mc.ctypes.data,
                                     None if wc is None else ctypes.addressof(wc), ctypes.addressof(lc), per,
-                                    GRAF_IN_PHASE, ctypes.byref(h))
+                                    kind, ctypes.byref(h))
         _check(st, "graf_batch_plan_create")
         self.handle = h
         self.offsets = np.concatenate([[0], np.cumsum(self.N.astype(np.int64))])
@@ -571,7 +598,7 @@ class BatchPlan:
         self._ws = None
 
     @classmethod
-    def scenarios(cls, N_src, src, windows, losses, M=None, device=None) -> "BatchPlan":
+    def scenarios(cls, N_src, src, windows, losses, M=None, device=None, kind: int = GRAF_IN_PHASE) -> "BatchPlan":
         """A multi-scenario plan (Eq. 24): entry b scores source src[b] of
         lengths N_src with windows[b] and losses[b]; loss_backward then takes
         the packed sources, the per-entry weights lambda as dL, and returns
@@ -579,6 +606,7 @@ class BatchPlan:
         torch = _torch()
         import numpy as np
         self = cls.__new__(cls)
+        self.kind = kind
         src = np.ascontiguousarray(np.asarray(src, dtype=np.int32))
         Ns = np.ascontiguousarray(np.asarray(N_src, dtype=np.int32))
         S = len(src)
@@ -590,7 +618,7 @@ class BatchPlan:
         h = ctypes.c_void_p()
         _check(graf_batch_plan_create_scenarios(S, src.ctypes.data, len(Ns), Ns.ctypes.data,
                                                 None if Mc is None else Mc.ctypes.data, ctypes.addressof(wc),
-                                                ctypes.addressof(lc), GRAF_IN_PHASE, ctypes.byref(h)),
+                                                ctypes.addressof(lc), kind, ctypes.byref(h)),
                "graf_batch_plan_create_scenarios")
         self.handle = h
         self.offsets = np.concatenate([[0], np.cumsum(Ns.astype(np.int64))])  # of the sources
@@ -614,16 +642,43 @@ class BatchPlan:
         return [dict(M=arrs[0][i], rows_per_tile=arrs[1][i], items=arrs[2][i], fused=bool(arrs[3][i]))
                 for i in range(n.value)]
 
-    def loss_backward(self, phi_packed, dL=None, out8=None, grad=None):
+    def loss_backward(self, x_packed, dL=None, out8=None, grad=None):
+        """(out8 [B, 8], gradient packed like the input): dL/dphi for a phase
+        plan (float32 input), dL/dRe s + j dL/dIm s for a complex plan
+        (complex64 input)."""
         torch = _torch()
         out8 = out8 if out8 is not None else torch.empty((self.B, 8), dtype=torch.float32, device=self.device)
-        grad = grad if grad is not None else torch.empty_like(phi_packed)
+        grad = grad if grad is not None else torch.empty_like(x_packed)
         ws = self.workspace()
-        st = graf_batch_loss_backward(self.handle, phi_packed.data_ptr(), out8.data_ptr(),
-                                      None if dL is None else dL.data_ptr(), grad.data_ptr(), ws.data_ptr(),
-                                      ws.numel(), torch.cuda.current_stream(self.device).cuda_stream)
-        _check(st, "graf_batch_loss_backward")
+        fn = graf_batch_loss_backward if self.kind == GRAF_IN_PHASE else graf_batch_loss_backward_complex
+        st = fn(self.handle, x_packed.data_ptr(), out8.data_ptr(), None if dL is None else dL.data_ptr(),
+                grad.data_ptr(), ws.data_ptr(), ws.numel(), torch.cuda.current_stream(self.device).cuda_stream)
+        _check(st, fn.__name__)
         return out8, grad
+
+    def loss(self, x_packed, out8=None):
+        """Loss scalars [B, 8] alone (graf_batch_loss)."""
+        torch = _torch()
+        out8 = out8 if out8 is not None else torch.empty((self.B, 8), dtype=torch.float32, device=self.device)
+        ws = self.workspace()
+        _check(graf_batch_loss(self.handle, x_packed.data_ptr(), out8.data_ptr(), ws.data_ptr(), ws.numel(),
+                               torch.cuda.current_stream(self.device).cuda_stream), "graf_batch_loss")
+        return out8
+
+    def af_offsets(self):
+        import numpy as np
+        off = np.zeros(self.B + 1, dtype=np.int64)
+        _check(graf_batch_af_offsets(self.handle, off.ctypes.data), "graf_batch_af_offsets")
+        return off
+
+    def forward(self, x_packed):
+        """Every waveform's Ahat window, packed (split with af_offsets())."""
+        torch = _torch()
+        off = self.af_offsets()
+        out = torch.empty(int(off[-1]), dtype=torch.float32, device=self.device)
+        _check(graf_batch_forward(self.handle, x_packed.data_ptr(), out.data_ptr(),
+                                  torch.cuda.current_stream(self.device).cuda_stream), "graf_batch_forward")
+        return out, off
 
     def autotune(self, phi_packed, cache_path=None):
         torch = _torch()

@@ -1,6 +1,9 @@
 """The paper's experiment loss (Sec. 7.1.1, Eq. 25) on the GPU optimiser:
 periodic AF PSL + lambda alpha spectral variance, Adam lr 0.01, against the
-FP64 restatement step by step."""
+FP64 restatement step by step -- with the hard PSL of Eq. 18 (the
+experiment's definition) and, as an option, the log-sum-exp PSL."""
+import math
+
 import numpy as np
 import pytest
 
@@ -21,7 +24,7 @@ def _lib():
 
 @pytest.mark.parametrize("lam", [0.0, 0.5, 2.0])
 @pytest.mark.parametrize("graph", [False, True])
-def test_experiment_steps_match_oracle(lam, graph):
+def test_experiment_soft_psl_steps_match_oracle(lam, graph):
     from paper_2506_22935_gb300.optim import Adam, PhaseOptimizer
     B, N, steps = 2, 64, 30
     lp = (1.0, 0.0, 100.0)
@@ -38,4 +41,44 @@ def test_experiment_steps_match_oracle(lam, graph):
         ref_phi, ref_hist = oracle.optimize_experiment(phi0[b], win.as_tuple(), *lp, 1e-12, 2000.0 * lam, steps)
         np.testing.assert_allclose(hist[:, b], ref_hist, rtol=2e-4)
         assert np.abs(got[b] - ref_phi).max() <= 2e-4
+    assert np.all(hist[-1] < hist[0])
+
+
+@pytest.mark.parametrize("lam", [0.0, 0.5, 2.0])
+def test_experiment_hard_psl_each_step(lam):
+    """Each of 25 eager steps from the GPU's own state: the recorded loss is
+    PSL_hard + lambda alpha SV of the oracle, the gradient is the oracle's
+    through one arg-max cell (any cell within a relative 1e-5 of the maximum
+    is a valid one) plus lambda alpha dSV/dphi, and the update is Adam's."""
+    from oracle import spectral
+    from paper_2506_22935_gb300.optim import Adam, PhaseOptimizer
+    B, N, steps, alpha = 2, 64, 25, 2000.0
+    win = g.Window.periodic(N)
+    wt = win.as_tuple()
+    phi = torch.from_numpy(inputs.random_phases(82, B, N)).to("cuda:0")
+    opt = PhaseOptimizer(phi, window=win, loss=g.Loss.hard(1.0, 0.0), adam=Adam(lr=1e-2), history_len=steps,
+                         periodic_sign=1, spectral_weight=alpha * lam)
+    for t in range(steps):
+        phi0, m0, v0 = phi.cpu().numpy().copy(), opt.m.cpu().numpy().copy(), opt.v.cpu().numpy().copy()
+        opt.enqueue_step()
+        torch.cuda.synchronize()
+        gr, hist, phi1 = opt.grad.cpu().numpy(), opt.history.cpu().numpy(), phi.cpu().numpy()
+        for b in range(B):
+            s = oracle.signal_from_phase(phi0[b].astype(np.float64))
+            ref8 = oracle.ploss(s, wt, 1.0, 0.0, math.inf, 1e-12, sign=1)
+            sv, _, gsv = spectral.spectral_variance_grad(s)
+            want_l = ref8[3] + alpha * lam * sv
+            assert abs(hist[t, b] - want_l) <= 2e-5 * want_l, (t, b, hist[t, b], want_l)
+            A2 = np.abs(oracle.paf_complex(s, 1)) ** 2 / oracle.energy(s) ** 2
+            A2[N // 2, N // 2] = -np.inf  # the origin is outside Omega
+            top = A2.max()
+            errs = []
+            for k, m in np.argwhere(A2 >= top * (1 - 1e-5)):
+                _, cp = oracle.pcell_grad(s, int(k) - N // 2, int(m) - N // 2, 1e-12, sign=1)
+                want = cp + alpha * lam * gsv
+                errs.append(np.linalg.norm(gr[b] - want) / np.linalg.norm(want))
+            assert min(errs) <= 1e-4, (t, b, errs)
+            x1, _, _ = oracle.adam_update(phi0[b], m0[b], v0[b], gr[b].astype(np.float64), t + 1)
+            assert np.abs(phi1[b] - x1).max() <= 1e-5, (t, b)
+    hist = opt.history.cpu().numpy()
     assert np.all(hist[-1] < hist[0])
