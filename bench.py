@@ -353,10 +353,13 @@ def run_graf(args):
                "speedup_of_graf": ms_c / ms_per_step,
                "loss_max_rel_diff": float(((lc_ - out8[:, 0]).abs() / out8[:, 0].abs()).max()),
                "grad_rel_l2_diff": float((gc_ - grad).norm() / grad.norm()),
-               "what": "torch.fft (cuFFT) row DFTs + eager torch lag products, magnitudes, "
-                       "log-sum-exp and autograd backward, rows k >= 0 with mirror weights, 32 codes per chunk"}
+               "what": "torch.fft (cuFFT) row DFTs and inverse DFTs + eager torch lag products, magnitudes, "
+                       "log-sum-exp and the hand-written adjoint with the kernels' exact split of the cell "
+                       "adjoint (same loss and gradient), rows k >= 0 with mirror weights, 32 codes per chunk"}
         del lc_, gc_
         torch.cuda.empty_cache()
+
+    fwd = run_forward_store(g, x, Bb, dev, stream, flush) if world == 1 and not args.no_forward_store else None
 
     peak_tflops, peak_src = _fp32_peak(dev)
     # algorithmic work of one call: the forward DFT and its adjoint for every
@@ -372,7 +375,13 @@ def run_graf(args):
                 "algorithmic_flop_per_launch": alg,
                 "executed_flop_per_launch": executed,
                 "executed_frac": executed / (ms_per_step / 1e3) / 1e12 / peak_tflops}
-    cpu = None
+    roofline["frac_basis"] = ("frac counts the algorithmic work, a forward DFT and its adjoint for every one "
+                              "of the 2N-1 delay rows (the basis the >= 50% target is stated on); the kernel "
+                              "executes half of it (rows k >= 0, |X[-k,m]| = |X[k,-m]|, and X reused by the "
+                              "adjoint), so executed_frac is its use of the FP32 pipes")
+    cpu, errors = None, None
+    if world == 1 and not args.no_cpu_baseline:
+        errors = fp64_errors(g, x, out8, grad, dev)
     if world == 1 and not args.no_cpu_baseline:
         import numpy as np
         cols = _oracle_budget_cols(15.0)
@@ -384,6 +393,7 @@ def run_graf(args):
             # the whole AF of waveform 0: both GPU gradients against FP64
             rel = lambda a: float(np.linalg.norm(a - g_orc) / np.linalg.norm(g_orc))
             cpu["grad_rel_l2_graf_vs_oracle_wave0"] = rel(grad[0].double().cpu().numpy())
+            errors["headline_B256_N1024_M2048"]["grad_rel_l2_wave0"] = rel(grad[0].double().cpu().numpy())
             if cufft_g0 is not None:
                 cmp["grad_rel_l2_vs_oracle_wave0"] = rel(cufft_g0)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -396,49 +406,142 @@ def run_graf(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": Bb * N * 4,
                     "d2h_bytes_per_step": Bb * 8 * 4 + Bb * N * 4},
             "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary(),
-            "cufft_pipeline": cmp}
+            "cufft_pipeline": cmp, "forward_store": fwd, "errors_vs_fp64": errors}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 
 
+def run_forward_store(g, x, Bb, dev, stream, flush, reps=5):
+    """graf_af_forward over the whole AF of the benchmark batch (all 2N-1
+    delays x M Doppler bins of every code: 4.29 GB of fp32 written at B =
+    256), timed with CUDA events: Gcells/s, GB/s of output, its fraction of
+    the measured HBM copy bandwidth, and the FP32 fraction of the forward
+    DFTs (5 M log2 M flop per delay row; the kernel transforms rows k >= 0)."""
+    import torch
+    w = g.Window.full(N, M)
+    out = torch.empty((Bb, 2 * N - 1, M), dtype=torch.float32, device=dev)
+    sp = stream.cuda_stream
+
+    def call():
+        st = g.graf_af_forward(x.data_ptr(), g.GRAF_IN_PHASE, Bb, N, M, w.c(), EPS, out.data_ptr(), sp)
+        assert st == 0, g.graf_status_string(st)
+
+    ms = _timed_events(call, reps, 2, stream, flush)
+    cells = Bb * (2 * N - 1) * M
+    nbytes = 4.0 * cells
+    peaks, src = _measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    peak_tf, _ = _fp32_peak(dev)
+    alg = Bb * (2 * N - 1) * FLOP_PER_ROW
+    exe = Bb * N * FLOP_PER_ROW
+    gbs = nbytes / (ms / 1e3) / 1e9
+    res = {"kernel": "af_forward_kernel<2048, N <= M/2>", "ms": ms, "Gcells_per_s": cells / (ms / 1e3) / 1e9,
+           "bytes_written": nbytes, "GB_per_s": gbs, "hbm_frac": gbs / hbm,
+           "hbm_peak_gbs": hbm, "hbm_peak_source": f"MEASURED_PEAKS.json hbm_gbs ({src})",
+           "fp32_frac_algorithmic": alg / (ms / 1e3) / 1e12 / peak_tf,
+           "fp32_frac_executed": exe / (ms / 1e3) / 1e12 / peak_tf, "reps": reps,
+           "what": f"the whole AF (2N-1 = {2 * N - 1} delays x {M} Doppler bins) of {Bb} codes, Ahat written "
+                   "as fp32 [B][2N-1][M]; output larger than L2"}
+    del out
+    torch.cuda.empty_cache()
+    return res
+
+
+def fp64_errors(g, x, out8, grad, dev):
+    """Errors against the FP64 oracle, stated per configuration: the LFM
+    chirp (N = 64, M = 128, all 127 delays, eps 1e-12) cell by cell, and on
+    the benchmark batch the loss scalars of code 0 and 2048 sampled AF cells
+    of codes 0 and 255 (the gradient of code 0 is added when the CPU baseline
+    covers its whole AF)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2506_22935_gb300 import inputs
+    res = {}
+    phi = inputs.lfm_phases(64)
+    w1 = g.Window.full(64, 128)
+    A = g.af_forward(torch.from_numpy(phi).to(dev), 128, w1, 1e-12).cpu().numpy()[0]
+    want = oracle.af_ahat(oracle.signal_from_phase(phi.astype(np.float64)), 128, *w1.as_tuple()[:4], 1e-12)
+    res["lfm_N64_M128"] = {"ahat_max_abs": float(np.abs(A - want).max()),
+                           "ahat_rms": float(np.sqrt(np.mean((A - want) ** 2))), "cells": int(A.size)}
+    rng = np.random.default_rng(1)
+    errs = []
+    sub = [0, x.shape[0] - 1]
+    Af = g.af_forward(x[sub], M, g.Window.full(N, M), EPS).cpu().numpy()
+    for i, b in enumerate(sub):
+        ks = rng.integers(-(N - 1), N, 1024)
+        ms = rng.integers(-(M // 2), M // 2, 1024)
+        s = oracle.signal_from_phase(x[b].double().cpu().numpy())
+        want = oracle.af_cells(s, M, ks, ms, EPS)
+        errs.append(np.abs(Af[i][ks + N - 1, ms + M // 2] - want))
+    errs = np.concatenate(errs)
+    o8 = out8[0].double().cpu().numpy()
+    ref = oracle.loss(oracle.signal_from_phase(x[0].double().cpu().numpy()), M, oracle.full_window(N, M), 1.0, 1.0,
+                      BETA, EPS)
+    res["headline_B256_N1024_M2048"] = {
+        "ahat_max_abs_sampled": float(errs.max()), "ahat_rms_sampled": float(np.sqrt(np.mean(errs ** 2))),
+        "cells_sampled": int(errs.size),
+        "loss_rel_wave0": {nm: float(abs(o8[i] - ref[i]) / abs(ref[i])) for i, nm in
+                           ((0, "L"), (1, "PSL_soft"), (2, "ISL"), (3, "PSL_hard"))}}
+    return res
+
+
 def cufft_loss_grad(phi, N_len, M_len, box_m, beta, eps, chunk=64):
-    """The comparison pipeline: the same loss and gradient with the row DFTs
-    done by cuFFT (torch.fft) and the rest in eager torch ops with autograd.
+    """The comparison pipeline: the same loss and dL/dphi with every row DFT
+    and its adjoint done by cuFFT (torch.fft) and the rest in eager torch ops.
+    The gradient is written out with the split of the cell adjoint the
+    kernels use -- w (1 + p) = w_b A' + [(w - w_b) A' + w (p - p0)], p =
+    exp(beta (A2 - PSL)), p0 = exp(-beta PSL), A' = 1 + p0, w_b the weight of
+    rows whose every bin carries the same weight -- because the row-uniform
+    part contributes exactly nothing to dL/dphi; only the remainder goes
+    through the inverse FFT (an FP32 chain rule through the whole cell
+    adjoint loses the gradient to cancellation).
     phi [B, Nmax] fp32 (columns >= N_len[b] ignored), N_len [B] int64 tensor,
     one M for all.  Rows k >= 0 only, weight 2 for k > 0 (the mirror rows),
     Omega = every cell minus {k = 0, |m| <= box_m} (box_m an int or a [B]
     tensor).  Returns (L [B], dL/dphi)."""
     import torch
+    F = torch.nn.functional
     dev = phi.device
     Bn, Nmax = phi.shape
     k = torch.arange(Nmax, device=dev)
     n = torch.arange(M_len, device=dev)
     mb = torch.minimum(n, M_len - n)
     box = torch.as_tensor(box_m, device=dev).expand(Bn)
+    # q[k, p + k] for p < Nmax: row k shifted left by k
+    shift = (torch.arange(Nmax, device=dev)[None, :] + k[:, None]).clamp(max=M_len - 1)
     losses, grads = [], []
     for c0 in range(0, Bn, chunk):
-        p = phi[c0:c0 + chunk].detach().clone().requires_grad_(True)
+        p = phi[c0:c0 + chunk]
+        C = p.shape[0]
         nl = N_len[c0:c0 + chunk]
-        live = (torch.arange(Nmax, device=dev)[None, :] < nl[:, None])
+        live = (k[None, :] < nl[:, None])
         s = torch.polar(live.float(), p)
-        s_pad = torch.nn.functional.pad(s, (0, M_len - Nmax))
+        s_pad = F.pad(s, (0, M_len - Nmax))
         # row k of the lagged signal s[n - k] as a window of s with Nmax - 1
         # leading zeros (window Nmax - 1 - k), rows put back in k order
-        s_ext = torch.nn.functional.pad(s_pad, (Nmax - 1, 0))
+        s_ext = F.pad(s_pad, (Nmax - 1, 0))
         lag = s_ext.unfold(-1, M_len, 1).flip(1)
         R = s_pad[:, None, :] * torch.conj(lag)
         X = torch.fft.fft(R, dim=-1)
-        E = (s.real ** 2 + s.imag ** 2).sum(dim=1)
-        A2 = (X.real ** 2 + X.imag ** 2 + eps) / (E ** 2)[:, None, None]
+        E2 = ((s.real ** 2 + s.imag ** 2).sum(dim=1) ** 2)[:, None, None]
+        A2 = (X.real ** 2 + X.imag ** 2 + eps) / E2
         w = torch.where(k[None, :, None] == 0, 1.0, 2.0) * (k[None, :, None] < nl[:, None, None])
-        w = w * ~((k[None, :, None] == 0) & (mb[None, None, :] <= box[c0:c0 + chunk, None, None]))
+        w = w * ~((k[None, :, None] == 0) & (mb[None, None, :] <= box[c0:c0 + C, None, None]))
         isl = (w * A2).sum(dim=(1, 2))
         psl = torch.logsumexp(beta * A2 + torch.log(w), dim=(1, 2)) / beta
-        L = psl + isl
-        (gp,) = torch.autograd.grad(L.sum(), p)
-        losses.append(L.detach())
-        grads.append(gp)
+        losses.append(psl + isl)
+        p0 = torch.exp(-beta * psl)[:, None, None]
+        wb = torch.where(k[None, :, None] == 0, torch.zeros_like(w), w)  # rows k >= 1 are uniform
+        c = (w - wb) * (1.0 + p0) + w * p0 * torch.expm1(beta * A2)
+        GR = torch.fft.ifft(c * X / E2, dim=-1) * M_len   # the adjoint DFT of each row
+        q = (GR * torch.conj(R)).imag                    # Im(G_R conj(R))
+        del R, X, GR
+        t2 = torch.gather(q, 2, shift[None].expand(C, -1, -1)).sum(dim=1)
+        grads.append(2.0 * (q.sum(dim=1)[:, :Nmax] - t2) * live)
+        del q
     return torch.cat(losses), torch.cat(grads)
 
 
@@ -719,9 +822,9 @@ def run_periodic(args):
 def run_lpi(args):
     """The paper's experiment (Sec. 7.1): L = PSL + lambda alpha SV (Eq. 25),
     alpha = 2000, periodic AF of Eq. 7, N = 256 phase codes, Adam lr 0.01,
-    2000 iterations; PSL taken as the log-sum-exp maximum over every cell but
-    the origin (beta = 100), reported as the hard maximum.  64 random codes per
-    lambda, each lambda's 2000 steps captured in one CUDA graph."""
+    2000 iterations; PSL the hard maximum of Ahat^2 over every cell but the
+    origin (Eq. 18, differentiated through its arg-max cell).  64 random codes
+    per lambda, each lambda's 2000 steps captured in one CUDA graph."""
     import numpy as np
     import torch
 
@@ -732,7 +835,7 @@ def run_lpi(args):
     g.load()
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
-    Bl, Nl, STEPS, ALPHA, BETA_L = 64, 256, 2000, 2000.0, 100.0
+    Bl, Nl, STEPS, ALPHA, BETA_L = 64, 256, 2000, 2000.0, math.inf
     seed = 2506229350 + 7
     phi0 = torch.from_numpy(inputs.random_phases(seed, Bl, Nl)).to(dev)
     win = g.Window.periodic(Nl)
@@ -781,7 +884,7 @@ def run_lpi(args):
             "value": v, "unit": "GPU ms per code-run at lambda = 0.5 (64 codes per graph)",
             "higher_is_better": False, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{Bl} random codes per lambda, periodic AF (Eq. 7, +j), N={Nl}, "
-                                   f"alpha={ALPHA:.0f}, beta={BETA_L:.0f}, Adam lr 1e-2, {STEPS} steps",
+                                   f"alpha={ALPHA:.0f}, hard PSL (Eq. 18), Adam lr 1e-2, {STEPS} steps",
                        "seed": seed},
             "vs_paper": {"paper_seconds_per_run_lambda_0.5_cpu": 67.0,
                          "paper_spectral_variance": {"0": 2.02e-5, "0.5": 3.03e-6, "2": 8.02e-7}},
@@ -890,7 +993,11 @@ def run_learned(args):
     secs, label_curve, graf_curve = {}, [], []
     if args.label_epochs > 0:
         t0 = time.perf_counter()
-        codes, _ = learned.optimise_codes(train, learned.lfm_init(args.train_specs), args.label_steps, device=dev)
+        init = (learned.lfm_init(args.train_specs) if args.label_init == "lfm"
+                else learned.common_init(args.train_specs, SEED + 12))
+        codes, lh = learned.optimise_codes(train, init, args.label_steps, isl_only=bool(args.label_isl_only),
+                                           device=dev)
+        secs["label_isl_median_start_end"] = [float(np.median(lh[0])), float(np.median(lh[-1]))]
         secs["labels"] = time.perf_counter() - t0
         feats = torch.from_numpy(inputs.spec_features(train)).to(dev)
         tgt = torch.from_numpy(codes).to(dev)
@@ -922,6 +1029,7 @@ def run_learned(args):
             "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "dtype": "bf16 mlp, f32 af",
             "config": {"workload": f"{args.train_specs} training specs, {args.test_specs} held-out, N=1024, M=2048",
                        "label_epochs": args.label_epochs, "label_steps": args.label_steps,
+                       "label_init": args.label_init, "label_isl_only": args.label_isl_only,
                        "graf_epochs": args.graf_epochs, "train_isl_only": args.train_isl_only,
                        "eval_steps": args.eval_steps},
             "learned_wins_fraction": float(np.mean(r["time_learned_ms"] < r["time_random_ms"])),
@@ -948,6 +1056,7 @@ def main():
     ap.add_argument("--impl", default="graf", choices=["graf", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison pipeline")
+    ap.add_argument("--no-forward-store", action="store_true", help="skip the full-AF forward store timing")
     ap.add_argument("--batch", type=int, default=B,
                     help="waveforms per GPU (default 256, the benchmark workload; smaller only for profiling)")
     ap.add_argument("--workload", default="af", choices=["af", "learned", "optim", "ragged", "periodic", "lpi",
@@ -959,6 +1068,8 @@ def main():
     ap.add_argument("--test-specs", type=int, default=512)
     ap.add_argument("--label-steps", type=int, default=300)
     ap.add_argument("--label-epochs", type=int, default=0)
+    ap.add_argument("--label-init", default="common", choices=["common", "lfm"])
+    ap.add_argument("--label-isl-only", type=int, default=0)
     ap.add_argument("--graf-epochs", type=int, default=400)
     ap.add_argument("--train-isl-only", type=int, default=1)
     ap.add_argument("--batch-mlp", type=int, default=256)

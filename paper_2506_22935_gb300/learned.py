@@ -164,9 +164,17 @@ def spec_windows_losses(specs, isl_only=False, beta=50.0):
 
 
 def lfm_init(count: int) -> np.ndarray:
-    """The deterministic starting code of the label optimiser: the discrete
+    """A deterministic starting code for the label optimiser: the discrete
     chirp pi n^2 / N for every spec."""
     return np.tile(inputs.lfm_phases(N_CODE), (count, 1))
+
+
+def common_init(count: int, seed: int) -> np.ndarray:
+    """The label optimiser's starting code: one seeded random phase code,
+    the same for every spec, so that each spec's label is that code carried
+    to its own optimum and labels vary with the spec rather than with the
+    start (a learnable map)."""
+    return np.tile(inputs.random_phases(seed, 1, N_CODE)[0], (count, 1))
 
 
 def optimise_codes(specs, phi0: np.ndarray, steps: int, isl_only=False, device=None, graph=True, chunk=1024):

@@ -11,7 +11,7 @@ import oracle
 from paper_2506_22935_gb300 import inputs
 
 
-@pytest.mark.parametrize("Ns,M", [([16, 11, 5], 32), ([24, 24], 64)])
+@pytest.mark.parametrize("Ns,M", [([16, 11, 5], 32), ([24, 24], 64), ([100, 64], 256)])
 def test_cufft_pipeline_matches_oracle(Ns, M):
     nmax = max(Ns)
     phi = np.zeros((len(Ns), nmax), dtype=np.float32)
@@ -27,5 +27,5 @@ def test_cufft_pipeline_matches_oracle(Ns, M):
         _, gp, out = oracle.grad(s, M, win, 1.0, 1.0, 50.0, 1e-12)
         assert abs(float(L[b]) - out[0]) <= 1e-5 * abs(out[0])
         g = gphi[b, :n].double().numpy()
-        assert np.linalg.norm(g - gp) <= 1e-3 * np.linalg.norm(gp) + 1e-6
+        assert np.linalg.norm(g - gp) <= 1e-4 * np.linalg.norm(gp) + 1e-7
         assert np.all(gphi[b, n:].numpy() == 0)
