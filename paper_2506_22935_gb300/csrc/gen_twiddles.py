@@ -13,8 +13,8 @@ an exact integer ratio and rounded once to float32:
   read consecutive i, so the loads coalesce.
 
 The radix plan must match ``graf_fft.cuh``: R_0 = the values per thread
-(32 from M = 128 on, else min(M, 64)) and the rest of M / R_0 is one
-pass if it is <= R_0, else 16 x (M / (16 R_0)).
+(32 from M = 512 on, 16 for M = 128 and 256, else min(M, 64)) and the rest
+of M / R_0 is one pass if it is <= R_0, else 16 x (M / (16 R_0)).
 """
 from __future__ import annotations
 
@@ -25,7 +25,7 @@ M_ALL = [8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 8192, 16384]
 
 
 def radix_plan(M: int) -> list[int]:
-    r0 = 32 if M >= 128 else min(M, 64)
+    r0 = 32 if M >= 512 else (16 if M >= 128 else min(M, 64))
     rest = M // r0
     if rest == 1:
         return [r0]

@@ -7,8 +7,8 @@
 // unnormalised).
 //
 // Layout: a row of length M is owned by TPR = M / VALS threads, VALS = 32
-// complex values per thread in registers (64 for M = 64, M below; see
-// RowPlan).  On entry AND on exit thread t
+// complex values per thread in registers (16 for M = 128 and 256, 64 for
+// M = 64, M below; see RowPlan).  On entry AND on exit thread t
 // holds element t + TPR * w in register w ("natural strided" layout), so the
 // lag-product builder, the loss epilogue and the gradient scatter all index
 // the same way and the forward and inverse transforms chain without any
@@ -188,21 +188,23 @@ __host__ __device__ __forceinline__ void dft(float2* v) {
 template <int M>
 struct RowPlan {
     static_assert(M >= 8 && M <= 16384 && (M & (M - 1)) == 0, "M must be a power of two in [8,16384]");
-    // values per thread: 32 from M = 128 on, so that a thread needs at most
+    // values per thread: 32 from M = 512 on, so that a thread needs at most
     // 128 registers and 16 warps share an SM (two CTAs of 256 threads, or one
     // of 512 threads for M = 16384, whose row spans 512 threads); a third FFT
-    // pass from M = 2048 on is the price.  64 for M = 64, M below.
-    static constexpr int VALS = M >= 128 ? 32 : (M < 64 ? M : 64);
+    // pass from M = 2048 on is the price.  16 for M = 128 and 256 (still two
+    // passes; the fused kernel's per-row state then fits 128 registers
+    // without spilling).  64 for M = 64, M below.
+    static constexpr int VALS = M >= 512 ? 32 : (M >= 128 ? 16 : (M < 64 ? M : 64));
     static constexpr int TPR = M / VALS;           // threads per row
     static constexpr int THREADS = TPR > 256 ? TPR : 256;  // threads per CTA
     static constexpr int NPASS = TPR == 1 ? 1 : (TPR <= VALS ? 2 : 3);
     static constexpr int R0 = VALS;
     static constexpr int R1 = NPASS == 1 ? 1 : (NPASS == 2 ? TPR : 16);
     static constexpr int R2 = NPASS == 3 ? TPR / 16 : 1;
-    static constexpr int MIN_BLOCKS = (VALS == 32 && THREADS == 256) ? 2 : 1;  // CTAs per SM the registers allow
+    static constexpr int MIN_BLOCKS = ((VALS == 32 || VALS == 16) && THREADS == 256) ? 2 : 1;  // CTAs per SM the registers allow
     // shared-memory row buffer (float2 units): one pad slot per VALS values
     // keeps the stride-VALS stores of the first pass free of bank conflicts
-    static constexpr int PAD = VALS < 32 ? 64 : VALS;
+    static constexpr int PAD = VALS < 16 ? 64 : VALS;
     static constexpr int SMEM_ROW = NPASS == 1 ? 0 : M + M / PAD;
     // exchange real and imaginary halves separately (half the buffer) for the
     // largest rows so that the backward's accumulators still fit

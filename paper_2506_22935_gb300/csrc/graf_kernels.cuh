@@ -228,7 +228,7 @@ struct Tiling {
 };
 
 // Host mirrors of RowPlan<M>: threads per row and per CTA.
-inline int tpr_of(int M) { return M >= 128 ? M / 32 : (M < 64 ? 1 : M / 64); }
+inline int tpr_of(int M) { return M >= 512 ? M / 32 : (M >= 128 ? M / 16 : (M < 64 ? 1 : M / 64)); }
 inline int threads_of(int M) { return tpr_of(M) > 256 ? tpr_of(M) : 256; }
 inline int slots_of(int M) { return threads_of(M) / tpr_of(M); }
 
