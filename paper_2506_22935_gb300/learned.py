@@ -177,13 +177,20 @@ def common_init(count: int, seed: int) -> np.ndarray:
     return np.tile(inputs.random_phases(seed, 1, N_CODE)[0], (count, 1))
 
 
-def optimise_codes(specs, phi0: np.ndarray, steps: int, isl_only=False, device=None, graph=True, chunk=1024):
+def optimise_codes(specs, phi0: np.ndarray, steps: int, isl_only=False, device=None, graph=True, chunk=1024,
+                   step_events=False):
     """Adam (lr 1e-2) on each spec's own masked loss from phi0 [count, N].
-    Returns (codes [count, N], loss history [steps, count]) as numpy."""
+    Returns (codes [count, N], loss history [steps, count]) as numpy; with
+    step_events (count <= chunk), also the GPU time in ms from the start of
+    the run to the end of each step, [steps], from a CUDA event recorded after
+    every step (the steps are then enqueued one by one)."""
     device = device or torch.device("cuda", torch.cuda.current_device())
     count = phi0.shape[0]
+    if step_events and count > chunk:
+        raise ValueError("per-step events need the specs in one chunk")
     codes = np.empty_like(phi0, dtype=np.float32)
     hist = np.empty((steps, count), dtype=np.float32)
+    step_ms = None
     for c0 in range(0, count, chunk):
         c1 = min(count, c0 + chunk)
         sub = {k: v[c0:c1] for k, v in specs.items()}
@@ -192,11 +199,25 @@ def optimise_codes(specs, phi0: np.ndarray, steps: int, isl_only=False, device=N
                            device=device)
         phi = torch.from_numpy(np.ascontiguousarray(phi0[c0:c1], dtype=np.float32)).to(device)
         opt = PhaseOptimizer(phi.view(-1), plan=plan, history_len=steps)
-        opt.run(steps, graph=graph)
+        if step_events:
+            stream = torch.cuda.current_stream(device)
+            start = torch.cuda.Event(enable_timing=True)
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+            torch.cuda.synchronize(device)
+            start.record(stream)
+            for i in range(steps):
+                opt.enqueue_step()
+                evs[i].record(stream)
+            torch.cuda.synchronize(device)
+            step_ms = np.array([start.elapsed_time(e) for e in evs])
+        else:
+            opt.run(steps, graph=graph)
         torch.cuda.synchronize(device)
         codes[c0:c1] = phi.cpu().numpy()
         hist[:, c0:c1] = opt.history.cpu().numpy()
         plan.close()
+    if step_events:
+        return codes, hist, step_ms
     return codes, hist
 
 
@@ -208,47 +229,56 @@ def steps_to_target(hist: np.ndarray, target: np.ndarray) -> np.ndarray:
     return first + 1
 
 
-def time_to_target(mlp: ProposalMLP, specs, steps=500, seeds=4, seed_base=7000, device=None):
-    """Per spec: target T = median over `seeds` random initialisations of the
-    masked ISL after `steps` Adam steps; then the steps (and GPU time) the
-    optimiser needs to reach T from the MLP proposal and from one more random
-    initialisation.  Returns a dict of numpy arrays and timings."""
-    device = device or torch.device("cuda", torch.cuda.current_device())
-    count = len(specs["K"])
+def masked_isl_targets(specs, steps=500, seeds=4, seed_base=7000, device=None) -> np.ndarray:
+    """Per spec, the target T: the median over `seeds` random initialisations
+    of the masked ISL after `steps` Adam steps of the plain optimiser."""
     finals = []
     for s in range(seeds):
-        phi0 = inputs.random_phases(seed_base + s, count, N_CODE)
+        phi0 = inputs.random_phases(seed_base + s, len(specs["K"]), N_CODE)
         _, h = optimise_codes(specs, phi0, steps, isl_only=True, device=device)
         finals.append(h[-1])
-    target = np.median(np.stack(finals), axis=0)
+    return np.median(np.stack(finals), axis=0)
+
+
+def random_run(specs, steps=500, seed=7004, device=None):
+    """The plain optimiser from one more random initialisation, timed per
+    step: (loss history [steps, count], ms to the end of each step)."""
+    phi_r = inputs.random_phases(seed, len(specs["K"]), N_CODE)
+    _, h, ms = optimise_codes(specs, phi_r, steps, isl_only=True, device=device, step_events=True)
+    return h, ms
+
+
+def _run_time(ms, s):
+    """GPU time to the end of the step whose loss first meets the target
+    (s, 1-based); the whole run plus one step where it never does."""
+    return np.where(s <= len(ms), ms[np.minimum(s, len(ms)) - 1], ms[-1] * (1.0 + 1.0 / len(ms)))
+
+
+def time_to_target(mlp: ProposalMLP, specs, target: np.ndarray, random: tuple, steps=500, device=None):
+    """Per held-out spec: the GPU time the optimiser needs to bring the spec
+    to its target T (masked_isl_targets) from the MLP proposal -- the
+    batch's MLP inference, timed with CUDA events, plus the run -- and from a
+    random initialisation (random_run).  Both runs take every spec in one
+    batch with a CUDA event after each step: a spec's time is the batch's
+    measured time to the end of the step whose loss evaluation first meets T;
+    a spec that does not reach T within `steps` is charged the whole run plus
+    one step.  Returns numpy arrays and timings."""
+    device = device or torch.device("cuda", torch.cuda.current_device())
     feats = torch.from_numpy(inputs.spec_features(specs)).to(device)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    mlp.forward(feats)  # warm-up
+    torch.cuda.synchronize(device)
     e0.record()
     prop = mlp.forward(feats)
     e1.record()
     torch.cuda.synchronize(device)
     mlp_ms = e0.elapsed_time(e1)
     prop = np.mod(prop.cpu().numpy(), 2 * math.pi).astype(np.float32)
-    e0.record()
-    _, h_learned = optimise_codes(specs, prop, steps, isl_only=True, device=device)
-    e1.record()
-    torch.cuda.synchronize(device)
-    learned_ms = e0.elapsed_time(e1)
-    phi_r = inputs.random_phases(seed_base + seeds, count, N_CODE)
-    e0.record()
-    _, h_random = optimise_codes(specs, phi_r, steps, isl_only=True, device=device)
-    e1.record()
-    torch.cuda.synchronize(device)
-    random_ms = e0.elapsed_time(e1)
+    _, h_learned, ms_l = optimise_codes(specs, prop, steps, isl_only=True, device=device, step_events=True)
+    h_random, ms_r = random
     s_l = steps_to_target(h_learned, target)
     s_r = steps_to_target(h_random, target)
-    # GPU time per spec: its share of the batch's inference plus the steps it
-    # needs at the batch's measured time per step and spec
-    t_step_l = learned_ms / (steps * count)
-    t_step_r = random_ms / (steps * count)
-    time_l = mlp_ms / count + s_l * t_step_l
-    time_r = s_r * t_step_r
     return dict(target=target, steps_learned=s_l, steps_random=s_r, isl0_learned=h_learned[0],
                 isl0_random=h_random[0], final_learned=h_learned[-1], final_random=h_random[-1],
-                time_learned_ms=time_l, time_random_ms=time_r, mlp_ms=mlp_ms, run_ms_learned=learned_ms,
-                run_ms_random=random_ms, steps=steps)
+                time_learned_ms=mlp_ms + _run_time(ms_l, s_l), time_random_ms=_run_time(ms_r, s_r),
+                mlp_ms=mlp_ms, run_ms_learned=float(ms_l[-1]), run_ms_random=float(ms_r[-1]), steps=steps)
