@@ -491,14 +491,14 @@ __device__ __forceinline__ void write_grad_partial(const AfParams& p, const Wave
         const float* acc_r = reinterpret_cast<const float*>(acc_all);
         for (int n = tid; n < wv.N; n += P::THREADS) {
             float a = acc_r[n];
-            for (int s = 1; s < p.acc_copies; ++s) a += acc_r[(size_t)s * wv.N + n];
+            for (int s = 1; s < p.acc_copies; ++s) a += acc_r[(size_t)s * acc_stride(wv.N, P::TPR) + n];
             out[n] = make_float2(a, 0.0f);
         }
         return;
     }
     for (int n = tid; n < wv.N; n += P::THREADS) {
         float2 a = acc_all[n];
-        for (int s = 1; s < p.acc_copies; ++s) a = cadd(a, acc_all[(size_t)s * wv.N + n]);
+        for (int s = 1; s < p.acc_copies; ++s) a = cadd(a, acc_all[(size_t)s * acc_stride(wv.N, P::TPR) + n]);
         out[n] = a;
     }
 }
@@ -538,8 +538,8 @@ __device__ __forceinline__ void backward_item(const AfParams& p, int b, int tile
     // slots sharing an accumulator (when shared memory is short) take turns
     const int turns = SLOTS / p.acc_copies;
     const int my_turn = slot / p.acc_copies;
-    float2* acc = acc_all + (size_t)(slot % p.acc_copies) * wv.N;
-    float* acc_r = reinterpret_cast<float*>(acc_all) + (size_t)(slot % p.acc_copies) * wv.N;
+    float2* acc = acc_all + (size_t)(slot % p.acc_copies) * acc_stride(wv.N, P::TPR);
+    float* acc_r = reinterpret_cast<float*>(acc_all) + (size_t)(slot % p.acc_copies) * acc_stride(wv.N, P::TPR);
 
     const int row0 = wv.r_lo + tile * wv.rows_per_tile;
     const int row_end = min(row0 + wv.rows_per_tile, wv.r_hi + 1);
@@ -626,8 +626,8 @@ __device__ __forceinline__ void match_item(const AfParams& p, int b, int tile, u
     const ColMasks cm = col_masks<M>(wv, t);
     const int turns = SLOTS / p.acc_copies;
     const int my_turn = slot / p.acc_copies;
-    float2* acc = acc_all + (size_t)(slot % p.acc_copies) * wv.N;
-    float* acc_r = reinterpret_cast<float*>(acc_all) + (size_t)(slot % p.acc_copies) * wv.N;
+    float2* acc = acc_all + (size_t)(slot % p.acc_copies) * acc_stride(wv.N, P::TPR);
+    float* acc_r = reinterpret_cast<float*>(acc_all) + (size_t)(slot % p.acc_copies) * acc_stride(wv.N, P::TPR);
     const int ncols = wv.m_hi - wv.m_lo + 1;
     const float* tgt = p.target + (size_t)b * (wv.k_hi - wv.k_lo + 1) * ncols;
 
@@ -1065,8 +1065,8 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
     constexpr unsigned long long full_mask = P::VALS == 64 ? ~0ull : ((1ull << P::VALS) - 1ull);
     const int turns = SLOTS / p.acc_copies;
     const int my_turn = slot / p.acc_copies;
-    float2* acc = acc_all + (size_t)(slot % p.acc_copies) * wv.N;
-    float* acc_r = reinterpret_cast<float*>(acc_all) + (size_t)(slot % p.acc_copies) * wv.N;
+    float2* acc = acc_all + (size_t)(slot % p.acc_copies) * acc_stride(wv.N, P::TPR);
+    float* acc_r = reinterpret_cast<float*>(acc_all) + (size_t)(slot % p.acc_copies) * acc_stride(wv.N, P::TPR);
 
     const int row0 = wv.r_lo + tile * wv.rows_per_tile;
     const int row_end = min(row0 + wv.rows_per_tile, wv.r_hi + 1);

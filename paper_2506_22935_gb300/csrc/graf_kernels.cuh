@@ -122,10 +122,21 @@ template <int M> cudaError_t run_spectral_m(const SpecParams& q, cudaStream_t st
 // Shared-memory length of the signal: N, or 2N for the periodic AF (the
 // signal twice, so that s[(n - k) mod N] is one load).
 __host__ __device__ __forceinline__ int sig_len(const AfParams& p) { return p.periodic ? 2 * p.N : p.N; }
-// Bytes of all gradient accumulators of a CTA (N entries each, 256-byte
-// aligned).
+// Host and device mirror of RowPlan<M>::TPR: threads per row.
+__host__ __device__ __forceinline__ int tpr_of(int M) {
+    return M >= 512 ? M / 32 : (M >= 128 ? M / 16 : (M < 64 ? 1 : M / 64));
+}
+
+// Elements (float or float2) from one gradient accumulator of a CTA to the
+// next: N, plus TPR when a warp holds several row slots (TPR < 32), so that
+// the slots of one warp, which use consecutive accumulators, fall in
+// different shared-memory banks.
+__host__ __device__ __forceinline__ int acc_stride(int N, int tpr) { return N + (tpr < 32 ? tpr : 0); }
+
+// Bytes of all gradient accumulators of a CTA (256-byte aligned).
 __host__ __device__ __forceinline__ size_t acc_region_bytes(const AfParams& p) {
-    return ((size_t)p.acc_copies * p.N * (p.phase_only ? sizeof(float) : sizeof(float2)) + 255) &
+    return ((size_t)p.acc_copies * acc_stride(p.N, tpr_of(p.M)) * (p.phase_only ? sizeof(float) : sizeof(float2)) +
+            255) &
            ~(size_t)255;
 }
 
@@ -227,8 +238,7 @@ struct Tiling {
     int r_lo, r_hi, nrows, slots, rows_per_tile, tiles;
 };
 
-// Host mirrors of RowPlan<M>: threads per row and per CTA.
-inline int tpr_of(int M) { return M >= 512 ? M / 32 : (M >= 128 ? M / 16 : (M < 64 ? 1 : M / 64)); }
+// Host mirrors of RowPlan<M>: threads per CTA and row slots (tpr_of above).
 inline int threads_of(int M) { return tpr_of(M) > 256 ? tpr_of(M) : 256; }
 inline int slots_of(int M) { return threads_of(M) / tpr_of(M); }
 
@@ -256,7 +266,9 @@ constexpr size_t forward_smem(int N) {
 template <int M>
 constexpr size_t backward_smem(int N, int acc_copies, int real = 0, int per = 0) {
     return smem_signal_bytes<M>(per ? 2 * N : N) + row_buffer_bytes<M>() +
-           (((size_t)acc_copies * N * (real ? sizeof(float) : sizeof(float2)) + 255) & ~(size_t)255) + kRedBytes;
+           (((size_t)acc_copies * acc_stride(N, RowPlan<M>::TPR) * (real ? sizeof(float) : sizeof(float2)) + 255) &
+            ~(size_t)255) +
+           kRedBytes;
 }
 // Number of gradient accumulators per CTA (a power of two <= slots; slots
 // sharing one take turns in the scatter): the largest that still lets the
