@@ -613,15 +613,20 @@ def run_optim(args):
     exe_step = B3 * 2 * (K3 + 1) * 5.0 * M3 * math.log2(M3)   # both transforms of the rows k >= 0
     peak, peak_src = _fp32_peak(dev)
     achieved = alg_step * STEPS / (ms_graph / 1e3) / 1e12
-    cpu = None
+    cpu, errors = None, None
     if not args.no_cpu_baseline:
         import oracle
         s = oracle.signal_from_phase(phi0[0].cpu().numpy().astype(np.float64))
         win = (-K3, K3, -W3, W3, 0, 0)
         cores = os.cpu_count() or 1
         t0 = time.perf_counter()
-        oracle.grad(s, M3, win, 0.0, 1.0, BETA, EPS, nthreads=cores)
+        _, gp_ref, o8_ref = oracle.grad(s, M3, win, 0.0, 1.0, BETA, EPS, nthreads=cores)
         dt = time.perf_counter() - t0
+        o8_0, g_0 = g.af_loss_backward(phi0[:1], M3, g.Window.masked(K3, W3), g.Loss(0.0, 1.0, BETA, EPS))
+        torch.cuda.synchronize()
+        g_0 = g_0[0].double().cpu().numpy()
+        errors = {"code0_step0_grad_rel_l2": float(np.linalg.norm(g_0 - gp_ref) / np.linalg.norm(gp_ref)),
+                  "code0_step0_isl_rel": float(abs(float(o8_0[0, 2]) - o8_ref[2]) / o8_ref[2])}
         cpu = {"value": dt * B3 * STEPS * 1e3, "unit": "ms per run (extrapolated)", "cores": cores,
                "kind": "oracle", "sample": f"one FP64 loss + gradient of 1 of {B3} codes ({dt:.1f} s), "
                                            f"x {B3} codes x {STEPS} steps, Adam update not counted"}
@@ -638,7 +643,8 @@ def run_optim(args):
                          "executed_frac": achieved * exe_step / alg_step / peak,
                          "peak_source": peak_src},
             "isl_median_start": float(np.median(hist[0])), "isl_median_end": float(np.median(hist[-1])),
-            "cpu_baseline": cpu, "gpu_launches": 5 * STEPS * runs, "clocks": clk.summary()}
+            "cpu_baseline": cpu, "errors_vs_fp64": errors, "gpu_launches": 5 * STEPS * runs,
+            "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
 
@@ -746,6 +752,23 @@ def run_ragged(args):
                "what": "per-M buckets padded to the longest code, torch.fft (cuFFT) + eager torch ops + autograd"}
         del res, parts
         torch.cuda.empty_cache()
+    errors = None
+    if not args.no_cpu_baseline:
+        import oracle
+        o8h, gh = ref8.cpu().numpy(), refg.cpu().numpy()
+        errors = {}
+        for Mb in sorted(set(Ms.tolist())):
+            if Mb > 8192:  # the M = 16384 bucket's shortest code costs ~3 min of oracle time: in the slow test
+                continue
+            ids = np.nonzero(Ms == Mb)[0]
+            b = int(ids[np.argmin(Ns[ids])])
+            n = int(Ns[b])
+            sb = oracle.signal_from_phase(phi_h[offs[b]:offs[b + 1]].astype(np.float64))
+            _, gp, o8r = oracle.grad(sb, Mb, oracle.full_window(n, Mb), 1.0, 1.0, BETA, EPS)
+            gb = gh[offs[b]:offs[b + 1]].astype(np.float64)
+            errors[f"M{Mb}_N{n}"] = {"grad_rel_l2": float(np.linalg.norm(gb - gp) / np.linalg.norm(gp)),
+                                     "loss_rel": float(abs(o8h[b, 0] - o8r[0]) / abs(o8r[0]))}
+        say("oracle checks done")
     plan.close()
     peak, peak_src = _fp32_peak(dev)
     achieved = alg / (ms_tuned / 1e3) / 1e12
@@ -762,7 +785,9 @@ def run_ragged(args):
                          "frac": achieved / peak, "traffic": None, "algorithmic_flop_per_step": alg,
                          "executed_flop_per_step": exe, "executed_frac": achieved * exe / alg / peak,
                          "peak_source": peak_src},
-            "cufft_pipeline": cmp, "clocks": clk.summary()}
+            "cufft_pipeline": cmp, "clocks": clk.summary(),
+            "errors_vs_fp64": errors, "errors_note": "the shortest code of each M bucket up to 8192 against the "
+                                                     "FP64 oracle (every bucket up to 16384 in the slow GPU test)"}
     print(json.dumps(line), flush=True)
 
 
@@ -804,6 +829,16 @@ def run_periodic(args):
     achieved = alg / (ms / 1e3) / 1e12
     chi = g.paf_forward(x[:64], 1, normalise=True)
     torch.cuda.synchronize()
+    import numpy as np
+
+    import oracle
+    s0 = oracle.signal_from_phase(x[0].double().cpu().numpy())
+    _, gp, o8r = oracle.pgrad(s0, w.as_tuple(), 1.0, 1.0, BETA, EPS, sign=1)
+    chi_ref = oracle.paf_chi(s0, 1, normalise=True)
+    g0 = grad[0].double().cpu().numpy()
+    errors = {"code0_grad_rel_l2": float(np.linalg.norm(g0 - gp) / np.linalg.norm(gp)),
+              "code0_loss_rel": float(abs(float(out8[0, 0]) - o8r[0]) / abs(o8r[0])),
+              "code0_chi_max_abs": float(np.abs(chi[0].double().cpu().numpy() - chi_ref).max())}
     line = {"metric": "periodic AF fwd+bwd Gcells/s at N=256", "value": cells / (ms / 1e3) / 1e9,
             "unit": UNIT, "higher_is_better": True, "n_gpus": 1, "steps": steps, "warmup": 5,
             "ms_per_step": ms, "dtype": "f32", "data": "synthetic",
@@ -816,7 +851,7 @@ def run_periodic(args):
                          "executed_flop_per_step": exe, "executed_frac": achieved * exe / alg / peak,
                          "peak_source": peak_src},
             "mean_psl_hard": float(out8[:, 3].mean()), "mean_chi_max": float(chi.amax(dim=(1, 2)).mean()),
-            "clocks": clk.summary()}
+            "errors_vs_fp64": errors, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
 
