@@ -114,6 +114,9 @@ GRAF_API int32_t graf_version(void);
  * graf_paf_*, the batch plans) and of graf_af_match. */
 #define GRAF_DEVERR_ENERGY 1u    /* a waveform's energy E = sum |s|^2 was 0 or not finite */
 #define GRAF_DEVERR_NONFINITE 2u /* a loss scalar came out not finite (NaN or Inf in the input) */
+#define GRAF_DEVERR_TIMEOUT 4u   /* a bounded wait of a tensor-core kernel (the proposal MLP's GEMMs) ran
+                                    out: that kernel stopped, freed its tensor memory, and its output is
+                                    not valid */
 
 /*
  * graf_get_device_error_word - takes the current device's error word in

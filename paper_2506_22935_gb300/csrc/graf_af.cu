@@ -17,6 +17,14 @@ __device__ unsigned int g_device_error_taken;
 
 __global__ void take_device_error_kernel() { g_device_error_taken = atomicExch(&g_device_error, 0u); }
 
+// Device address of this device's error word in the current context (looked
+// up at every call: a reset or another context moves it); nullptr on error.
+unsigned int* device_error_word_address() {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_device_error) != cudaSuccess) return nullptr;
+    return static_cast<unsigned int*>(p);
+}
+
 int device_sm_count() {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&

@@ -1,8 +1,8 @@
 // graf_mlp.cu - the learned proposal network: an MLP that maps a design spec
 // to initial phase codes (the "neural network -> waveform -> GRAF layer ->
 // loss" pipeline of the paper's Sec. 6.1), trained and run entirely by these
-// kernels.  BF16 operands on the tensor cores (mma.sync m16n8k16), FP32
-// accumulation, FP32 master weights.
+// kernels.  BF16 operands on the 5th-generation tensor cores (tcgen05.mma,
+// accumulators in tensor memory), FP32 accumulation, FP32 master weights.
 //
 // Layer l: Y = X W_l + b_l (X [rows][K] bf16 row-major, W_l [K][N] bf16
 // row-major, b_l fp32), followed by GELU on the hidden layers.  Activations
@@ -15,10 +15,11 @@
 
 #include "graf.h"
 
-namespace {
+namespace graf {
+unsigned int* device_error_word_address();  // graf_af.cu
+}
 
-constexpr int BM = 64, BN = 64, BK = 16;  // CTA tile
-constexpr int PAD = 8;                    // bf16 elements of row padding in shared memory
+namespace {
 
 // GELU(x) = x Phi(x), Phi the standard normal CDF; GELU'(x) = Phi(x) + x phi(x).
 __device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
@@ -32,15 +33,6 @@ __device__ __forceinline__ unsigned pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi
     return (unsigned)__bfloat16_as_ushort(lo) | ((unsigned)__bfloat16_as_ushort(hi) << 16);
 }
 
-// D = A B + D for one 16x8x16 tile (PTX mma.sync, row.col, bf16 -> f32).
-__device__ __forceinline__ void mma16816(float* d, const unsigned* a, const unsigned* b) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
 enum Epi { EPI_BIAS_GELU = 0, EPI_BIAS = 1, EPI_DGELU = 2, EPI_STORE = 3 };
 
 // C[M][N] = op(A) op(B) with
@@ -51,93 +43,253 @@ enum Epi { EPI_BIAS_GELU = 0, EPI_BIAS = 1, EPI_DGELU = 2, EPI_STORE = 3 };
 //   EPI_BIAS:      out_f32 = C + bias[n]
 //   EPI_DGELU:     out_bf16 = bf16(C * GELU'(aux[m][n]))   (aux: pre-activation below)
 //   EPI_STORE:     out_f32 = C
-// 4 warps, each a 32x32 sub-tile (2 x 4 mma tiles); K stepped by 16 through
-// shared memory, where A is kept [m][k] and B [n][k] (k contiguous), the
-// fragment orders of mma.sync's row.col form.
-template <bool TA, bool TB, int EPI>
-__global__ void __launch_bounds__(128) gemm_bf16_kernel(const __nv_bfloat16* __restrict__ A, int lda,
-                                                         const __nv_bfloat16* __restrict__ B, int ldb, int M,
-                                                         int N, int K, const float* __restrict__ bias,
-                                                         const float* __restrict__ aux, int ldaux,
-                                                         float* __restrict__ out_f32,
-                                                         __nv_bfloat16* __restrict__ out_bf16, int ldo) {
-    __shared__ __align__(16) __nv_bfloat16 As[BM][BK + PAD];
-    __shared__ __align__(16) __nv_bfloat16 Bs[BN][BK + PAD];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    const int g = lane >> 2, q = lane & 3;
-    float acc[2][4][4];
+//
+// ------------------------------------------------------- tcgen05 / TMEM GEMM
+// The GEMM runs on the 5th-generation tensor cores: one
+// CTA of 4 warps per 128 x 64 tile of C; per 64-wide step of K, the threads
+// stage A (128 rows of M) and B (64 rows of N), both K-major, in shared
+// memory in the canonical layout without swizzle -- 8 x 8 core matrices of
+// 128 B, core (row / 8, k / 8) at ((row / 8) (64 / 8) + k / 8) 128 B, with
+// 16-byte loads and stores where k is the operand's contiguous index -- then
+// one thread issues four tcgen05.mma.kind::f16 (M = 128, N = 64, K = 16,
+// BF16 in, FP32 accumulated in tensor memory) and commits them to an
+// mbarrier that every thread waits on before the tiles are refilled.  The
+// accumulator (128 lanes x 64 columns of TMEM) is read back with tcgen05.ld,
+// warp w owning lanes 32w .. 32w + 31 (rows of the tile), and goes through the
+// epilogue.  Every wait is bounded (about a second of clock cycles); one that
+// runs out sets GRAF_DEVERR_TIMEOUT in the device error word, and the CTA
+// skips the rest, frees its tensor memory and returns.
+constexpr int TC_BM = 128, TC_BN = 64, TC_BK = 64, TC_THREADS = 128;
+constexpr int TC_A_BYTES = TC_BM * TC_BK * 2;                  // 16 KB
+constexpr int TC_B_BYTES = TC_BN * TC_BK * 2;                  // 8 KB
+constexpr int TC_SMEM_LAUNCH = 29 * 1024;                      // at most 7 CTAs per SM: 7 x 64 <= 512 TMEM columns
+constexpr long long TC_WAIT_CYCLES = 2000000000LL;             // ~1 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Byte offset of element (row, k) of a K-major tile with 64 columns of K in
+// the canonical no-swizzle layout.
+__device__ __forceinline__ uint32_t core_offset(int row, int k) {
+    return (uint32_t)((((row >> 3) * (TC_BK / 8) + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1));
+}
+
+// Shared-memory matrix descriptor: start address, leading-dimension byte
+// offset (between core matrices adjacent in K), stride-dimension byte offset
+// (between core matrices adjacent in M or N), the fixed version field
+// (bits 46-48 = 1), no swizzle.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
+// (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0), N / 8 at bits
+// 17-22, M / 16 at bits 24-28.
+constexpr uint32_t umma_idesc(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Tile of ROWS x 64 from X with k contiguous (element (row, k) at
+// X[(row0 + row) ld + k0 + k]): 8 consecutive k -- one row of a core matrix --
+// per 16-byte load and store where the row is whole and aligned, elementwise
+// at the edges.
+template <int ROWS>
+__device__ __forceinline__ void load_tile_k(const __nv_bfloat16* __restrict__ X, int ld, int row0, int nrows,
+                                            int k0, int K, unsigned char* T, int tid) {
+    const bool vec = (ld % 8 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+    for (int e = tid; e < ROWS * (TC_BK / 8); e += TC_THREADS) {
+        const int r = e / (TC_BK / 8), c = (e % (TC_BK / 8)) * 8;
+        const int gr = row0 + r, gk = k0 + c;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (gr < nrows) {
+            if (vec && gk + 8 <= K) {
+                v = *reinterpret_cast<const uint4*>(X + (size_t)gr * ld + gk);
+            } else {
+                unsigned w[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0f;
-    const __nv_bfloat16 zero = __float2bfloat16(0.0f);
-    for (int k0 = 0; k0 < K; k0 += BK) {
-        // 64 x 16 elements of each operand, 8 per thread
-        for (int e = tid; e < BM * BK; e += 128) {
-            const int r = e / BK, c = e % BK;
-            const int gm = m0 + r, gk = k0 + c;
-            As[r][c] = (gm < M && gk < K) ? (TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk]) : zero;
-            const int gn = n0 + r;
-            Bs[r][c] = (gn < N && gk < K) ? (TB ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn]) : zero;
+                for (int i = 0; i < 4; ++i) {
+                    const int ka = gk + 2 * i, kb = ka + 1;
+                    w[i] = pack_bf16(ka < K ? X[(size_t)gr * ld + ka] : __float2bfloat16(0.0f),
+                                     kb < K ? X[(size_t)gr * ld + kb] : __float2bfloat16(0.0f));
+                }
+                v = make_uint4(w[0], w[1], w[2], w[3]);
+            }
         }
-        __syncthreads();
-        unsigned af[2][4], bf[4][2];
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int r = wm + i * 16 + g;
-            af[i][0] = pack_bf16(As[r][2 * q], As[r][2 * q + 1]);
-            af[i][1] = pack_bf16(As[r + 8][2 * q], As[r + 8][2 * q + 1]);
-            af[i][2] = pack_bf16(As[r][2 * q + 8], As[r][2 * q + 9]);
-            af[i][3] = pack_bf16(As[r + 8][2 * q + 8], As[r + 8][2 * q + 9]);
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int c = wn + j * 8 + g;
-            bf[j][0] = pack_bf16(Bs[c][2 * q], Bs[c][2 * q + 1]);
-            bf[j][1] = pack_bf16(Bs[c][2 * q + 8], Bs[c][2 * q + 9]);
-        }
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) mma16816(acc[i][j], af[i], bf[j]);
-        __syncthreads();
+        *reinterpret_cast<uint4*>(T + core_offset(r, c)) = v;
     }
-    // epilogue: acc[i][j] holds rows g, g+8 and columns 2q, 2q+1 of tile (i, j)
+}
+
+// Tile of ROWS x 64 from X with the row index contiguous (element (row, k) at
+// X[(k0 + k) ld + row0 + row]): loads coalesce along the rows, stores are
+// elementwise.
+template <int ROWS>
+__device__ __forceinline__ void load_tile_mn(const __nv_bfloat16* __restrict__ X, int ld, int row0, int nrows,
+                                             int k0, int K, unsigned char* T, int tid) {
+    for (int e = tid; e < ROWS * TC_BK; e += TC_THREADS) {
+        const int r = e % ROWS, c = e / ROWS;
+        const int gr = row0 + r, gk = k0 + c;
+        const __nv_bfloat16 v = (gr < nrows && gk < K) ? X[(size_t)gk * ld + gr] : __float2bfloat16(0.0f);
+        *reinterpret_cast<__nv_bfloat16*>(T + core_offset(r, c)) = v;
+    }
+}
+
+template <bool TA, bool TB, int EPI>
+__global__ void __launch_bounds__(TC_THREADS) gemm_tc_kernel(const __nv_bfloat16* __restrict__ A, int lda,
+                                                              const __nv_bfloat16* __restrict__ B, int ldb, int M,
+                                                              int N, int K, const float* __restrict__ bias,
+                                                              const float* __restrict__ aux, int ldaux,
+                                                              float* __restrict__ out_f32,
+                                                              __nv_bfloat16* __restrict__ out_bf16, int ldo,
+                                                              unsigned int* err) {
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    unsigned char* As = tc_smem;
+    unsigned char* Bs = tc_smem + TC_A_BYTES;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tc_smem + TC_A_BYTES + TC_B_BYTES);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(tc_smem + TC_A_BYTES + TC_B_BYTES + 8);
+    volatile int* sflag = reinterpret_cast<volatile int*>(tc_smem + TC_A_BYTES + TC_B_BYTES + 16);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * TC_BN;
+    const uint32_t bar_a = smem_u32(bar);
+
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar_a) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        *sflag = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                     "r"(TC_BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = *tslot;
+    constexpr uint32_t idesc = umma_idesc(TC_BM, TC_BN);
+    const int nk = (K + TC_BK - 1) / TC_BK;
+    bool ok = true;
+    for (int kc = 0; kc < nk && ok; ++kc) {
+        const int k0 = kc * TC_BK;
+        // A tile (row m, k); B tile, K-major: (row n, k) = op(B)[k][n]
+        if (TA) load_tile_mn<TC_BM>(A, lda, m0, M, k0, K, As, tid);
+        else load_tile_k<TC_BM>(A, lda, m0, M, k0, K, As, tid);
+        if (TB) load_tile_k<TC_BN>(B, ldb, n0, N, k0, K, Bs, tid);
+        else load_tile_mn<TC_BN>(B, ldb, n0, N, k0, K, Bs, tid);
+        // the tiles, written by the generic proxy, become visible to the
+        // tensor cores' (async proxy) reads
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+            for (int s = 0; s < TC_BK / 16; ++s)  // K = 16 per instruction: two core matrices along K
+                umma_f16(tmem, umma_desc(a0 + s * 256, 128, (TC_BK / 8) * 128),
+                         umma_desc(b0 + s * 256, 128, (TC_BK / 8) * 128), idesc, (kc > 0 || s > 0) ? 1u : 0u);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                             bar_a)
+                         : "memory");
+            const long long t0 = clock64();
+            while (!mbar_try_wait(bar_a, (uint32_t)(kc & 1))) {
+                if (clock64() - t0 > TC_WAIT_CYCLES) {
+                    *sflag = 1 + (kc & 1);  // the phase still awaited, plus one
+                    atomicOr(err, GRAF_DEVERR_TIMEOUT);
+                    break;
+                }
+            }
+        }
+        __syncthreads();
+        ok = *sflag == 0;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (ok) {
+        // this warp's 32 rows of the tile, 16 columns per load
+        const int m = m0 + warp * 32 + lane;
+        for (int j = 0; j < TC_BN / 16; ++j) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(j * 16), v);
+            if (m >= M) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int m = m0 + wm + i * 16 + g + (r >= 2 ? 8 : 0);
-                const int n = n0 + wn + j * 8 + 2 * q + (r & 1);
-                if (m >= M || n >= N) continue;
-                const float c = acc[i][j][r];
+            for (int c = 0; c < 16; ++c) {
+                const int n = n0 + j * 16 + c;
+                if (n >= N) continue;
                 const size_t o = (size_t)m * ldo + n;
                 if constexpr (EPI == EPI_BIAS_GELU) {
-                    const float pre = c + bias[n];
+                    const float pre = v[c] + bias[n];
                     out_f32[o] = pre;
                     out_bf16[o] = __float2bfloat16(gelu(pre));
                 } else if constexpr (EPI == EPI_BIAS) {
-                    out_f32[o] = c + bias[n];
+                    out_f32[o] = v[c] + bias[n];
                 } else if constexpr (EPI == EPI_DGELU) {
-                    out_bf16[o] = __float2bfloat16(c * gelu_grad(aux[(size_t)m * ldaux + n]));
+                    out_bf16[o] = __float2bfloat16(v[c] * gelu_grad(aux[(size_t)m * ldaux + n]));
                 } else {
-                    out_f32[o] = c;
+                    out_f32[o] = v[c];
                 }
             }
+        }
+    }
+    if (!ok && tid == 0) {
+        // a wait ran out: give the MMAs in flight one more bounded wait
+        // before their tensor memory is freed
+        const long long t0 = clock64();
+        while (!mbar_try_wait(bar_a, (uint32_t)(*sflag - 1)) && clock64() - t0 < TC_WAIT_CYCLES) {
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TC_BN) : "memory");
+    }
 }
 
 template <bool TA, bool TB, int EPI>
 cudaError_t gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K,
                  const float* bias, const float* aux, int ldaux, float* of, __nv_bfloat16* ob, int ldo,
                  cudaStream_t st) {
-    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
-    gemm_bf16_kernel<TA, TB, EPI><<<grid, 128, 0, st>>>(A, lda, B, ldb, M, N, K, bias, aux, ldaux, of, ob, ldo);
+    unsigned int* err = graf::device_error_word_address();
+    if (!err) return cudaErrorUnknown;
+    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<TA, TB, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         TC_SMEM_LAUNCH);
+    if (e != cudaSuccess) return e;
+    dim3 grid((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM);
+    gemm_tc_kernel<TA, TB, EPI><<<grid, TC_THREADS, TC_SMEM_LAUNCH, st>>>(A, lda, B, ldb, M, N, K, bias, aux, ldaux,
+                                                                          of, ob, ldo, err);
     return cudaGetLastError();
 }
 
