@@ -1146,11 +1146,18 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
                     const RowMasks rmk = row_masks(wv, cm, k);
                     const bool uniform = !valid || (rmk.one == full_mask && (rmk.two == 0ull || rmk.two == full_mask));
                     const float wrow = valid ? (rmk.two != 0ull ? 2.0f : (rmk.one != 0ull ? 1.0f : 0.0f)) : 0.0f;
+                    // registers with weight 0 and no row-uniform part to take out
+                    // (wb = 0): their loss terms and their adjoint input c X are
+                    // 0.  A narrow Doppler window leaves most registers so, in
+                    // the same registers on every lane of a warp, so the branches
+                    // below skip the work for the whole warp.
+                    const unsigned long long need = !valid ? 0ull : (wb != 0.0f ? full_mask : rmk.one);
                     // pass 1 (running shift only): largest weighted a2 of the row
                     // (two independent chains)
                     float tmx[2] = {-CUDART_INF_F, -CUDART_INF_F};
                     if (!fixed) {
                         sfor<0, P::VALS>([&](auto w) {
+                            if (!mbit<decltype(w)::value>(need)) return;
                             const float2 x = v[w];
                             const float a2 = fmaf(fmaf(x.x, x.x, x.y * x.y), invE2, eps_n);
                             const float wt = uniform ? wrow : mweight<decltype(w)::value>(rmk);
@@ -1185,6 +1192,10 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
                     float r_c[2] = {0.0f, 0.0f}, r_h[2] = {-CUDART_INF_F, -CUDART_INF_F};
                     sfor<0, P::VALS>([&](auto w) {
                         constexpr int h = decltype(w)::value & 1;
+                        if (!mbit<decltype(w)::value>(need)) {
+                            v[w] = make_float2(0.0f, 0.0f);
+                            return;
+                        }
                         const float2 x = v[w];
                         const float a2 = fmaf(fmaf(x.x, x.x, x.y * x.y), invE2, eps_n);
                         const float wt = uniform ? wrow : mweight<decltype(w)::value>(rmk);
@@ -1330,9 +1341,9 @@ template <int M>
 cudaError_t run_fused_m(const AfParams& p, cudaStream_t st) {
     if (p.acc_copies < 1 || (RowPlan<M>::THREADS / RowPlan<M>::TPR) % p.acc_copies) return cudaErrorInvalidConfiguration;
     const size_t smem = backward_smem<M>(p.N, p.acc_copies, p.phase_only, p.periodic);
-    // the phase-gradient-only kernel carries no complex scatter (for N > M/2,
-    // the periodic AF among them, it measured slower and is not used)
+    // the phase-gradient-only kernel carries no complex scatter
     if (2 * p.N <= M && p.phase_only) return launch_rows<M>(af_fused_kernel<M, true, true>, smem, p, st);
+    if (p.phase_only) return launch_rows<M>(af_fused_kernel<M, false, true>, smem, p, st);
     if (2 * p.N <= M) return launch_rows<M>(af_fused_kernel<M, true, false>, smem, p, st);
     return launch_rows<M>(af_fused_kernel<M, false, false>, smem, p, st);
 }
