@@ -506,8 +506,9 @@ __device__ __forceinline__ void write_grad_partial(const AfParams& p, const Wave
     }
 }
 
-template <int M, bool HALF>
+template <int M, bool HALF, bool RO>
 __device__ __forceinline__ void backward_item(const AfParams& p, int b, int tile, unsigned char* smem) {
+    const bool phase_only = RO || p.phase_only;  // RO: only dL/dphi is wanted, known at compile time
     using P = RowPlan<M>;
     constexpr int SLOTS = P::THREADS / P::TPR;
     // the waveform's parameters live in shared memory (CTA-uniform), so they
@@ -526,14 +527,24 @@ __device__ __forceinline__ void backward_item(const AfParams& p, int b, int tile
     for (int i = tid; i < (int)(acc_region_bytes(p) / sizeof(float2)); i += P::THREADS)
         acc_all[i] = make_float2(0.0f, 0.0f);
     const float E = load_signal(wv, s_sm, red);  // includes __syncthreads
-    const float invE2 = 1.0f / (E * E);
-    const float eps_n = wv.eps * invE2;
-    const float bl2 = wv.beta * 1.4426950408889634f;
-    const float psl_soft = p.saved8[(size_t)b * 8 + 1];
-    const float sh = psl_soft * bl2;
-    const float p0 = ex2a(-sh);
-    const float cA = fmaf(wv.w_psl, p0, wv.w_isl) * invE2;  // A' / E^2
-    const float cP = wv.w_psl * invE2;
+    // the item's constants live in shared memory and are re-read after the
+    // forward transform, so that none of them occupies a register during it
+    __shared__ float s_c[7];
+    if (tid == 0) {
+        const float invE2 = 1.0f / (E * E);
+        const float bl2 = wv.beta * 1.4426950408889634f;
+        const float psl_soft = p.saved8[(size_t)b * 8 + 1];
+        const float sh = psl_soft * bl2;
+        const float p0 = ex2a(-sh);
+        s_c[0] = invE2;
+        s_c[1] = wv.eps * invE2;                         // eps / E^2
+        s_c[2] = bl2;
+        s_c[3] = sh;
+        s_c[4] = p0;
+        s_c[5] = fmaf(wv.w_psl, p0, wv.w_isl) * invE2;  // cA = A' / E^2
+        s_c[6] = wv.w_psl * invE2;                       // cP
+    }
+    __syncthreads();
     float csum = 0.0f;
     float2* buf = bufs + (size_t)slot * (P::SPLIT ? P::SMEM_ROW / 2 : P::SMEM_ROW);
     const ColMasks cm = col_masks<M>(wv, t);
@@ -553,7 +564,7 @@ __device__ __forceinline__ void backward_item(const AfParams& p, int b, int tile
     for (int it = 0; it < iters; ++it) {
         const int k = row0 + slot + it * SLOTS;
         // row 0 is R[0,n] = |s[n]|^2: it does not depend on the phases
-        const bool valid = k < row_end && !(p.phase_only && k == 0);
+        const bool valid = k < row_end && !(phase_only && k == 0);
         build_lag_row<M, HALF>(v, s_sm, wv.N, wv.periodic ? k - wv.N : k, t, valid);
         // one transform instance, run twice: recompute X, then the adjoint as
         // conj(DFT(conj(c X)))
@@ -562,11 +573,20 @@ __device__ __forceinline__ void backward_item(const AfParams& p, int b, int tile
             row_sync<P::TPR>(slot);
             row_fft<M, false, false, false>(v, buf, t, slot);
             if (ph == 1) break;
+            const float invE2 = s_c[0], eps_n = s_c[1], bl2 = s_c[2], sh = s_c[3], p0 = s_c[4], cA = s_c[5],
+                        cP = s_c[6];
             const RowMasks rmk = row_masks(wv, cm, k);
             const bool uniform = rmk.one == full_mask && (rmk.two == 0ull || rmk.two == full_mask);
             const float wrow = valid ? (rmk.two != 0ull ? 2.0f : (rmk.one != 0ull ? 1.0f : 0.0f)) : 0.0f;
             const float wb = valid ? (float)base_weight(wv, k) : 0.0f;
+            // registers with weight 0 and no row-uniform part (wb = 0) have
+            // c = 0: skipped (the same registers on every lane for a Doppler band)
+            const unsigned long long need = !valid ? 0ull : (wb != 0.0f ? full_mask : rmk.one);
             sfor<0, P::VALS>([&](auto w) {
+                if (!mbit<decltype(w)::value>(need)) {
+                    v[w] = make_float2(0.0f, 0.0f);
+                    return;
+                }
                 const float2 x = v[w];
                 const float a2 = fmaf(fmaf(x.x, x.x, x.y * x.y), invE2, eps_n);
                 const float wt = (uniform || !valid) ? wrow : mweight<decltype(w)::value>(rmk);
@@ -583,20 +603,21 @@ __device__ __forceinline__ void backward_item(const AfParams& p, int b, int tile
                 v[w] = make_float2(c * x.x, -c * x.y);
             });
         }
-        if (p.phase_only)
+        if (phase_only) {
             scatter_row_real<M, HALF>(v, acc_r, s_sm, wv.N, wv.periodic ? k - wv.N : k, t, valid, slot, turns,
                                       my_turn, wv.periodic != 0);
-        else
+        } else if constexpr (!RO) {
             scatter_row<M, HALF, true>(v, acc, s_sm, wv.N, wv.periodic ? k - wv.N : k, t, valid, slot, turns,
                                        my_turn, wv.periodic != 0);
+        }
     }
     write_grad_partial<M>(p, wv, acc_all, red, csum, tile);
 }
 
-template <int M, bool HALF>
+template <int M, bool HALF, bool RO>
 __global__ void __launch_bounds__(RowPlan<M>::THREADS, RowPlan<M>::MIN_BLOCKS) af_backward_kernel(AfParams p) {
     extern __shared__ __align__(256) unsigned char smem[];
-    for_each_item(p, [&](int b, int tile) { backward_item<M, HALF>(p, b, tile, smem); });
+    for_each_item(p, [&](int b, int tile) { backward_item<M, HALF, RO>(p, b, tile, smem); });
 }
 
 // ---------------------------------------------------------- match to a target
@@ -1321,7 +1342,9 @@ template <int M>
 cudaError_t run_backward_m(const AfParams& p, cudaStream_t st) {
     if (p.acc_copies < 1 || (RowPlan<M>::THREADS / RowPlan<M>::TPR) % p.acc_copies) return cudaErrorInvalidConfiguration;
     const size_t smem = backward_smem<M>(p.N, p.acc_copies, p.phase_only, p.periodic);
-    return launch_rows<M>(af_backward_kernel<M, false>, smem, p, st);
+    // the phase-gradient-only kernel carries no complex scatter
+    if (p.phase_only) return launch_rows<M>(af_backward_kernel<M, false, true>, smem, p, st);
+    return launch_rows<M>(af_backward_kernel<M, false, false>, smem, p, st);
 }
 
 // The kernels that run two transforms per row use one transform instance for

@@ -334,6 +334,20 @@ template <int M, int P_, int R, int NS, bool INV, bool HOUT>
 __device__ __forceinline__ void pass_compute(float2* v, int t) {
     using P = RowPlan<M>;
     constexpr int NB = P::VALS / R;
+    if constexpr (NB > 1 && P::TPR % NS == 0) {
+        // j mod NS = t mod NS for every butterfly j = t + TPR u of this
+        // thread: one load of each twiddle serves all of them
+        const float2* tw = tw_table<M, P_>() + (t % NS);
+        sfor<1, R>([&](auto r) {
+            const float2 w = ld_tw(tw + (decltype(r)::value - 1) * NS);
+            sfor<0, NB>([&](auto u) {
+                float2& x = v[decltype(u)::value * R + decltype(r)::value];
+                x = INV ? cmulc(x, w) : cmul(x, w);
+            });
+        });
+        sfor<0, NB>([&](auto u) { dft<R, decltype(u)::value * R, 1, INV, false, HOUT>(v); });
+        return;
+    }
     sfor<0, NB>([&](auto u) {
         const int j = t + P::TPR * decltype(u)::value;
         const float2* tw = tw_table<M, P_>() + (j % NS);
