@@ -1077,6 +1077,34 @@ def learned_eval(args, dev):
         secs["graf_train"] = time.perf_counter() - t3
         tuned = arm(learned.time_to_target(net, test, target, rand, args.eval_steps, device=dev))
     secs["total"] = time.perf_counter() - t_all
+    errors = None
+    if not args.no_cpu_baseline:
+        # the trained network's outputs and one held-out spec's masked-ISL loss
+        # and gradient at its proposal, against the FP64 references
+        import oracle
+        from oracle import mlp as omlp
+
+        from paper_2506_22935_gb300 import graf as g
+        nchk = min(16, args.test_specs)
+        sub = {k: v[:nchk] for k, v in test.items()}
+        fsub = inputs.spec_features(sub)
+        out = net.forward(torch.from_numpy(fsub).to(dev)).cpu().numpy().astype(np.float64)
+        ref, _ = omlp.forward(fsub.astype(np.float64), net.master.cpu().numpy().astype(np.float64))
+        i = int(np.argmin(sub["K"]))  # the narrowest delay mask: the cheapest FP64 check
+        phi_i = np.mod(out[i], 2 * np.pi).astype(np.float32)
+        win = g.Window.masked(int(sub["K"][i]), int(sub["Mw"][i]))
+        plan = g.BatchPlan([1024], M=[2048], windows=[win], losses=[g.Loss(0.0, 1.0, 50.0, EPS)], device=dev)
+        o8, gr = plan.loss_backward(torch.from_numpy(phi_i).to(dev))
+        torch.cuda.synchronize(dev)
+        plan.close()
+        _, gp_ref, o8_ref = oracle.grad(oracle.signal_from_phase(phi_i.astype(np.float64)), 2048, win.as_tuple(),
+                                        0.0, 1.0, 50.0, EPS, nthreads=os.cpu_count() or 1)
+        gr = gr.double().cpu().numpy()
+        errors = {"mlp_output_rel_l2_vs_bf16_reference": float(np.linalg.norm(out - ref) / np.linalg.norm(ref)),
+                  "mlp_specs_checked": nchk,
+                  "masked_isl_rel": float(abs(float(o8[0, 2]) - o8_ref[2]) / o8_ref[2]),
+                  "masked_isl_grad_rel_l2": float(np.linalg.norm(gr - gp_ref) / np.linalg.norm(gp_ref)),
+                  "graf_check": f"held-out spec {i} (K={int(sub['K'][i])}, Mw={int(sub['Mw'][i])}) at its proposal"}
     every = lambda c: [round(x, 4) for x in c[:: max(1, len(c) // 10)]]
     return {"metric": "time to masked-ISL target, learned vs plain", "value": labels_arm["value"],
             "unit": "median over held-out specs of GPU time to target, learned proposal / random init",
@@ -1094,7 +1122,8 @@ def learned_eval(args, dev):
             "median_target_isl": float(np.median(target)),
             "label_isl_median_start_end": [float(np.median(lh[0])), float(np.median(lh[-1]))],
             "labels_only": labels_arm, "labels_then_graf_finetune": tuned,
-            "label_loss_curve": every(label_curve), "graf_loss_curve": every(graf_curve), "seconds": secs}
+            "label_loss_curve": every(label_curve), "graf_loss_curve": every(graf_curve), "seconds": secs,
+            "errors_vs_fp64": errors}
 
 
 def run_learned(args):
