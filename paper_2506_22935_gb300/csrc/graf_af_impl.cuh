@@ -475,10 +475,10 @@ __device__ __forceinline__ void scatter_row_real(const float2* v, float* acc, co
 // fixed order (warp xor tree, then warps in order).  Phase-only mode: the
 // accumulators are real (copy i at floats [i N, (i+1) N)) and a partial is
 // stored as (sum, 0).
-template <int M>
+template <int M, int V = 0>
 __device__ __forceinline__ void write_grad_partial(const AfParams& p, const Wave& wv, const float2* acc_all,
                                                    float* red, float cs, int tile) {
-    using P = RowPlan<M>;
+    using P = RowPlan<M, V>;
     const int tid = threadIdx.x;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
@@ -1045,10 +1045,10 @@ cudaError_t run_composite_m(const CompParams& q, cudaStream_t st) {
 // not uniform) contribute loss partials only; af_backward_kernel adds their
 // gradient once PSL_soft is known.  On the PSL path every slot owns its
 // accumulator (acc_copies == slot count).
-template <int M, bool HALF, bool RO>
+template <int M, bool HALF, bool RO, int V = 0>
 __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, unsigned char* smem) {
     const bool phase_only = RO || p.phase_only;  // RO: only dL/dphi is wanted, known at compile time
-    using P = RowPlan<M>;
+    using P = RowPlan<M, V>;
     constexpr int SLOTS = P::THREADS / P::TPR;
     constexpr int NW = P::THREADS / 32;
     // the waveform's parameters live in shared memory (CTA-uniform), so they
@@ -1059,7 +1059,7 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
     const Wave& wv = s_wave;
     float2* s_sm = reinterpret_cast<float2*>(smem);
     float2* bufs = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(sig_len(p)));
-    float2* acc_all = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(sig_len(p)) + row_buffer_bytes<M>());
+    float2* acc_all = reinterpret_cast<float2*>(smem + smem_signal_bytes<M>(sig_len(p)) + row_buffer_bytes<M, V>());
     float* red = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(acc_all) +
                                           acc_region_bytes(p));
     // red: [0,16) reductions, [32,48) slot-max scratch (TPR > 32), [64, 64+SLOTS) final slot shifts
@@ -1120,7 +1120,7 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
 #pragma unroll 1
             for (int ph = 0; ph < 2; ++ph) {
                 row_sync<P::TPR>(slot);
-                row_fft<M, false, false, false>(v, buf, t, slot);
+                row_fft<M, false, false, false, V>(v, buf, t, slot);
                 if (ph == 1) break;
                 const float invE2 = s_k[0], eps_n = s_k[1], bl2 = s_k[2], cP = s_k[3], cI = s_k[4];
                 const bool psl_mode = wv.w_psl != 0.0f;
@@ -1294,19 +1294,19 @@ __device__ __forceinline__ void fused_item(const AfParams& p, int b, int tile, u
         }
         p.rec[wv.rec_off + tile] = a;
     }
-    write_grad_partial<M>(p, wv, acc_all, red, cs, tile);
+    write_grad_partial<M, V>(p, wv, acc_all, red, cs, tile);
 }
 
-template <int M, bool HALF, bool RO>
-__global__ void __launch_bounds__(RowPlan<M>::THREADS, RowPlan<M>::MIN_BLOCKS) af_fused_kernel(AfParams p) {
+template <int M, bool HALF, bool RO, int V = 0>
+__global__ void __launch_bounds__(RowPlan<M, V>::THREADS, RowPlan<M, V>::MIN_BLOCKS) af_fused_kernel(AfParams p) {
     extern __shared__ __align__(256) unsigned char smem[];
-    for_each_item(p, [&](int b, int tile) { fused_item<M, HALF, RO>(p, b, tile, smem); });
+    for_each_item(p, [&](int b, int tile) { fused_item<M, HALF, RO, V>(p, b, tile, smem); });
 }
 
 // ---------------------------------------------------------- host launchers
-template <int M, class K>
+template <int M, int V = 0, class K>
 static cudaError_t launch_rows(K kernel, size_t smem, const AfParams& p, cudaStream_t st) {
-    using P = RowPlan<M>;
+    using P = RowPlan<M, V>;
     if (smem > kMaxSmem) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -1363,6 +1363,21 @@ cudaError_t run_match_m(const AfParams& p, cudaStream_t st) {
 template <int M>
 cudaError_t run_fused_m(const AfParams& p, cudaStream_t st) {
     if (p.acc_copies < 1 || (RowPlan<M>::THREADS / RowPlan<M>::TPR) % p.acc_copies) return cudaErrorInvalidConfiguration;
+    if constexpr (M == 8192) {
+        // two row slots per CTA, each with a whole exchange buffer (no
+        // real/imaginary split), when the signal is short enough for both to
+        // fit: one gradient accumulator per slot, else one shared in turns
+        if (2 * p.N <= M && p.phase_only && !p.periodic) {
+            for (int a = 2; a >= 1; a /= 2) {
+                const size_t smem2 = backward_smem<M, 1>(p.N, a, 1, 0);
+                if (smem2 <= kMaxSmem) {
+                    AfParams q = p;
+                    q.acc_copies = a;
+                    return launch_rows<M, 1>(af_fused_kernel<M, true, true, 1>, smem2, q, st);
+                }
+            }
+        }
+    }
     const size_t smem = backward_smem<M>(p.N, p.acc_copies, p.phase_only, p.periodic);
     // the phase-gradient-only kernel carries no complex scatter
     if (2 * p.N <= M && p.phase_only) return launch_rows<M>(af_fused_kernel<M, true, true>, smem, p, st);

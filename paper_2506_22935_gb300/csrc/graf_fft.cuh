@@ -185,7 +185,11 @@ __host__ __device__ __forceinline__ void dft(float2* v) {
 }
 
 // ------------------------------------------------------------------ row plan
-template <int M>
+// V = 1 (M = 8192 only): two row slots per CTA of 512 threads, each with a
+// whole exchange buffer (no real/imaginary split) -- the plan of the fused
+// kernel when the signal is short enough for both buffers to fit (N <= M/2,
+// phase gradient only).
+template <int M, int V = 0>
 struct RowPlan {
     static_assert(M >= 8 && M <= 16384 && (M & (M - 1)) == 0, "M must be a power of two in [8,16384]");
     // values per thread: 32 from M = 512 on, so that a thread needs at most
@@ -196,7 +200,8 @@ struct RowPlan {
     // without spilling).  64 for M = 64, M below.
     static constexpr int VALS = M >= 512 ? 32 : (M >= 128 ? 16 : (M < 64 ? M : 64));
     static constexpr int TPR = M / VALS;           // threads per row
-    static constexpr int THREADS = TPR > 256 ? TPR : 256;  // threads per CTA
+    static_assert(V == 0 || M == 8192, "the two-slot plan exists for M = 8192 only");
+    static constexpr int THREADS = V == 1 ? 2 * TPR : (TPR > 256 ? TPR : 256);  // threads per CTA
     static constexpr int NPASS = TPR == 1 ? 1 : (TPR <= VALS ? 2 : 3);
     static constexpr int R0 = VALS;
     static constexpr int R1 = NPASS == 1 ? 1 : (NPASS == 2 ? TPR : 16);
@@ -208,7 +213,7 @@ struct RowPlan {
     static constexpr int SMEM_ROW = NPASS == 1 ? 0 : M + M / PAD;
     // exchange real and imaginary halves separately (half the buffer) for the
     // largest rows so that the backward's accumulators still fit
-    static constexpr bool SPLIT = M >= 8192;
+    static constexpr bool SPLIT = V == 0 && M >= 8192;
 };
 
 template <int PAD>
@@ -287,9 +292,9 @@ __device__ __forceinline__ void pass_load(float2* v, const float2* buf, int t) {
 // Exchange through shared memory between pass p (radix RS, span NSS) and
 // pass p+1 (radix RL): store, barrier, load.  The caller guarantees the buffer
 // is free on entry (a barrier since its last reads).
-template <int M, int RS, int NSS, int RL>
+template <int M, int RS, int NSS, int RL, int V = 0>
 __device__ __forceinline__ void exchange(float2* v, float2* buf, int t, int slot) {
-    using P = RowPlan<M>;
+    using P = RowPlan<M, V>;
     if constexpr (!P::SPLIT) {
         pass_store<M, RS, NSS, true, false>(v, buf, t);
         row_sync<P::TPR>(slot);
@@ -383,22 +388,22 @@ __device__ __forceinline__ void final_permute(float2* v) {
 // `buf` is this row's shared-memory buffer (RowPlan<M>::SMEM_ROW float2),
 // free on entry; on exit it may still be read by other threads of the row
 // until the next row_sync.
-template <int M, bool INV, bool HIN, bool HOUT>
+template <int M, bool INV, bool HIN, bool HOUT, int V = 0>
 __device__ __forceinline__ void row_fft(float2* v, float2* buf, int t, int slot) {
-    using P = RowPlan<M>;
+    using P = RowPlan<M, V>;
     if constexpr (P::NPASS == 1) {
         dft<P::R0, 0, 1, INV, HIN, HOUT>(v);
     } else if constexpr (P::NPASS == 2) {
         dft<P::R0, 0, 1, INV, HIN, false>(v);
-        exchange<M, P::R0, 1, P::R1>(v, buf, t, slot);
+        exchange<M, P::R0, 1, P::R1, V>(v, buf, t, slot);
         pass_compute<M, 1, P::R1, P::R0, INV, HOUT>(v, t);
         final_permute<P::VALS, P::R1>(v);
     } else {
         dft<P::R0, 0, 1, INV, HIN, false>(v);
-        exchange<M, P::R0, 1, P::R1>(v, buf, t, slot);
+        exchange<M, P::R0, 1, P::R1, V>(v, buf, t, slot);
         pass_compute<M, 1, P::R1, P::R0, INV, false>(v, t);
         row_sync<P::TPR>(slot);
-        exchange<M, P::R1, P::R0, P::R2>(v, buf, t, slot);
+        exchange<M, P::R1, P::R0, P::R2, V>(v, buf, t, slot);
         pass_compute<M, 2, P::R2, P::R0 * P::R1, INV, HOUT>(v, t);
         final_permute<P::VALS, P::R2>(v);
     }

@@ -250,9 +250,9 @@ template <int M>
 __host__ __device__ constexpr size_t smem_signal_bytes(int N) {
     return ((size_t)N * sizeof(float2) + 255) & ~(size_t)255;
 }
-template <int M>
+template <int M, int V = 0>
 __host__ __device__ constexpr size_t row_buffer_bytes() {
-    using P = RowPlan<M>;
+    using P = RowPlan<M, V>;
     return (((size_t)P::SMEM_ROW * (P::SPLIT ? sizeof(float) : sizeof(float2)) * (P::THREADS / P::TPR)) + 255) &
            ~(size_t)255;
 }
@@ -263,9 +263,9 @@ constexpr size_t forward_smem(int N) {
 // Gradient accumulators: complex (float2) in general, real (float) when only
 // the phase gradient is wanted (see scatter_row_real).
 // per: periodic AF (the signal is stored twice; accumulators keep N entries).
-template <int M>
+template <int M, int V = 0>
 constexpr size_t backward_smem(int N, int acc_copies, int real = 0, int per = 0) {
-    return smem_signal_bytes<M>(per ? 2 * N : N) + row_buffer_bytes<M>() +
+    return smem_signal_bytes<M>(per ? 2 * N : N) + row_buffer_bytes<M, V>() +
            (((size_t)acc_copies * acc_stride(N, RowPlan<M>::TPR) * (real ? sizeof(float) : sizeof(float2)) + 255) &
             ~(size_t)255) +
            kRedBytes;
